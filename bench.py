@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Throughput of the Count Sketch halo-finder hot path on one GB300.
+
+A step is one pass of the whole path over one synthetic snapshot: reset the
+sketch, stream every particle through it (mesh reduction, sampling, Add), then
+the full-search top-k (Algorithm 1 of arXiv:1711.00975).  The metric is
+particles per second into sketch + top-k; the JSON line also carries the HBM
+roofline of the dominant kernel, the end-to-end number through the C ABI with
+host buffers, the CPU oracle's throughput on a bounded sample, and clocks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+# the 10^9-particle, 500 Mpc/h workload (5000^3 cells of 0.1 Mpc/h)
+WORKLOAD = dict(name="halo-box-1e9", n=10**9, box=500.0, n_halo=10**6, cell=0.1, rows=5,
+                log2_width=24, k=10**4, box_seed=1, hash_seed=1, sample_seed=2)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--rate", type=float, default=1.0)
+    ap.add_argument("--n", type=int, default=None, help="override the particle count")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--second-rate", type=float, default=0.1,
+                    help="also time this sample rate (0 to skip)")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._proc = None
+
+    def __enter__(self):
+        try:
+            self._proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self._proc = None
+        return self
+
+    def _read(self):
+        for line in self._proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self._proc is not None:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self._proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if s[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def make_box(n):
+    import synth
+    spec = synth.BoxSpec(n=n, box=WORKLOAD["box"], n_halo=max(1, WORKLOAD["n_halo"] * n // 10**9),
+                         seed=WORKLOAD["box_seed"])
+    return spec, synth.HaloBox(spec)
+
+
+def cpu_sample_rates(xyz_host: np.ndarray, n_update: int, n_cells: int, k: int, rate: float):
+    """Oracle throughput on a bounded sample: (particles/s, cells/s, cores, seconds)."""
+    import oracle
+    cores = oracle.default_threads()
+    p = oracle.Params(WORKLOAD["rows"], WORKLOAD["log2_width"], WORKLOAD["box"], WORKLOAD["cell"],
+                      WORKLOAD["hash_seed"], WORKLOAD["sample_seed"])
+    C = oracle.new_counters(p)
+    sample = xyz_host[:n_update]
+    t0 = time.perf_counter()
+    oracle.sketch_update(C, p, sample, rate=rate, nthreads=cores)
+    t1 = time.perf_counter()
+    oracle.topk_full(C, p, k, nthreads=cores, key_lo=0, key_hi=n_cells)
+    t2 = time.perf_counter()
+    return n_update / (t1 - t0), n_cells / (t2 - t1), cores, t2 - t0
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step a bounded sample of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n = args.n or WORKLOAD["n"]
+    G = round(WORKLOAD["box"] / WORKLOAD["cell"])
+    n_upd = min(n, 1 << 24)
+    n_cells = min(G ** 3, 4 * 10**8)
+    spec, box = make_box(n)
+    xyz = box.generate(0, n_upd)
+    for _ in range(args.warmup):
+        cpu_sample_rates(xyz, n_upd, n_cells, WORKLOAD["k"], args.rate)
+    times = []
+    cores = 1
+    for _ in range(args.steps):
+        ru, rq, cores, _ = cpu_sample_rates(xyz, n_upd, n_cells, WORKLOAD["k"], args.rate)
+        times.append(n / ru + G ** 3 / rq)      # extrapolated time of one full step
+    step_s = float(np.mean(times))
+    value = n / step_s
+    line = {"impl": "reference", "metric": "particles/s into sketch+top-k", "value": value,
+            "unit": "particles/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "particles": n, "grid": G,
+                       "rows": WORKLOAD["rows"], "width": 1 << WORKLOAD["log2_width"],
+                       "k": WORKLOAD["k"], "sample_rate": args.rate},
+            "cpu_baseline": {"value": value, "unit": "particles/s", "cores": cores, "kind": "oracle",
+                             "sample": f"update of {n_upd} particles + full search of {n_cells} "
+                                       f"cells per step, extrapolated to {n} particles and "
+                                       f"{G ** 3} cells"},
+            "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    import synth
+    from paper_1711_00975_gb300 import halosketch as hs
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    hs.lib()
+
+    n = args.n or WORKLOAD["n"]
+    k = WORKLOAD["k"]
+    G = round(WORKLOAD["box"] / WORKLOAD["cell"])
+    spec, box = make_box(n)
+    t0 = time.time()
+    host = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+    box.generate_into_ptr(host.data_ptr(), 0, n)
+    gen_s = time.time() - t0
+    dev = host.to(f"cuda:{local}", non_blocking=False)
+    stream = torch.cuda.current_stream()
+    sk = hs.Sketch(WORKLOAD["rows"], WORKLOAD["log2_width"], WORKLOAD["box"], WORKLOAD["cell"],
+                   WORKLOAD["hash_seed"], WORKLOAD["sample_seed"], stream=stream)
+    keys = np.empty(k, np.uint64)
+    ests = np.empty(k, np.int32)
+
+    def step(src, rate):
+        hs.sketch_reset(sk.h)
+        hs.sketch_update(sk.h, src, n, rate)
+        return hs.topk_extract(sk.h, k, keys, ests)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def timed(src, rate, steps, warmup):
+        for _ in range(warmup):
+            step(src, rate)
+        sk.stats(reset=True)
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        upd = []
+        ev0.record(stream)
+        for _ in range(steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            hs.sketch_reset(sk.h)
+            a.record(stream)
+            hs.sketch_update(sk.h, src, n, rate)
+            b.record(stream)
+            hs.topk_extract(sk.h, k, keys, ests)
+            upd.append((a, b))
+        ev1.record(stream)
+        barrier()
+        total_ms = ev0.elapsed_time(ev1)
+        upd_ms = [a.elapsed_time(b) for a, b in upd]
+        st = sk.stats(reset=True)
+        if dist is not None:
+            t = torch.tensor([total_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        return total_ms, upd_ms, st
+
+    hbm, peak_kind = peaks()
+    with Clocks(local) as clk:
+        total_ms, upd_ms, st = timed(dev, args.rate, args.steps, args.warmup)
+    clocks = clk.summary()
+    ms_step = total_ms / args.steps
+    value = n * world / (ms_step * 1e-3)
+    upd_avg = float(np.mean(upd_ms))
+    search_avg = st["search_ms"] / max(1, st["search_launches"])
+    search_per_step = st["search_ms"] / args.steps
+    topk_per_step = st["topk_ms"] / args.steps
+    stream_gbs = 12.0 * n / (upd_avg * 1e-3) / 1e9
+
+    # dominant kernel by device time per step
+    if upd_avg >= search_per_step:
+        roof = {"kernel": "update", "bound": "hbm", "achieved": stream_gbs, "peak": hbm,
+                "unit": "GB/s", "frac": stream_gbs / hbm, "traffic": None,
+                "peak_source": peak_kind}
+    else:
+        cells_per_s = G ** 3 / (search_avg * 1e-3)
+        roof = {"kernel": "full_search", "bound": "hbm", "achieved": None, "peak": hbm,
+                "unit": "GB/s", "frac": None, "traffic": None, "peak_source": peak_kind,
+                "cells_per_s": cells_per_s}
+
+    second = None
+    if args.second_rate and args.second_rate != args.rate:
+        t2, u2, s2 = timed(dev, args.second_rate, max(2, args.steps // 2), 1)
+        u2avg = float(np.mean(u2))
+        second = {"sample_rate": args.second_rate, "value": n * world / (t2 / max(2, args.steps // 2) * 1e-3),
+                  "update_ms": u2avg, "stream_gbs": 12.0 * n / (u2avg * 1e-3) / 1e9,
+                  "stream_frac": 12.0 * n / (u2avg * 1e-3) / 1e9 / hbm}
+
+    red = None
+    try:
+        ops = hs.hs_measure_red_rate(WORKLOAD["rows"] << WORKLOAD["log2_width"], 1 << 31)
+        red = {"ops_per_s": ops, "table_counters": WORKLOAD["rows"] << WORKLOAD["log2_width"],
+               "needed_ops_per_particle": WORKLOAD["rows"] * args.rate,
+               "particles_per_s_bound": ops / (WORKLOAD["rows"] * args.rate)}
+    except hs.HSError as e:
+        red = {"error": str(e)}
+
+    e2e = None
+    if not args.no_e2e:
+        steps_e = max(2, args.steps // 2)
+        for _ in range(1):
+            step(host, args.rate)
+        barrier()
+        t0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps_e):
+            step(host, args.rate)
+        e1.record(stream)
+        barrier()
+        ems = e0.elapsed_time(e1) / steps_e
+        wall = (time.perf_counter() - t0) / steps_e
+        e2e = {"value": n * world / max(ems * 1e-3, wall), "unit": "particles/s",
+               "h2d_bytes_per_step": 12 * n, "d2h_bytes_per_step": 12 * k,
+               "ms_per_step": max(ems, wall * 1e3)}
+
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        n_upd = min(n, 1 << 27)
+        n_cells = min(G ** 3, 2 * 10**9)
+        ru, rq, cores, secs = cpu_sample_rates(host.numpy(), n_upd, n_cells, k, args.rate)
+        cpu = {"value": n / (n / ru + G ** 3 / rq), "unit": "particles/s", "cores": cores,
+               "kind": "oracle", "seconds": secs,
+               "sample": f"oracle update of the first {n_upd} particles ({ru:.3g} particles/s) and "
+                         f"full search of the first {n_cells} cells ({rq:.3g} cells/s), "
+                         f"extrapolated to {n} particles + {G ** 3} cells"}
+
+    line = {"metric": "particles/s into sketch+top-k", "value": value, "unit": "particles/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "particles": n, "box_mpc_h": WORKLOAD["box"],
+                       "cell_mpc_h": WORKLOAD["cell"], "grid": G, "rows": WORKLOAD["rows"],
+                       "width": 1 << WORKLOAD["log2_width"], "k": k, "sample_rate": args.rate,
+                       "l2": "inputs (12 GB) larger than L2", "generation_s": gen_s},
+            "breakdown": {"update_ms": upd_avg, "topk_ms": topk_per_step,
+                          "full_search_ms": search_per_step,
+                          "stream_gbs": stream_gbs, "stream_frac": stream_gbs / hbm,
+                          "candidates": st["last_candidates"], "threshold": st["last_threshold"],
+                          "passes": st["last_passes"]},
+            "roofline": roof, "red_rate": red, "second_rate": second, "e2e": e2e,
+            "cpu_baseline": cpu, "clocks": clocks,
+            "gpu_launches": int(st["kernel_launches"])}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sk.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,193 @@
+/*
+ * halosketch.h - C ABI of the GB300 (sm_103a) Count Sketch halo finder.
+ *
+ * The library implements the data-parallel hot path of Ivkin et al.,
+ * "Scalable Streaming Tools for Analyzing N-body Simulations: Finding Halos
+ * and Investigating Excursion Sets in One Pass" (arXiv:1711.00975):
+ *
+ *   particle xyz --(mesh reduction, Sec. 2.1)--> cell key
+ *                --(Bernoulli sampling by an index hash, Sec. 3.1)-->
+ *                --(Count Sketch Add, Sec. 2.2)--> t x W int32 counters
+ *   counters --(Estimate = median of rows, Sec. 2.2; full search over every
+ *               cell, Algorithm 1 "CSFS")--> top-k heaviest cells.
+ *
+ * It answers the top-k form of the Heavy Hitter problem (Sec. 2.1, Problem 1:
+ * the k most frequent cells are the (alpha_k, l1)-heavy items).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an hs_status; none aborts.  On failure the thread's
+ *    last error message is available from hs_last_error().
+ *  - The caller owns all input and output buffers; the library owns the
+ *    counters and its scratch memory.
+ *  - Buffers may be device memory or host memory (pageable or pinned) unless
+ *    the entry point says otherwise; the library inspects each pointer.
+ *  - Work is ordered on the CUDA stream given to sketch_create (the legacy
+ *    default stream when NULL).  Calls on one handle are not thread-safe.
+ *  - Particles are float32 xyz triples, array-of-structures
+ *    [x0, y0, z0, x1, y1, z1, ...], 12 bytes per particle.
+ *  - Cells: G = round(box / cell) per axis, inv_cell = (float)(1.0 / cell)
+ *    (computed in double, rounded once to float).  The cell coordinate on each
+ *    axis is floor(fl32(x * inv_cell)) reduced periodically into [0, G); a
+ *    particle whose scaled coordinate is not a finite value in
+ *    [-2^31, 2^31) is skipped.  key = cx + G * (cy + G * cz) (uint64).
+ *  - Row r of the sketch hashes a cell with vector multiply-shift:
+ *    v = (a0*cx + a1*cy + a2*cz + b) mod 2^64, bucket = v >> (64 - log2W),
+ *    sign = -1 if bit (63 - log2W) of v is set, else +1.  (a0, a1, a2, b) of
+ *    row r are splitmix64 outputs 4r .. 4r+3 of the generator seeded with
+ *    hash_seed.
+ *  - Sampling: particle number g of the stream (g counts every particle ever
+ *    passed to sketch_update on this handle, from 0) is kept iff rate >= 1 or
+ *    splitmix64 output number g of the generator seeded with sample_seed is
+ *    below floor(rate * 2^64).
+ *  - Estimate(key) = lower median over rows of sign_r(key) * C[r][bucket_r(key)]
+ *    (int32, two's-complement wrap-around; counters wrap the same way).
+ *  - Ranking: estimate descending, then key ascending.
+ */
+#ifndef HALOSKETCH_H
+#define HALOSKETCH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hs_sketch hs_sketch; /* opaque, owned by the library */
+
+typedef enum {
+    HS_OK = 0,
+    HS_ERR_ARG = 1,        /* invalid argument: null pointer, bad size or range   */
+    HS_ERR_CUDA = 2,       /* a CUDA runtime call or kernel launch failed          */
+    HS_ERR_OOM = 3,        /* device or host allocation failed                     */
+    HS_ERR_TABLE_FULL = 4, /* a bounded-probe hash table ran out of probes         */
+    HS_ERR_TIMEOUT = 5,    /* a bounded device-side wait gave up                   */
+    HS_ERR_STATE = 6       /* handle in a state that does not allow the call       */
+} hs_status;
+
+/* Sketch parameters.  rows in [1, 32]; log2_width in [1, 30]; box > 0 and
+ * cell > 0 with 1 <= round(box / cell) <= 2^21; flags must be 0. */
+typedef struct {
+    uint32_t rows;        /* t: number of independent rows (Sec. 2.2)         */
+    uint32_t log2_width;  /* b = W = 2^log2_width counters per row            */
+    double box;           /* side of the periodic simulation box              */
+    double cell;          /* mesh cell size (Sec. 2.1)                         */
+    uint64_t hash_seed;   /* seeds the row hash functions                     */
+    uint64_t sample_seed; /* seeds the sampling hash                          */
+    uint32_t flags;       /* reserved, must be 0                              */
+    uint32_t reserved;    /* must be 0                                        */
+} hs_params;
+
+/* Read-only description of a handle. */
+typedef struct {
+    uint32_t rows;
+    uint32_t log2_width;
+    uint32_t grid;        /* G                                               */
+    float inv_cell;
+    uint64_t width;       /* W                                               */
+    uint64_t n_cells;     /* G^3, the size of the dictionary                 */
+    uint64_t n_seen;      /* particles passed to sketch_update so far        */
+} hs_info;
+
+/* Counters kept by the library for benchmarking. */
+typedef struct {
+    uint64_t kernel_launches;   /* every kernel this handle launched          */
+    uint64_t update_launches;   /* launches of the update kernel              */
+    double update_ms;           /* summed device time of update launches       */
+    uint64_t search_launches;   /* launches of the full-search kernel          */
+    double search_ms;           /* summed device time of full-search launches  */
+    double topk_ms;             /* summed device time of whole top-k queries   */
+    uint64_t topk_calls;
+    uint64_t last_candidates;   /* candidates collected by the last query      */
+    int32_t last_threshold;     /* pruning threshold of the last query's pass  */
+    uint32_t last_passes;       /* full-search passes of the last query        */
+} hs_stats;
+
+/*
+ * Initialization (Algorithm 1): allocate a t x W matrix of int32 counters
+ * filled with zeros on the current CUDA device and bind the handle to
+ * `cuda_stream` (a cudaStream_t; NULL = legacy default stream).
+ * HS_ERR_ARG for invalid parameters or out == NULL; HS_ERR_OOM if device
+ * memory is short.  *out is set only on success.
+ */
+hs_status sketch_create(const hs_params *params, void *cuda_stream, hs_sketch **out);
+
+/*
+ * Processing the stream (Algorithm 1; per item: Add of Sec. 2.2 after the mesh
+ * reduction of Sec. 2.1 and the sampling of Sec. 3.1).  Adds n particles
+ * (xyz, 3n floats) with global indices n_seen .. n_seen + n - 1, then
+ * n_seen += n.  sample_rate in (0, 1]; rate 1 keeps every particle.
+ * Device xyz: asynchronous on the handle's stream; the buffer must stay valid
+ * until that work completes.  Host xyz: copied in chunks through the
+ * library's staging buffers; the call returns after the last copy is issued
+ * (pageable memory may be reused on return; pinned memory once the stream
+ * has drained).  n == 0 is a no-op.  HS_ERR_ARG for a null handle, a null
+ * xyz with n > 0, or a rate outside (0, 1].
+ */
+hs_status sketch_update(hs_sketch *h, const float *xyz, uint64_t n, double sample_rate);
+
+/*
+ * Estimate (Sec. 2.2) for m cell keys: est[i] = median over rows of
+ * sign_r(keys[i]) * C[r][bucket_r(keys[i])].  keys and est may each be host or
+ * device memory.  Synchronous: returns once est is written.  A key >= G^3
+ * gives HS_ERR_ARG (its est entry is 0; the others are still written).
+ */
+hs_status sketch_query(hs_sketch *h, const uint64_t *keys, uint64_t m, int32_t *est);
+
+/*
+ * Querying the data structure of Count Sketch with Full Search (Algorithm 1,
+ * the "GPU without heap" design of Sec. 3.1): estimate every cell of the
+ * dictionary [0, G^3) and return the min(k, G^3) best by (estimate desc,
+ * key asc).  keys (uint64) and est (int32) receive *n_out entries in rank
+ * order; they are HOST arrays of at least k entries.  Synchronous.  The result
+ * is exactly that of enumerating every cell (the search prunes only cells
+ * that provably cannot reach the k-th estimate).  HS_ERR_ARG for k == 0 or
+ * null pointers.
+ */
+hs_status topk_extract(hs_sketch *h, uint32_t k, uint64_t *keys, int32_t *est, uint32_t *n_out);
+
+/* Free the counters, scratch and staging buffers of h (NULL is a no-op). */
+hs_status sketch_destroy(hs_sketch *h);
+
+/* ---- extensions ---- */
+
+/* Zero the counters and n_seen (asynchronous on the handle's stream). */
+hs_status sketch_reset(hs_sketch *h);
+
+/* Copy the t x W counters (row-major, int32) to out (host or device); synchronous. */
+hs_status sketch_counters(hs_sketch *h, int32_t *out);
+
+/* Replace the counters with t x W int32 values from in (host or device); synchronous.
+ * n_seen is unchanged. */
+hs_status sketch_load_counters(hs_sketch *h, const int32_t *in);
+
+/* Sketches built with the same parameters sum to the sketch of the union of
+ * their streams (Sec. 5): dst.C += src.C element-wise (int32 wrap-around) and
+ * dst.n_seen += src.n_seen.  HS_ERR_ARG if the parameters differ.  Ordered on
+ * dst's stream after src's pending work. */
+hs_status sketch_merge(hs_sketch *dst, hs_sketch *src);
+
+/* Describe h. */
+hs_status sketch_info(const hs_sketch *h, hs_info *out);
+
+/* Block until the handle's stream has finished its work. */
+hs_status sketch_synchronize(hs_sketch *h);
+
+/* Read (and with reset != 0, clear) the handle's benchmarking counters;
+ * synchronises the handle's stream first. */
+hs_status sketch_stats(hs_sketch *h, hs_stats *out, int reset);
+
+/* Benchmark aid with no counterpart in the paper: the rate (operations per
+ * second) of random 32-bit atomic adds into a fresh device table of n_counters
+ * (a power of two) counters, total_ops adds in one launch.  This is the
+ * second roofline of the update (besides the particle stream's HBM bytes):
+ * t adds per kept particle resolve in L2.  Allocates and frees its table. */
+hs_status hs_measure_red_rate(uint64_t n_counters, uint64_t total_ops, double *ops_per_s);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char *hs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HALOSKETCH_H */

@@ -1,0 +1,633 @@
+// capi.cu - the library's C ABI (include/halosketch.h): handle lifetime, the
+// update path (device buffers directly, host buffers through double-buffered
+// staging), point queries and the exact full-search top-k.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/halosketch.h"
+#include "hs_device.cuh"
+#include "hs_kernels.h"
+
+using namespace hs;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+hs_status fail(hs_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+#define HS_CUDA(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(e_ == cudaErrorMemoryAllocation ? HS_ERR_OOM : HS_ERR_CUDA,        \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                         \
+    } while (0)
+
+constexpr uint64_t kProbeCap = 1ull << 20;        // keys of the first 2^20 particles
+constexpr uint32_t kProbeSlotsLog2 = 21;
+constexpr uint64_t kStageParticles = 1ull << 23;  // 96 MiB per staging buffer
+constexpr size_t kSearchSmemBudget = 192 * 1024;
+
+struct EventPair {
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct hs_sketch {
+    hs_params p;
+    SketchDesc d;
+    uint64_t n_cells = 0;
+    uint32_t key_bits = 0;
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    int32_t *C = nullptr;
+    uint64_t *probe = nullptr;
+    uint64_t n_seen = 0;
+
+    // staging for host particle buffers
+    float *stage[2] = {nullptr, nullptr};
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+    cudaEvent_t ev_free[2] = {nullptr, nullptr};
+
+    // top-k scratch
+    uint64_t cap = 0;               // candidate capacity
+    uint64_t *cand_key = nullptr;
+    int32_t *cand_est = nullptr;
+    unsigned long long *counters = nullptr;   // [0] candidates, [1] tmp, [2] distinct
+    uint32_t *flags = nullptr;                // [0] bad key, [1] probe overflow
+    uint32_t *bitmap = nullptr;
+    uint32_t nb = 0;
+    uint64_t *slots = nullptr;
+    uint64_t *distinct = nullptr;
+    int32_t *distinct_est = nullptr;
+    SelectState *sel = nullptr;
+    unsigned long long *hist = nullptr;
+    uint64_t *tmp_key = nullptr;
+    int32_t *tmp_est = nullptr;
+    uint64_t *out_key = nullptr;
+    int32_t *out_est = nullptr;
+    uint64_t out_cap = 0;
+    uint64_t *q_keys = nullptr;
+    int32_t *q_est = nullptr;
+    uint64_t q_cap = 0;
+
+    // benchmarking
+    hs_stats stats;
+    std::vector<EventPair> pending_update, pending_search, pool;
+};
+
+namespace {
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+hs_status check_params(const hs_params *p) {
+    if (!p) return fail(HS_ERR_ARG, "params is NULL");
+    if (p->rows < 1 || p->rows > (uint32_t)kMaxRows)
+        return fail(HS_ERR_ARG, "rows=%u outside [1, %d]", p->rows, kMaxRows);
+    if (p->log2_width < 1 || p->log2_width > 30)
+        return fail(HS_ERR_ARG, "log2_width=%u outside [1, 30]", p->log2_width);
+    if (!(p->box > 0) || !(p->cell > 0) || !std::isfinite(p->box) || !std::isfinite(p->cell))
+        return fail(HS_ERR_ARG, "box and cell must be positive and finite");
+    double g = std::llround(p->box / p->cell);
+    if (g < 1 || g > (double)(1u << 21))
+        return fail(HS_ERR_ARG, "grid round(box/cell)=%.0f outside [1, 2^21]", g);
+    if (p->flags != 0 || p->reserved != 0) return fail(HS_ERR_ARG, "flags/reserved must be 0");
+    return HS_OK;
+}
+
+EventPair take_events(hs_sketch *h) {
+    if (!h->pool.empty()) {
+        EventPair e = h->pool.back();
+        h->pool.pop_back();
+        return e;
+    }
+    EventPair e{nullptr, nullptr};
+    cudaEventCreate(&e.a);
+    cudaEventCreate(&e.b);
+    return e;
+}
+
+// fold finished event pairs into the stats (caller has synchronised)
+void drain_timings(hs_sketch *h) {
+    for (auto &e : h->pending_update) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) h->stats.update_ms += ms;
+        h->pool.push_back(e);
+    }
+    h->pending_update.clear();
+    for (auto &e : h->pending_search) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) h->stats.search_ms += ms;
+        h->pool.push_back(e);
+    }
+    h->pending_search.clear();
+    cudaGetLastError();
+}
+
+void free_topk_scratch(hs_sketch *h) {
+    void *ps[] = {h->cand_key, h->cand_est, h->counters, h->bitmap,  h->slots,
+                  h->distinct, h->distinct_est, h->sel, h->hist,  h->tmp_key, h->tmp_est,
+                  h->out_key, h->out_est};
+    for (void *p : ps)
+        if (p) cudaFree(p);
+    h->cand_key = nullptr;
+    h->cand_est = nullptr;
+    h->counters = nullptr;
+    h->bitmap = nullptr;
+    h->slots = nullptr;
+    h->distinct = nullptr;
+    h->distinct_est = nullptr;
+    h->sel = nullptr;
+    h->hist = nullptr;
+    h->tmp_key = nullptr;
+    h->tmp_est = nullptr;
+    h->out_key = nullptr;
+    h->out_est = nullptr;
+    h->cap = 0;
+    h->out_cap = 0;
+}
+
+hs_status ensure_topk_scratch(hs_sketch *h, uint64_t k) {
+    uint64_t want_cap = std::max<uint64_t>(1ull << 22, 8 * k);
+    if (h->cand_key && h->cap >= want_cap && h->out_cap >= k) return HS_OK;
+    free_topk_scratch(h);
+    h->cap = want_cap;
+    h->out_cap = std::max<uint64_t>(k, 1);
+    h->nb = bitmap_log2_bits(h->d.rows, h->d.log2w, kSearchSmemBudget);
+    uint64_t words = (uint64_t)h->d.rows * std::max<uint64_t>((1ull << h->nb) >> 5, 1);
+    HS_CUDA(cudaMalloc(&h->cand_key, h->cap * 8));
+    HS_CUDA(cudaMalloc(&h->cand_est, h->cap * 4));
+    HS_CUDA(cudaMalloc(&h->counters, 4 * sizeof(unsigned long long)));
+    HS_CUDA(cudaMalloc(&h->bitmap, words * 4));
+    HS_CUDA(cudaMalloc(&h->slots, (size_t)8 << kProbeSlotsLog2));
+    HS_CUDA(cudaMalloc(&h->distinct, kProbeCap * 8));
+    HS_CUDA(cudaMalloc(&h->distinct_est, kProbeCap * 4));
+    HS_CUDA(cudaMalloc(&h->sel, sizeof(SelectState)));
+    HS_CUDA(cudaMalloc(&h->hist, 256 * sizeof(unsigned long long)));
+    HS_CUDA(cudaMalloc(&h->tmp_key, h->out_cap * 8));
+    HS_CUDA(cudaMalloc(&h->tmp_est, h->out_cap * 4));
+    HS_CUDA(cudaMalloc(&h->out_key, h->out_cap * 8));
+    HS_CUDA(cudaMalloc(&h->out_est, h->out_cap * 4));
+    return HS_OK;
+}
+
+hs_status ensure_staging(hs_sketch *h) {
+    if (h->stage[0]) return HS_OK;
+    for (int i = 0; i < 2; ++i) {
+        HS_CUDA(cudaMalloc(&h->stage[i], kStageParticles * 12));
+        HS_CUDA(cudaEventCreateWithFlags(&h->ev_copied[i], cudaEventDisableTiming));
+        HS_CUDA(cudaEventCreateWithFlags(&h->ev_free[i], cudaEventDisableTiming));
+    }
+    HS_CUDA(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    return HS_OK;
+}
+
+hs_status ensure_query_scratch(hs_sketch *h, uint64_t m) {
+    if (h->q_cap >= m) return HS_OK;
+    if (h->q_keys) cudaFree(h->q_keys);
+    if (h->q_est) cudaFree(h->q_est);
+    h->q_keys = nullptr;
+    h->q_est = nullptr;
+    h->q_cap = 0;
+    uint64_t c = std::max<uint64_t>(m, 1 << 16);
+    HS_CUDA(cudaMalloc(&h->q_keys, c * 8));
+    HS_CUDA(cudaMalloc(&h->q_est, c * 4));
+    h->q_cap = c;
+    return HS_OK;
+}
+
+hs_status launch_update_timed(hs_sketch *h, const float *xyz, uint64_t n, uint64_t g0,
+                              double rate) {
+    EventPair ev = take_events(h);
+    cudaEventRecord(ev.a, h->stream);
+    HS_CUDA(launch_update(xyz, n, g0, h->d, h->C, rate, h->p.sample_seed, h->probe, kProbeCap, 0,
+                          (uint32_t)h->d.W, h->num_sms * 8, h->stream));
+    cudaEventRecord(ev.b, h->stream);
+    h->pending_update.push_back(ev);
+    h->stats.update_launches += 1;
+    h->stats.kernel_launches += 1;
+    return HS_OK;
+}
+
+// One full-search pass over lines [line_lo, line_hi); appends after *count_base.
+// Returns the new candidate count (possibly above cap).
+hs_status search_pass(hs_sketch *h, int32_t theta, SearchMode mode, uint64_t line_lo,
+                      uint64_t line_hi, unsigned long long count_base,
+                      unsigned long long *count_out) {
+    int64_t hot = (int64_t)theta + (mode == kGT ? 1 : 0);
+    int prune = hot >= 1;
+    if (prune) {
+        HS_CUDA(launch_hot_bitmap(h->C, h->d, h->nb, (int32_t)std::min<int64_t>(hot, INT32_MAX),
+                                  h->bitmap, h->num_sms * 8, h->stream));
+        h->stats.kernel_launches += 1;
+    }
+    HS_CUDA(cudaMemcpyAsync(&h->counters[0], &count_base, sizeof(count_base),
+                            cudaMemcpyHostToDevice, h->stream));
+    SearchOut out{h->cand_key, h->cand_est, &h->counters[0], h->cap};
+    if (mode == kGT && theta == INT32_MAX) {
+        line_hi = line_lo;   // nothing is above the largest int32
+    }
+    EventPair ev = take_events(h);
+    cudaEventRecord(ev.a, h->stream);
+    HS_CUDA(launch_full_search(h->C, h->d, theta, mode, h->bitmap, h->nb, prune, line_lo, line_hi,
+                               out, h->num_sms, h->stream));
+    cudaEventRecord(ev.b, h->stream);
+    h->pending_search.push_back(ev);
+    h->stats.search_launches += 1;
+    h->stats.kernel_launches += 1;
+    h->stats.last_passes += 1;
+    h->stats.last_threshold = theta;
+    unsigned long long c = 0;
+    HS_CUDA(cudaMemcpyAsync(&c, &h->counters[0], sizeof(c), cudaMemcpyDeviceToHost, h->stream));
+    HS_CUDA(cudaStreamSynchronize(h->stream));
+    *count_out = c;
+    return HS_OK;
+}
+
+// estimate of the k-th best entry of (key, est)[0..m)
+hs_status kth_estimate(hs_sketch *h, const uint64_t *key, const int32_t *est, uint64_t m,
+                       uint64_t k, int32_t *theta) {
+    int launches = 0;
+    HS_CUDA(launch_select_kth(key, est, m, k, h->key_bits, h->sel, h->hist, h->num_sms * 4,
+                              h->stream, &launches));
+    h->stats.kernel_launches += launches;
+    SelectState st;
+    HS_CUDA(cudaMemcpyAsync(&st, h->sel, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+    HS_CUDA(cudaStreamSynchronize(h->stream));
+    *theta = (int32_t)(st.hi ^ 0x80000000u);
+    return HS_OK;
+}
+
+// the k best of the m >= k candidates, in rank order, into h->out_*
+hs_status finalize(hs_sketch *h, uint64_t m, uint64_t k) {
+    int launches = 0;
+    int all = m <= k;
+    if (!all)
+        HS_CUDA(launch_select_kth(h->cand_key, h->cand_est, m, k, h->key_bits, h->sel, h->hist,
+                                  h->num_sms * 4, h->stream, &launches));
+    uint64_t n_take = all ? m : k;
+    HS_CUDA(launch_take_sorted(h->cand_key, h->cand_est, m, h->sel, all, h->tmp_key, h->tmp_est,
+                               &h->counters[1], n_take, h->out_key, h->out_est, h->num_sms * 4,
+                               h->stream, &launches));
+    h->stats.kernel_launches += launches;
+    return HS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *hs_last_error(void) { return g_last_error.c_str(); }
+
+hs_status sketch_create(const hs_params *params, void *cuda_stream, hs_sketch **out) {
+    if (!out) return fail(HS_ERR_ARG, "out is NULL");
+    hs_status st = check_params(params);
+    if (st != HS_OK) return st;
+    hs_sketch *h = new (std::nothrow) hs_sketch();
+    if (!h) return fail(HS_ERR_OOM, "host allocation failed");
+    h->p = *params;
+    h->stream = (cudaStream_t)cuda_stream;
+    std::memset(&h->stats, 0, sizeof(h->stats));
+    SketchDesc &d = h->d;
+    std::memset(&d, 0, sizeof(d));
+    d.rows = params->rows;
+    d.log2w = params->log2_width;
+    d.G = (uint32_t)std::llround(params->box / params->cell);
+    d.inv_cell = (float)(1.0 / params->cell);
+    d.W = 1ull << params->log2_width;
+    for (uint32_t r = 0; r < d.rows; ++r) {   // splitmix64 outputs 4r .. 4r+3
+        d.seed[r].a0 = splitmix64_at(params->hash_seed, 4 * r + 0);
+        d.seed[r].a1 = splitmix64_at(params->hash_seed, 4 * r + 1);
+        d.seed[r].a2 = splitmix64_at(params->hash_seed, 4 * r + 2);
+        d.seed[r].b = splitmix64_at(params->hash_seed, 4 * r + 3);
+    }
+    h->n_cells = (uint64_t)d.G * d.G * d.G;
+    h->key_bits = 1;
+    while (h->key_bits < 64 && (1ull << h->key_bits) < h->n_cells) ++h->key_bits;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) e = cudaMalloc(&h->C, (size_t)d.rows * d.W * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&h->probe, kProbeCap * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&h->flags, 4 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->C, 0, (size_t)d.rows * d.W * 4, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->probe, 0xFF, kProbeCap * 8, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        hs_status code = e == cudaErrorMemoryAllocation ? HS_ERR_OOM : HS_ERR_CUDA;
+        sketch_destroy(h);
+        return fail(code, "sketch_create: %s", cudaGetErrorString(e));
+    }
+    *out = h;
+    return HS_OK;
+}
+
+hs_status sketch_destroy(hs_sketch *h) {
+    if (!h) return HS_OK;
+    cudaStreamSynchronize(h->stream);
+    free_topk_scratch(h);
+    if (h->C) cudaFree(h->C);
+    if (h->probe) cudaFree(h->probe);
+    if (h->q_keys) cudaFree(h->q_keys);
+    if (h->q_est) cudaFree(h->q_est);
+    if (h->flags) cudaFree(h->flags);
+    for (int i = 0; i < 2; ++i) {
+        if (h->stage[i]) cudaFree(h->stage[i]);
+        if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
+        if (h->ev_free[i]) cudaEventDestroy(h->ev_free[i]);
+    }
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    for (auto *v : {&h->pending_update, &h->pending_search, &h->pool})
+        for (auto &e : *v) {
+            cudaEventDestroy(e.a);
+            cudaEventDestroy(e.b);
+        }
+    delete h;
+    cudaGetLastError();
+    return HS_OK;
+}
+
+hs_status sketch_update(hs_sketch *h, const float *xyz, uint64_t n, double sample_rate) {
+    if (!h) return fail(HS_ERR_ARG, "handle is NULL");
+    if (!(sample_rate > 0.0 && sample_rate <= 1.0))
+        return fail(HS_ERR_ARG, "sample_rate=%g outside (0, 1]", sample_rate);
+    if (n == 0) return HS_OK;
+    if (!xyz) return fail(HS_ERR_ARG, "xyz is NULL");
+    if (n > (~0ull - h->n_seen)) return fail(HS_ERR_ARG, "particle index overflow");
+    if (is_device_ptr(xyz)) {
+        hs_status st = launch_update_timed(h, xyz, n, h->n_seen, sample_rate);
+        if (st != HS_OK) return st;
+    } else {
+        hs_status st = ensure_staging(h);
+        if (st != HS_OK) return st;
+        int i = 0;
+        for (uint64_t off = 0; off < n; off += kStageParticles, ++i) {
+            uint64_t cnt = std::min(kStageParticles, n - off);
+            int b = i & 1;
+            HS_CUDA(cudaStreamWaitEvent(h->copy_stream, h->ev_free[b], 0));
+            HS_CUDA(cudaMemcpyAsync(h->stage[b], xyz + 3 * off, cnt * 12, cudaMemcpyHostToDevice,
+                                    h->copy_stream));
+            HS_CUDA(cudaEventRecord(h->ev_copied[b], h->copy_stream));
+            HS_CUDA(cudaStreamWaitEvent(h->stream, h->ev_copied[b], 0));
+            st = launch_update_timed(h, h->stage[b], cnt, h->n_seen + off, sample_rate);
+            if (st != HS_OK) return st;
+            HS_CUDA(cudaEventRecord(h->ev_free[b], h->stream));
+        }
+    }
+    h->n_seen += n;
+    return HS_OK;
+}
+
+hs_status sketch_query(hs_sketch *h, const uint64_t *keys, uint64_t m, int32_t *est) {
+    if (!h) return fail(HS_ERR_ARG, "handle is NULL");
+    if (m == 0) return HS_OK;
+    if (!keys || !est) return fail(HS_ERR_ARG, "keys/est is NULL");
+    bool kd = is_device_ptr(keys), ed = is_device_ptr(est);
+    hs_status st = ensure_query_scratch(h, (kd && ed) ? 0 : m);
+    if (st != HS_OK) return st;
+    const uint64_t *dk = keys;
+    int32_t *de = est;
+    if (!kd) {
+        HS_CUDA(cudaMemcpyAsync(h->q_keys, keys, m * 8, cudaMemcpyHostToDevice, h->stream));
+        dk = h->q_keys;
+    }
+    if (!ed) de = h->q_est;
+    HS_CUDA(cudaMemsetAsync(h->flags, 0, 4 * sizeof(uint32_t), h->stream));
+    HS_CUDA(launch_point_query(h->C, h->d, dk, m, de, &h->flags[0], h->stream));
+    h->stats.kernel_launches += 1;
+    if (!ed) HS_CUDA(cudaMemcpyAsync(est, de, m * 4, cudaMemcpyDeviceToHost, h->stream));
+    uint32_t bad = 0;
+    HS_CUDA(cudaMemcpyAsync(&bad, &h->flags[0], 4, cudaMemcpyDeviceToHost, h->stream));
+    HS_CUDA(cudaStreamSynchronize(h->stream));
+    if (bad) return fail(HS_ERR_ARG, "a key is >= G^3 = %llu", (unsigned long long)h->n_cells);
+    return HS_OK;
+}
+
+hs_status topk_extract(hs_sketch *h, uint32_t k, uint64_t *keys, int32_t *est, uint32_t *n_out) {
+    if (!h) return fail(HS_ERR_ARG, "handle is NULL");
+    if (k == 0 || !keys || !est || !n_out) return fail(HS_ERR_ARG, "k == 0 or NULL output");
+    const uint64_t kk = std::min<uint64_t>(k, h->n_cells);
+    hs_status st = ensure_topk_scratch(h, kk);
+    if (st != HS_OK) return st;
+    h->stats.last_passes = 0;
+    EventPair whole = take_events(h);
+    cudaEventRecord(whole.a, h->stream);
+    const uint64_t lines = (uint64_t)h->d.G * h->d.G;
+
+    // 1. a lower bound on the k-th estimate: the k-th best estimate among the
+    //    distinct cells of the first particles of the stream
+    int32_t theta = INT32_MIN;
+    uint64_t m_probe = std::min<uint64_t>(h->n_seen, kProbeCap);
+    if (m_probe >= kk) {
+        HS_CUDA(cudaMemsetAsync(h->counters, 0, 4 * sizeof(unsigned long long), h->stream));
+        HS_CUDA(cudaMemsetAsync(h->flags, 0, 4 * sizeof(uint32_t), h->stream));
+        HS_CUDA(launch_probe_distinct(h->probe, m_probe, h->slots, kProbeSlotsLog2, h->distinct,
+                                      &h->counters[2], &h->flags[1], h->stream));
+        unsigned long long nd = 0;
+        HS_CUDA(cudaMemcpyAsync(&nd, &h->counters[2], 8, cudaMemcpyDeviceToHost, h->stream));
+        HS_CUDA(cudaStreamSynchronize(h->stream));
+        h->stats.kernel_launches += 1;
+        if (nd >= kk) {
+            HS_CUDA(launch_point_query(h->C, h->d, h->distinct, nd, h->distinct_est, &h->flags[0],
+                                       h->stream));
+            h->stats.kernel_launches += 1;
+            st = kth_estimate(h, h->distinct, h->distinct_est, nd, kk, &theta);
+            if (st != HS_OK) return st;
+        }
+    }
+
+    // 2. full search with that threshold; raise it on overflow
+    uint64_t final_m = 0;
+    for (int round = 0;; ++round) {
+        if (round > 64) return fail(HS_ERR_STATE, "top-k threshold did not converge");
+        unsigned long long c = 0;
+        st = search_pass(h, theta, kGE, 0, lines, 0, &c);
+        if (st != HS_OK) return st;
+        h->stats.last_candidates = c;
+        if (c <= h->cap) {
+            if (c >= kk) {
+                final_m = c;
+                break;
+            }
+            if (theta == INT32_MIN) return fail(HS_ERR_STATE, "fewer cells than k");
+            theta = INT32_MIN;   // cannot happen for a valid lower bound; start over
+            continue;
+        }
+        int32_t t2 = 0;
+        st = kth_estimate(h, h->cand_key, h->cand_est, h->cap, kk, &t2);
+        if (st != HS_OK) return st;
+        if (t2 > theta) {
+            theta = t2;
+            continue;
+        }
+        // many cells tie at theta: take every cell above it, then the ties in key order
+        unsigned long long c_gt = 0;
+        st = search_pass(h, theta, kGT, 0, lines, 0, &c_gt);
+        if (st != HS_OK) return st;
+        if (c_gt > h->cap) {
+            st = kth_estimate(h, h->cand_key, h->cand_est, h->cap, kk, &t2);
+            if (st != HS_OK) return st;
+            theta = t2;
+            continue;
+        }
+        if (c_gt >= kk) {
+            final_m = c_gt;
+            break;
+        }
+        uint64_t need = kk - c_gt, have = 0, line = 0;
+        while (have < need && line < lines) {
+            uint64_t room = h->cap - c_gt - have;
+            uint64_t seg = std::max<uint64_t>(1, room / h->d.G);
+            uint64_t hi = std::min(lines, line + seg);
+            unsigned long long c2 = 0;
+            st = search_pass(h, theta, kEQ, line, hi, c_gt + have, &c2);
+            if (st != HS_OK) return st;
+            have = c2 - c_gt;
+            line = hi;
+        }
+        final_m = c_gt + have;
+        h->stats.last_candidates = final_m;
+        break;
+    }
+    st = finalize(h, final_m, kk);
+    if (st != HS_OK) return st;
+    uint64_t n = std::min<uint64_t>(final_m, kk);
+    HS_CUDA(cudaMemcpyAsync(keys, h->out_key, n * 8, cudaMemcpyDeviceToHost, h->stream));
+    HS_CUDA(cudaMemcpyAsync(est, h->out_est, n * 4, cudaMemcpyDeviceToHost, h->stream));
+    cudaEventRecord(whole.b, h->stream);
+    HS_CUDA(cudaStreamSynchronize(h->stream));
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, whole.a, whole.b) == cudaSuccess) h->stats.topk_ms += ms;
+    h->pool.push_back(whole);
+    h->stats.topk_calls += 1;
+    drain_timings(h);
+    *n_out = (uint32_t)n;
+    return HS_OK;
+}
+
+hs_status sketch_reset(hs_sketch *h) {
+    if (!h) return fail(HS_ERR_ARG, "handle is NULL");
+    HS_CUDA(cudaMemsetAsync(h->C, 0, (size_t)h->d.rows * h->d.W * 4, h->stream));
+    HS_CUDA(cudaMemsetAsync(h->probe, 0xFF, kProbeCap * 8, h->stream));
+    h->n_seen = 0;
+    return HS_OK;
+}
+
+hs_status sketch_counters(hs_sketch *h, int32_t *out) {
+    if (!h || !out) return fail(HS_ERR_ARG, "NULL argument");
+    HS_CUDA(cudaMemcpyAsync(out, h->C, (size_t)h->d.rows * h->d.W * 4, cudaMemcpyDefault,
+                            h->stream));
+    HS_CUDA(cudaStreamSynchronize(h->stream));
+    return HS_OK;
+}
+
+hs_status sketch_load_counters(hs_sketch *h, const int32_t *in) {
+    if (!h || !in) return fail(HS_ERR_ARG, "NULL argument");
+    HS_CUDA(cudaMemcpyAsync(h->C, in, (size_t)h->d.rows * h->d.W * 4, cudaMemcpyDefault,
+                            h->stream));
+    HS_CUDA(cudaStreamSynchronize(h->stream));
+    return HS_OK;
+}
+
+hs_status sketch_merge(hs_sketch *dst, hs_sketch *src) {
+    if (!dst || !src) return fail(HS_ERR_ARG, "NULL handle");
+    const hs_params &a = dst->p, &b = src->p;
+    if (a.rows != b.rows || a.log2_width != b.log2_width || a.hash_seed != b.hash_seed ||
+        dst->d.G != src->d.G || dst->d.inv_cell != src->d.inv_cell)
+        return fail(HS_ERR_ARG, "sketches were built with different parameters");
+    if (dst == src) return fail(HS_ERR_ARG, "cannot merge a sketch into itself");
+    cudaEvent_t ev;
+    HS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    HS_CUDA(cudaEventRecord(ev, src->stream));
+    HS_CUDA(cudaStreamWaitEvent(dst->stream, ev, 0));
+    cudaEventDestroy(ev);
+    HS_CUDA(launch_add_counters(dst->C, src->C, (uint64_t)a.rows << a.log2_width, dst->stream));
+    dst->stats.kernel_launches += 1;
+    dst->n_seen += src->n_seen;
+    return HS_OK;
+}
+
+hs_status sketch_info(const hs_sketch *h, hs_info *out) {
+    if (!h || !out) return fail(HS_ERR_ARG, "NULL argument");
+    out->rows = h->d.rows;
+    out->log2_width = h->d.log2w;
+    out->grid = h->d.G;
+    out->inv_cell = h->d.inv_cell;
+    out->width = h->d.W;
+    out->n_cells = h->n_cells;
+    out->n_seen = h->n_seen;
+    return HS_OK;
+}
+
+hs_status sketch_synchronize(hs_sketch *h) {
+    if (!h) return fail(HS_ERR_ARG, "handle is NULL");
+    HS_CUDA(cudaStreamSynchronize(h->stream));
+    return HS_OK;
+}
+
+hs_status sketch_stats(hs_sketch *h, hs_stats *out, int reset) {
+    if (!h || !out) return fail(HS_ERR_ARG, "NULL argument");
+    HS_CUDA(cudaStreamSynchronize(h->stream));
+    drain_timings(h);
+    *out = h->stats;
+    if (reset) std::memset(&h->stats, 0, sizeof(h->stats));
+    return HS_OK;
+}
+
+hs_status hs_measure_red_rate(uint64_t n_counters, uint64_t total_ops, double *ops_per_s) {
+    if (!ops_per_s || n_counters == 0 || (n_counters & (n_counters - 1)) || total_ops == 0)
+        return fail(HS_ERR_ARG, "n_counters must be a power of two and total_ops > 0");
+    int dev = 0, sms = 0;
+    HS_CUDA(cudaGetDevice(&dev));
+    HS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    uint32_t *t = nullptr;
+    HS_CUDA(cudaMalloc(&t, n_counters * 4));
+    cudaStream_t s;
+    cudaEvent_t a, b;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    int blocks = sms * 8;
+    uint64_t per = std::max<uint64_t>(1, total_ops / ((uint64_t)blocks * 256));
+    cudaMemsetAsync(t, 0, n_counters * 4, s);
+    launch_red_rate(t, n_counters, per, blocks, s);   // warm the table into L2
+    cudaEventRecord(a, s);
+    cudaError_t e = launch_red_rate(t, n_counters, per, blocks, s);
+    cudaEventRecord(b, s);
+    cudaStreamSynchronize(s);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaStreamDestroy(s);
+    cudaFree(t);
+    if (e != cudaSuccess) return fail(HS_ERR_CUDA, "red-rate kernel: %s", cudaGetErrorString(e));
+    *ops_per_s = (double)per * blocks * 256 / (ms * 1e-3);
+    return HS_OK;
+}
+
+}  // extern "C"

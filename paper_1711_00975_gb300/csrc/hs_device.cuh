@@ -1,0 +1,138 @@
+// hs_device.cuh - device-side building blocks of the Count Sketch path.
+//
+// Mesh reduction (arXiv:1711.00975 Sec. 2.1), index-hash sampling (Sec. 3.1)
+// and the per-row bucket/sign hash of the Count Sketch (Sec. 2.2), written for
+// sm_103a.  The quantisation multiply uses __fmul_rn so it is one IEEE-754
+// float32 rounding and can never be contracted into an FMA.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hs {
+
+constexpr int kMaxRows = 32;
+constexpr uint64_t kInvalidKey = 0xFFFFFFFFFFFFFFFFull;
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;   // splitmix64 increment
+
+struct RowSeed {
+    uint64_t a0, a1, a2, b;
+};
+
+// Everything a kernel needs to hash and quantise; passed by value.
+struct SketchDesc {
+    uint32_t rows;
+    uint32_t log2w;
+    uint32_t G;
+    float inv_cell;
+    uint64_t W;
+    RowSeed seed[kMaxRows];
+};
+
+// splitmix64 output number g of the generator seeded with `seed`
+// (Steele, Lea & Flood 2014: state advances by the golden gamma, output mixes it).
+__host__ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t g) {
+    uint64_t z = seed + (g + 1) * kGamma;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Low 64 bits of a * x for a 64-bit a and 32-bit x: one wide and one narrow
+// integer multiply-add instead of a full 64x64 product.
+__device__ __forceinline__ uint64_t mul_lo64(uint64_t a, uint32_t x) {
+    uint64_t lo = (uint64_t)(uint32_t)a * (uint64_t)x;
+    uint32_t hi = (uint32_t)(a >> 32) * x;
+    return lo + ((uint64_t)hi << 32);
+}
+
+// v = (a0*cx + a1*cy + a2*cz + b) mod 2^64 (vector multiply-shift before the shift)
+__device__ __forceinline__ uint64_t row_value(const RowSeed &s, uint32_t cx, uint32_t cy,
+                                              uint32_t cz) {
+    return s.b + mul_lo64(s.a0, cx) + mul_lo64(s.a1, cy) + mul_lo64(s.a2, cz);
+}
+
+__device__ __forceinline__ uint32_t bucket_of(uint64_t v, uint32_t log2w) {
+    return (uint32_t)(v >> (64 - log2w));
+}
+
+// +1 or -1 as an unsigned addend (wrap-around arithmetic)
+__device__ __forceinline__ uint32_t sign_of(uint64_t v, uint32_t log2w) {
+    return ((v >> (63 - log2w)) & 1ull) ? 0xFFFFFFFFu : 1u;
+}
+
+// sign * counter with int32 wrap-around
+__device__ __forceinline__ int32_t signed_count(int32_t c, uint64_t v, uint32_t log2w) {
+    uint32_t u = (uint32_t)c;
+    return ((v >> (63 - log2w)) & 1ull) ? (int32_t)(0u - u) : (int32_t)u;
+}
+
+// One axis of the mesh reduction: floor(fl32(x * inv)) reduced into [0, G).
+// Returns false when the scaled coordinate is not a finite value in [-2^31, 2^31).
+__device__ __forceinline__ bool axis_cell(float x, float inv, uint32_t G, uint32_t &c) {
+    float p = __fmul_rn(x, inv);
+    float f = floorf(p);
+    if (!(f >= -2147483648.0f && f < 2147483648.0f)) return false;
+    int i = (int)f;
+    if ((unsigned)i < G) {
+        c = (uint32_t)i;
+        return true;
+    }
+    int m = i % (int)G;
+    if (m < 0) m += (int)G;
+    c = (uint32_t)m;
+    return true;
+}
+
+__device__ __forceinline__ uint64_t key_of(uint32_t cx, uint32_t cy, uint32_t cz, uint32_t G) {
+    return (uint64_t)cx + (uint64_t)G * ((uint64_t)cy + (uint64_t)G * (uint64_t)cz);
+}
+
+// Lower median of n values in registers (n <= kMaxRows), insertion sort.
+template <int N>
+__device__ __forceinline__ int32_t lower_median_fixed(int32_t (&v)[N]) {
+#pragma unroll
+    for (int i = 1; i < N; ++i) {
+#pragma unroll
+        for (int j = i; j > 0; --j) {
+            int32_t a = v[j - 1], b = v[j];
+            v[j - 1] = min(a, b);
+            v[j] = max(a, b);
+        }
+    }
+    return v[(N - 1) / 2];
+}
+
+__device__ __forceinline__ int32_t lower_median_dyn(int32_t *v, int n) {
+    for (int i = 1; i < n; ++i) {
+        int32_t x = v[i];
+        int j = i;
+        while (j > 0 && v[j - 1] > x) {
+            v[j] = v[j - 1];
+            --j;
+        }
+        v[j] = x;
+    }
+    return v[(n - 1) / 2];
+}
+
+// Median of five with six comparisons: sort two pairs; the smaller of the two
+// pair minima has three values at or above it, so it cannot be the median and
+// is replaced by the fifth value; the median is then the second smallest of the
+// four that remain.
+__host__ __device__ __forceinline__ int32_t median5(int32_t a, int32_t b, int32_t c, int32_t d,
+                                                    int32_t e) {
+    int32_t t;
+    if (a > b) { t = a; a = b; b = t; }
+    if (c > d) { t = c; c = d; d = t; }
+    if (a < c) {
+        a = e;
+        if (a > b) { t = a; a = b; b = t; }
+    } else {
+        c = e;
+        if (c > d) { t = c; c = d; d = t; }
+    }
+    return (a < c) ? (b < c ? b : c) : (a < d ? a : d);
+}
+
+}  // namespace hs

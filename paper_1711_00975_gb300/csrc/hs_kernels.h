@@ -1,0 +1,74 @@
+// hs_kernels.h - host-side launchers of the library's kernels (internal).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hs_device.cuh"
+
+namespace hs {
+
+// ---- update mode (k_update.cu) ----
+cudaError_t launch_update(const float *xyz, uint64_t n, uint64_t g0, const SketchDesc &d,
+                          int32_t *C, double rate, uint64_t sample_seed, uint64_t *probe,
+                          uint64_t probe_cap, uint32_t band_lo, uint32_t band_hi, int max_blocks,
+                          cudaStream_t s);
+// dst[i] += src[i] (int32 wrap-around), the merge of two sketches
+cudaError_t launch_add_counters(int32_t *dst, const int32_t *src, uint64_t n, cudaStream_t s);
+cudaError_t launch_red_rate(uint32_t *table, uint64_t n_counters, uint64_t ops_per_thread,
+                            int blocks, cudaStream_t s);
+
+// ---- estimate mode (k_search.cu) ----
+enum SearchMode : uint32_t { kGE = 0, kGT = 1, kEQ = 2 };
+
+struct SearchOut {
+    uint64_t *key;
+    int32_t *est;
+    unsigned long long *count;   // entries appended (may exceed cap)
+    uint64_t cap;
+};
+
+// bits per row of the hot-bucket bitmap that fits the shared-memory budget
+uint32_t bitmap_log2_bits(uint32_t rows, uint32_t log2w, size_t smem_budget_bytes);
+// bitmap[r][sb] = 1 iff some counter of super-bucket sb in row r has |C| >= theta_hot
+cudaError_t launch_hot_bitmap(const int32_t *C, const SketchDesc &d, uint32_t nb,
+                              int32_t theta_hot, uint32_t *bitmap, int max_blocks, cudaStream_t s);
+// estimate every cell of lines [line_lo, line_hi) (line = cy + G*cz) and append
+// the cells whose estimate passes (mode, theta)
+cudaError_t launch_full_search(const int32_t *C, const SketchDesc &d, int32_t theta,
+                               SearchMode mode, const uint32_t *bitmap, uint32_t nb, int prune,
+                               uint64_t line_lo, uint64_t line_hi, SearchOut out, int blocks,
+                               cudaStream_t s);
+// est[i] = Estimate(keys[i]); keys >= G^3 give 0 and set *bad
+cudaError_t launch_point_query(const int32_t *C, const SketchDesc &d, const uint64_t *keys,
+                               uint64_t m, int32_t *est, uint32_t *bad, cudaStream_t s);
+// distinct valid keys of probe[0..m) via an open-addressing set of 2^log2_slots slots
+cudaError_t launch_probe_distinct(const uint64_t *probe, uint64_t m, uint64_t *slots,
+                                  uint32_t log2_slots, uint64_t *distinct,
+                                  unsigned long long *n_distinct, uint32_t *overflow,
+                                  cudaStream_t s);
+
+// ---- ranking (k_select.cu) ----
+struct SelectState {
+    uint32_t hi;        // decided digits of the estimate part
+    uint32_t pad;
+    uint64_t lo;        // decided digits of the key part
+    uint64_t k_rem;     // rank (1-based) still to find among matching entries
+};
+
+// Find the k-th best (estimate desc, key asc) entry of (key, est)[0..m) by a
+// most-significant-digit radix select; leaves the threshold in *state.
+// key_bits: keys are < 2^key_bits.  hist: 256 uint64 of scratch.
+cudaError_t launch_select_kth(const uint64_t *key, const int32_t *est, uint64_t m, uint64_t k,
+                              uint32_t key_bits, SelectState *state, unsigned long long *hist,
+                              int blocks, cudaStream_t s, int *launches);
+// Entries ranked at or above the threshold, written in rank order to
+// out_key/out_est (exactly min(k, m) of them when the threshold came from
+// launch_select_kth with the same k).  tmp_* hold min(k, m) entries of scratch.
+cudaError_t launch_take_sorted(const uint64_t *key, const int32_t *est, uint64_t m,
+                               const SelectState *state, int all, uint64_t *tmp_key,
+                               int32_t *tmp_est, unsigned long long *tmp_count,
+                               uint64_t n_take, uint64_t *out_key, int32_t *out_est,
+                               int blocks, cudaStream_t s, int *launches);
+
+}  // namespace hs

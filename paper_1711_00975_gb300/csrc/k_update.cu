@@ -1,0 +1,159 @@
+// k_update.cu - the stream-processing kernel (update mode of Count Sketch with
+// Full Search, arXiv:1711.00975 Algorithm 1 / Sec. 3.1 "GPU without heap").
+//
+// Per particle: mesh reduction to a cell (Sec. 2.1), Bernoulli sampling by the
+// particle's global index (Sec. 3.1), then Add (Sec. 2.2): for each row r,
+// C[r][bucket_r] += sign_r.  The paper's GPU design gives one block per stream
+// item and one thread per row (Algorithm 4, Update); here one thread owns four
+// particles and all rows, so the particle stream is read with 16-byte
+// coalesced loads (three float4 = four xyz triples) marked evict-first, and the
+// counter updates are fire-and-forget reductions (RED) that resolve in L2.
+// Counters are uint32 so the wrap-around of int32 two's complement is defined.
+#include "hs_device.cuh"
+#include "hs_kernels.h"
+
+namespace hs {
+
+namespace {
+
+struct UpdateArgs {
+    uint64_t n;
+    uint64_t g0;           // global index of particle 0 of this launch
+    uint64_t thr;          // keep iff splitmix64(g) < thr (unless keep_all)
+    uint64_t sample_seed;
+    uint64_t *probe;       // probe[g] = key for g < probe_cap
+    uint64_t probe_cap;
+    uint32_t keep_all;
+    uint32_t band_lo;      // only buckets in [band_lo, band_hi) are updated
+    uint32_t band_hi;
+};
+
+template <int T>
+__device__ __forceinline__ void add_particle(float x, float y, float z, uint64_t g,
+                                             const SketchDesc &d, const UpdateArgs &a,
+                                             uint32_t *__restrict__ C) {
+    bool keep = a.keep_all || splitmix64_at(a.sample_seed, g) < a.thr;
+    uint32_t cx = 0, cy = 0, cz = 0;
+    bool valid = axis_cell(x, d.inv_cell, d.G, cx);
+    valid &= axis_cell(y, d.inv_cell, d.G, cy);
+    valid &= axis_cell(z, d.inv_cell, d.G, cz);
+    if (g < a.probe_cap) a.probe[g] = valid ? key_of(cx, cy, cz, d.G) : kInvalidKey;
+    if (!(keep && valid)) return;
+    constexpr int kRows = T > 0 ? T : kMaxRows;
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        if (T == 0 && r >= (int)d.rows) break;
+        uint64_t v = row_value(d.seed[r], cx, cy, cz);
+        uint32_t b = bucket_of(v, d.log2w);
+        if (b >= a.band_lo && b < a.band_hi)
+            atomicAdd(&C[(uint64_t)r * d.W + b], sign_of(v, d.log2w));
+    }
+}
+
+// xyz 16-byte aligned: thread q owns particles 4q .. 4q+3 (48 bytes, three float4).
+template <int T>
+__global__ void __launch_bounds__(256) k_update_vec4(const float *__restrict__ xyz,
+                                                     const SketchDesc d, const UpdateArgs a,
+                                                     uint32_t *__restrict__ C) {
+    const uint64_t ngroups = a.n >> 2;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const float4 *p4 = reinterpret_cast<const float4 *>(xyz);
+    for (uint64_t q = tid; q < ngroups; q += stride) {
+        float4 u = __ldcs(p4 + 3 * q);
+        float4 v = __ldcs(p4 + 3 * q + 1);
+        float4 w = __ldcs(p4 + 3 * q + 2);
+        uint64_t g = a.g0 + 4 * q;
+        add_particle<T>(u.x, u.y, u.z, g, d, a, C);
+        add_particle<T>(u.w, v.x, v.y, g + 1, d, a, C);
+        add_particle<T>(v.z, v.w, w.x, g + 2, d, a, C);
+        add_particle<T>(w.y, w.z, w.w, g + 3, d, a, C);
+    }
+    // the n % 4 particles after the last full group
+    uint64_t i = (ngroups << 2) + tid;
+    if (i < a.n)
+        add_particle<T>(__ldcs(xyz + 3 * i), __ldcs(xyz + 3 * i + 1), __ldcs(xyz + 3 * i + 2),
+                        a.g0 + i, d, a, C);
+}
+
+// any 4-byte aligned xyz: one particle per thread per step
+template <int T>
+__global__ void __launch_bounds__(256) k_update_scalar(const float *__restrict__ xyz,
+                                                       const SketchDesc d, const UpdateArgs a,
+                                                       uint32_t *__restrict__ C) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride)
+        add_particle<T>(__ldcs(xyz + 3 * i), __ldcs(xyz + 3 * i + 1), __ldcs(xyz + 3 * i + 2),
+                        a.g0 + i, d, a, C);
+}
+
+// Random fire-and-forget adds into an n_counters table (power of two): the
+// L2 reduction rate that bounds the update when the particle stream does not.
+__global__ void __launch_bounds__(256) k_red_rate(uint32_t *__restrict__ T, uint64_t mask,
+                                                  uint64_t ops_per_thread, uint64_t salt) {
+    uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint64_t s = splitmix64_at(salt, tid);
+    for (uint64_t i = 0; i < ops_per_thread; ++i) {
+        s = s * 6364136223846793005ull + 1442695040888963407ull;
+        atomicAdd(&T[(s >> 20) & mask], 1u);
+    }
+}
+
+__global__ void k_add_counters(uint32_t *__restrict__ dst, const uint32_t *__restrict__ src,
+                               uint64_t n) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        dst[i] += src[i];
+}
+
+}  // namespace
+
+cudaError_t launch_add_counters(int32_t *dst, const int32_t *src, uint64_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    uint64_t blocks = (n + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    k_add_counters<<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<uint32_t *>(dst),
+                                                   reinterpret_cast<const uint32_t *>(src), n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update(const float *xyz, uint64_t n, uint64_t g0, const SketchDesc &d,
+                          int32_t *C, double rate, uint64_t sample_seed, uint64_t *probe,
+                          uint64_t probe_cap, uint32_t band_lo, uint32_t band_hi, int max_blocks,
+                          cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    UpdateArgs a;
+    a.n = n;
+    a.g0 = g0;
+    a.keep_all = rate >= 1.0 ? 1u : 0u;
+    a.thr = rate >= 1.0 ? 0 : (uint64_t)ldexp(rate, 64);
+    a.sample_seed = sample_seed;
+    a.probe = probe;
+    // probe slots that this launch can touch: global indices below probe_cap
+    a.probe_cap = probe ? probe_cap : 0;
+    a.band_lo = band_lo;
+    a.band_hi = band_hi;
+    uint32_t *Cu = reinterpret_cast<uint32_t *>(C);
+    const int threads = 256;
+    bool vec = (reinterpret_cast<uintptr_t>(xyz) & 15u) == 0;
+    uint64_t work = vec ? (n >> 2) + 1 : n;
+    uint64_t blocks = (work + threads - 1) / threads;
+    if (blocks > (uint64_t)max_blocks) blocks = (uint64_t)max_blocks;
+    if (blocks < 1) blocks = 1;
+    if (d.rows == 5) {
+        if (vec) k_update_vec4<5><<<(unsigned)blocks, threads, 0, s>>>(xyz, d, a, Cu);
+        else k_update_scalar<5><<<(unsigned)blocks, threads, 0, s>>>(xyz, d, a, Cu);
+    } else {
+        if (vec) k_update_vec4<0><<<(unsigned)blocks, threads, 0, s>>>(xyz, d, a, Cu);
+        else k_update_scalar<0><<<(unsigned)blocks, threads, 0, s>>>(xyz, d, a, Cu);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_red_rate(uint32_t *table, uint64_t n_counters, uint64_t ops_per_thread,
+                            int blocks, cudaStream_t s) {
+    k_red_rate<<<blocks, 256, 0, s>>>(table, n_counters - 1, ops_per_thread, 0x1234567ull);
+    return cudaGetLastError();
+}
+
+}  // namespace hs

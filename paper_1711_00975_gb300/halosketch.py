@@ -1,0 +1,266 @@
+"""ctypes binding of libhalosketch.so (include/halosketch.h), argument marshalling only.
+
+Every function here forwards to the C entry point of the same name; arrays may
+be torch tensors (device or host) or numpy arrays (host), passed by pointer.
+All arithmetic of the path runs in the library's CUDA kernels; if the library
+cannot be loaded the functions raise - there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_lock = threading.Lock()
+_lib = None
+
+HS_OK, HS_ERR_ARG, HS_ERR_CUDA, HS_ERR_OOM, HS_ERR_TABLE_FULL, HS_ERR_TIMEOUT, HS_ERR_STATE = range(7)
+_NAMES = ["HS_OK", "HS_ERR_ARG", "HS_ERR_CUDA", "HS_ERR_OOM", "HS_ERR_TABLE_FULL",
+          "HS_ERR_TIMEOUT", "HS_ERR_STATE"]
+
+
+class HSError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        self.status = status
+        super().__init__(f"{where}: {_NAMES[status] if 0 <= status < 7 else status}: {msg}")
+
+
+class hs_params(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_uint32), ("log2_width", ctypes.c_uint32),
+                ("box", ctypes.c_double), ("cell", ctypes.c_double),
+                ("hash_seed", ctypes.c_uint64), ("sample_seed", ctypes.c_uint64),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class hs_info(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_uint32), ("log2_width", ctypes.c_uint32),
+                ("grid", ctypes.c_uint32), ("inv_cell", ctypes.c_float),
+                ("width", ctypes.c_uint64), ("n_cells", ctypes.c_uint64),
+                ("n_seen", ctypes.c_uint64)]
+
+
+class hs_stats(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_uint64), ("update_launches", ctypes.c_uint64),
+                ("update_ms", ctypes.c_double), ("search_launches", ctypes.c_uint64),
+                ("search_ms", ctypes.c_double), ("topk_ms", ctypes.c_double),
+                ("topk_calls", ctypes.c_uint64), ("last_candidates", ctypes.c_uint64),
+                ("last_threshold", ctypes.c_int32), ("last_passes", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def library_path() -> str:
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "libhalosketch.so")
+
+
+def lib():
+    """Load libhalosketch.so (building it first when stale and nvcc is present)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            from . import build as _build
+            path = library_path()
+            try:
+                path = _build.build()
+            except (OSError, RuntimeError) as e:   # no nvcc: use a library built earlier
+                if not os.path.exists(path):
+                    raise RuntimeError(f"libhalosketch.so is not built and cannot be: {e}")
+            L = ctypes.CDLL(path)
+            vp, u32, u64, i32, f64, ci = (ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
+                                          ctypes.c_int32, ctypes.c_double, ctypes.c_int)
+            sig = {
+                "sketch_create": [ctypes.POINTER(hs_params), vp, ctypes.POINTER(vp)],
+                "sketch_update": [vp, vp, u64, f64],
+                "sketch_query": [vp, vp, u64, vp],
+                "topk_extract": [vp, u32, vp, vp, ctypes.POINTER(u32)],
+                "sketch_destroy": [vp],
+                "sketch_reset": [vp],
+                "sketch_counters": [vp, vp],
+                "sketch_load_counters": [vp, vp],
+                "sketch_merge": [vp, vp],
+                "sketch_info": [vp, ctypes.POINTER(hs_info)],
+                "sketch_synchronize": [vp],
+                "sketch_stats": [vp, ctypes.POINTER(hs_stats), ci],
+                "hs_measure_red_rate": [u64, u64, ctypes.POINTER(f64)],
+            }
+            for name, args in sig.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+            L.hs_last_error.argtypes = []
+            L.hs_last_error.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+def hs_last_error() -> str:
+    return lib().hs_last_error().decode()
+
+
+def _check(st: int, where: str):
+    if st != HS_OK:
+        raise HSError(st, where, hs_last_error())
+
+
+def _ptr(a) -> int:
+    """Address of a torch tensor or numpy array (None -> 0)."""
+    if a is None:
+        return 0
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_params(rows: int, log2_width: int, box: float, cell: float, hash_seed: int = 0,
+                sample_seed: int = 0) -> hs_params:
+    return hs_params(rows, log2_width, box, cell, hash_seed, sample_seed, 0, 0)
+
+
+# ---- the C entry points ----
+
+def sketch_create(params: hs_params, stream=None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().sketch_create(ctypes.byref(params), _stream_ptr(stream), ctypes.byref(h)),
+           "sketch_create")
+    return h
+
+
+def sketch_update(h, xyz, n: int | None = None, sample_rate: float = 1.0) -> None:
+    if n is None:
+        n = (xyz.numel() if hasattr(xyz, "numel") else xyz.size) // 3
+    _check(lib().sketch_update(h, _ptr(xyz), n, sample_rate), "sketch_update")
+
+
+def sketch_query(h, keys, est) -> None:
+    m = keys.numel() if hasattr(keys, "numel") else keys.size
+    _check(lib().sketch_query(h, _ptr(keys), m, _ptr(est)), "sketch_query")
+
+
+def topk_extract(h, k: int, keys: np.ndarray, est: np.ndarray) -> int:
+    n = ctypes.c_uint32()
+    assert keys.size >= k and est.size >= k
+    _check(lib().topk_extract(h, k, _ptr(keys), _ptr(est), ctypes.byref(n)), "topk_extract")
+    return n.value
+
+
+def sketch_destroy(h) -> None:
+    _check(lib().sketch_destroy(h), "sketch_destroy")
+
+
+def sketch_reset(h) -> None:
+    _check(lib().sketch_reset(h), "sketch_reset")
+
+
+def sketch_counters(h, out) -> None:
+    _check(lib().sketch_counters(h, _ptr(out)), "sketch_counters")
+
+
+def sketch_load_counters(h, src) -> None:
+    _check(lib().sketch_load_counters(h, _ptr(src)), "sketch_load_counters")
+
+
+def sketch_merge(dst, src) -> None:
+    _check(lib().sketch_merge(dst, src), "sketch_merge")
+
+
+def sketch_info(h) -> hs_info:
+    info = hs_info()
+    _check(lib().sketch_info(h, ctypes.byref(info)), "sketch_info")
+    return info
+
+
+def sketch_synchronize(h) -> None:
+    _check(lib().sketch_synchronize(h), "sketch_synchronize")
+
+
+def sketch_stats(h, reset: bool = False) -> dict:
+    s = hs_stats()
+    _check(lib().sketch_stats(h, ctypes.byref(s), 1 if reset else 0), "sketch_stats")
+    return s.as_dict()
+
+
+def hs_measure_red_rate(n_counters: int, total_ops: int) -> float:
+    r = ctypes.c_double()
+    _check(lib().hs_measure_red_rate(n_counters, total_ops, ctypes.byref(r)), "hs_measure_red_rate")
+    return r.value
+
+
+# ---- convenience wrapper ----
+
+class Sketch:
+    """Owns one library handle; methods forward to the entry points above."""
+
+    def __init__(self, rows: int, log2_width: int, box: float, cell: float, hash_seed: int = 0,
+                 sample_seed: int = 0, stream=None):
+        self.params = make_params(rows, log2_width, box, cell, hash_seed, sample_seed)
+        self.h = sketch_create(self.params, stream)
+        info = sketch_info(self.h)
+        self.rows, self.width, self.G, self.n_cells = info.rows, info.width, info.grid, info.n_cells
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            sketch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def update(self, xyz, n=None, rate: float = 1.0):
+        sketch_update(self.h, xyz, n, rate)
+
+    def query(self, keys) -> np.ndarray:
+        keys = np.ascontiguousarray(keys, np.uint64)
+        est = np.empty(keys.size, np.int32)
+        sketch_query(self.h, keys, est)
+        return est
+
+    def topk(self, k: int):
+        keys = np.empty(k, np.uint64)
+        est = np.empty(k, np.int32)
+        n = topk_extract(self.h, k, keys, est)
+        return keys[:n], est[:n]
+
+    def counters(self) -> np.ndarray:
+        out = np.empty((self.rows, self.width), np.int32)
+        sketch_counters(self.h, out)
+        return out
+
+    def load_counters(self, c: np.ndarray):
+        c = np.ascontiguousarray(c, np.int32)
+        assert c.shape == (self.rows, self.width)
+        sketch_load_counters(self.h, c)
+
+    def reset(self):
+        sketch_reset(self.h)
+
+    def merge(self, other: "Sketch"):
+        sketch_merge(self.h, other.h)
+
+    def info(self) -> hs_info:
+        return sketch_info(self.h)
+
+    def stats(self, reset=False) -> dict:
+        return sketch_stats(self.h, reset)
+
+    def synchronize(self):
+        sketch_synchronize(self.h)

@@ -1,0 +1,232 @@
+"""GPU path vs the CPU oracle, through the C ABI: counters, estimates and top-k
+must match bit for bit (integer work; the only float op, the quantisation
+multiply, is one float32 rounding on both sides)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+NT = oracle.default_threads()
+
+
+@pytest.fixture(scope="module")
+def hs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1711_00975_gb300 import halosketch
+    halosketch.lib()
+    return halosketch
+
+
+@pytest.fixture(scope="module")
+def small():
+    spec = synth.small_box(0)
+    return spec, synth.HaloBox(spec).generate()
+
+
+def _pair(hs, rows, log2w, box, cell, hash_seed, sample_seed=0):
+    sk = hs.Sketch(rows, log2w, box, cell, hash_seed, sample_seed)
+    p = oracle.Params(rows, log2w, box, cell, hash_seed, sample_seed)
+    return sk, p
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+# ---------------------------------------------------------------- update mode
+
+@pytest.mark.parametrize("rate", [1.0, 0.1, 1.0 / 16])
+def test_update_small_box_bitexact(hs, small, rate):
+    spec, xyz = small
+    sk, p = _pair(hs, 5, 16, spec.box, 0.1, 11, 22)
+    sk.update(_dev(xyz), rate=rate)
+    want = oracle.sketch_update(oracle.new_counters(p), p, xyz, rate=rate, nthreads=NT)
+    assert np.array_equal(sk.counters(), want)
+    assert sk.info().n_seen == len(xyz)
+
+
+def test_update_ragged_calls_and_alignment(hs, small):
+    # uneven call sizes keep the global particle index running across calls;
+    # the 1-particle offsets give 12-byte (unaligned) starts
+    spec, xyz = small
+    sk, p = _pair(hs, 5, 12, spec.box, 0.1, 5, 9)
+    d = _dev(xyz)
+    sizes = [0, 1, 3, 4, 5, 1023, 100003, 7, 64, 250001]
+    off = 0
+    want = oracle.new_counters(p)
+    for n in sizes:
+        sk.update(d[off:off + n], n, rate=0.5)
+        oracle.sketch_update(want, p, xyz[off:off + n], g0=off, rate=0.5, nthreads=NT)
+        off += n
+    assert np.array_equal(sk.counters(), want)
+
+
+def test_update_from_host_buffers(hs, small):
+    spec, xyz = small
+    sk, p = _pair(hs, 5, 16, spec.box, 0.1, 3, 4)
+    pinned = torch.from_numpy(xyz[:600000]).pin_memory()
+    sk.update(xyz[600000:700001])                 # pageable numpy
+    sk.update(pinned)                             # pinned torch
+    want = oracle.new_counters(p)
+    oracle.sketch_update(want, p, xyz[600000:700001], g0=0, nthreads=NT)
+    oracle.sketch_update(want, p, xyz[:600000], g0=100001, nthreads=NT)
+    assert np.array_equal(sk.counters(), want)
+
+
+@pytest.mark.parametrize("rows,log2w", [(1, 10), (3, 14), (4, 8), (7, 18), (32, 6)])
+def test_update_other_shapes(hs, small, rows, log2w):
+    spec, xyz = small
+    sk, p = _pair(hs, rows, log2w, spec.box, 0.1, 100 + rows, 1)
+    sk.update(_dev(xyz[:300000]), rate=0.7)
+    want = oracle.sketch_update(oracle.new_counters(p), p, xyz[:300000], rate=0.7, nthreads=NT)
+    assert np.array_equal(sk.counters(), want)
+
+
+def test_update_edge_coordinates(hs):
+    sk, p = _pair(hs, 5, 10, 100.0, 0.1, 1)
+    pts = np.array([[0, 0, 0], [100.0, 99.99999, -0.05], [0.7, 0.3, 250.0], [-1e-30, 5e9, 1],
+                    [np.nan, 1, 1], [1, np.inf, 2], [3e9, -3e9, 1], [1, 2, 3]], np.float32)
+    pts = np.repeat(pts, 3, axis=0)
+    sk.update(_dev(pts))
+    want = oracle.sketch_update(oracle.new_counters(p), p, pts)
+    assert np.array_equal(sk.counters(), want)
+
+
+def test_counter_wraparound(hs):
+    sk, p = _pair(hs, 3, 4, 0.1, 0.1, 0)               # one cell
+    c = np.zeros((3, 16), np.int32)
+    for r in range(3):
+        b, s = oracle.hash_row(p, r, (0, 0, 0))
+        c[r, b] = 2**31 - 1 if s > 0 else -2**31
+    sk.load_counters(c)
+    sk.update(_dev(np.zeros((2, 3), np.float32)))
+    want = c.copy()
+    oracle.sketch_update(want, p, np.zeros((2, 3), np.float32))
+    assert np.array_equal(sk.counters(), want)
+
+
+def test_merge_is_the_sketch_of_the_union(hs, small):
+    spec, xyz = small
+    a, p = _pair(hs, 5, 14, spec.box, 0.1, 8, 8)
+    b, _ = _pair(hs, 5, 14, spec.box, 0.1, 8, 8)
+    a.update(_dev(xyz[:400000]))
+    b.update(_dev(xyz[400000:]))
+    a.merge(b)
+    want = oracle.sketch_update(oracle.new_counters(p), p, xyz, nthreads=NT)
+    assert np.array_equal(a.counters(), want)
+    c, _ = _pair(hs, 5, 13, spec.box, 0.1, 8, 8)
+    with pytest.raises(hs.HSError):
+        a.merge(c)
+
+
+def test_reset(hs, small):
+    spec, xyz = small
+    sk, p = _pair(hs, 5, 12, spec.box, 0.1, 2)
+    sk.update(_dev(xyz[:1000]))
+    sk.reset()
+    assert not sk.counters().any() and sk.info().n_seen == 0
+
+
+# --------------------------------------------------------------- estimate mode
+
+def test_point_query(hs, small):
+    spec, xyz = small
+    sk, p = _pair(hs, 5, 16, spec.box, 0.1, 7)
+    sk.update(_dev(xyz))
+    C = oracle.sketch_update(oracle.new_counters(p), p, xyz, nthreads=NT)
+    rng = np.random.default_rng(0)
+    keys = np.concatenate([oracle.keys_of(xyz[:5000], p),
+                           rng.integers(0, p.n_cells, 5000, dtype=np.uint64)])
+    assert np.array_equal(sk.query(keys), oracle.estimate(C, p, keys))
+    dkeys, dest = _dev(keys), torch.empty(keys.size, dtype=torch.int32, device="cuda")
+    hs.sketch_query(sk.h, dkeys, dest)
+    assert np.array_equal(dest.cpu().numpy(), oracle.estimate(C, p, keys))
+    with pytest.raises(hs.HSError):
+        sk.query(np.array([p.n_cells], np.uint64))
+
+
+def test_topk_small_box_bitexact(hs, small):
+    spec, xyz = small
+    sk, p = _pair(hs, 5, 16, spec.box, 0.1, 13)
+    sk.update(_dev(xyz))
+    C = sk.counters()
+    assert np.array_equal(C, oracle.sketch_update(oracle.new_counters(p), p, xyz, nthreads=NT))
+    keys, est = sk.topk(1000)
+    wk, we = oracle.topk_full(C, p, 1000, nthreads=NT)
+    assert np.array_equal(keys, wk) and np.array_equal(est, we)
+
+
+@pytest.mark.parametrize("rows,log2w,G,k", [(5, 6, 16, 50), (5, 8, 40, 4000), (3, 7, 24, 300),
+                                            (4, 5, 20, 100), (1, 9, 30, 77), (7, 10, 36, 500),
+                                            (5, 4, 12, 1728), (5, 4, 12, 5000)])
+def test_topk_small_dictionaries_bitexact(hs, rows, log2w, G, k):
+    # narrow sketches: many collisions, ties and negative estimates
+    rng = np.random.default_rng(rows * 1000 + G)
+    box = G * 0.1
+    sk, p = _pair(hs, rows, log2w, box, 0.1, 50 + G)
+    centres = rng.uniform(0, box, (6, 3))
+    pts = centres[rng.integers(0, 6, 20000)] + rng.normal(0, box / 20, (20000, 3))
+    pts = np.mod(pts, box).astype(np.float32)
+    sk.update(_dev(pts))
+    C = sk.counters()
+    keys, est = sk.topk(k)
+    wk, we = oracle.topk_full(C, p, k, nthreads=NT)
+    assert len(keys) == min(k, G ** 3)
+    assert np.array_equal(keys, wk) and np.array_equal(est, we)
+
+
+def test_topk_loaded_random_counters(hs):
+    # arbitrary counters (any sign, any magnitude) through the same search
+    rng = np.random.default_rng(77)
+    for rows, log2w, G, k in [(5, 10, 50, 2000), (5, 12, 64, 3000), (6, 9, 33, 1000)]:
+        sk, p = _pair(hs, rows, log2w, G * 0.1, 0.1, rows + G)
+        C = rng.integers(-50, 50, size=(rows, 1 << log2w)).astype(np.int32)
+        C[:, ::97] = rng.integers(-2**31, 2**31 - 1, size=C[:, ::97].shape)
+        sk.load_counters(C)
+        keys, est = sk.topk(k)
+        wk, we = oracle.topk_full(C, p, k, nthreads=NT)
+        assert np.array_equal(keys, wk) and np.array_equal(est, we)
+
+
+def test_topk_empty_sketch_ties(hs):
+    # every estimate is 0: the k smallest keys, through the tie path
+    sk, p = _pair(hs, 5, 16, 100.0, 0.1, 1)
+    keys, est = sk.topk(1000)
+    assert np.array_equal(keys, np.arange(1000, dtype=np.uint64)) and not est.any()
+
+
+def test_topk_single_heavy_cell_many_ties(hs):
+    # one occupied cell: it ranks first with its exact count; every other cell
+    # estimates 0 (it could only differ by colliding with the heavy cell in 3 of
+    # 5 rows, about 1e9 * 10 * 2^-60 expected cells), so the rest are the
+    # smallest keys - reached through the tie path
+    sk, p = _pair(hs, 5, 20, 100.0, 0.1, 4)
+    pts = np.tile(np.array([[50.05, 50.05, 50.05]], np.float32), (333, 1))
+    sk.update(_dev(pts))
+    keys, est = sk.topk(64)
+    heavy = int(oracle.keys_of(pts[:1], p)[0])
+    assert [int(v) for v in keys] == [heavy] + list(range(63))
+    assert [int(v) for v in est] == [333] + [0] * 63
+    C = sk.counters()
+    assert np.array_equal(oracle.estimate(C, p, keys), est)
+
+
+def test_topk_after_reset_and_requery(hs, small):
+    spec, xyz = small
+    sk, p = _pair(hs, 5, 16, spec.box, 0.1, 21)
+    sk.update(_dev(xyz[:500000]))
+    k1 = sk.topk(200)
+    k1b = sk.topk(200)
+    assert np.array_equal(k1[0], k1b[0]) and np.array_equal(k1[1], k1b[1])
+    sk.reset()
+    sk.update(_dev(xyz[500000:]))
+    C = sk.counters()
+    keys, est = sk.topk(300)
+    wk, we = oracle.topk_full(C, p, 300, nthreads=NT)
+    assert np.array_equal(keys, wk) and np.array_equal(est, we)
