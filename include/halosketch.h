@@ -64,8 +64,15 @@ typedef enum {
     HS_ERR_STATE = 6       /* handle in a state that does not allow the call       */
 } hs_status;
 
+/* Flags of hs_params.  The full search picks, per pass, the cheaper of two
+ * exact methods - scanning every cell with a shared-memory filter, or
+ * enumerating the cells of hot buckets through a directory of mesh lines;
+ * these flags force one (for testing; both give the same result). */
+#define HS_FLAG_SEARCH_SCAN 1u
+#define HS_FLAG_SEARCH_DIRECTORY 2u
+
 /* Sketch parameters.  rows in [1, 32]; log2_width in [1, 30]; box > 0 and
- * cell > 0 with 1 <= round(box / cell) <= 2^21; flags must be 0. */
+ * cell > 0 with 1 <= round(box / cell) <= 2^21; flags: 0 or one HS_FLAG_*. */
 typedef struct {
     uint32_t rows;        /* t: number of independent rows (Sec. 2.2)         */
     uint32_t log2_width;  /* b = W = 2^log2_width counters per row            */
@@ -73,7 +80,7 @@ typedef struct {
     double cell;          /* mesh cell size (Sec. 2.1)                         */
     uint64_t hash_seed;   /* seeds the row hash functions                     */
     uint64_t sample_seed; /* seeds the sampling hash                          */
-    uint32_t flags;       /* reserved, must be 0                              */
+    uint32_t flags;       /* 0 or one HS_FLAG_SEARCH_* value                  */
     uint32_t reserved;    /* must be 0                                        */
 } hs_params;
 

@@ -89,6 +89,19 @@ struct hs_sketch {
     int32_t *q_est = nullptr;
     uint64_t q_cap = 0;
 
+    // output-sensitive search: exact hot bitmap, hot-bucket lists, and one
+    // directory of mesh lines per enumerated row (kept across queries)
+    uint32_t *xbits = nullptr;
+    uint32_t *hot_list = nullptr;
+    unsigned long long *hot_cnt = nullptr;
+    uint64_t hot_cap = 0;
+    uint32_t dir_D = 0;
+    uint32_t *dir_off[kMaxRows] = {};
+    DirRecord *dir_rec[kMaxRows] = {};
+    uint32_t *dir_cursor = nullptr;
+    uint32_t *scan_scratch = nullptr;
+    bool dir_failed = false;
+
     // benchmarking
     hs_stats stats;
     std::vector<EventPair> pending_update, pending_search, pool;
@@ -116,7 +129,11 @@ hs_status check_params(const hs_params *p) {
     double g = std::llround(p->box / p->cell);
     if (g < 1 || g > (double)(1u << 21))
         return fail(HS_ERR_ARG, "grid round(box/cell)=%.0f outside [1, 2^21]", g);
-    if (p->flags != 0 || p->reserved != 0) return fail(HS_ERR_ARG, "flags/reserved must be 0");
+    if ((p->flags & ~(uint32_t)(HS_FLAG_SEARCH_SCAN | HS_FLAG_SEARCH_DIRECTORY)) != 0 ||
+        p->reserved != 0)
+        return fail(HS_ERR_ARG, "unknown flags or reserved != 0");
+    if ((p->flags & HS_FLAG_SEARCH_SCAN) && (p->flags & HS_FLAG_SEARCH_DIRECTORY))
+        return fail(HS_ERR_ARG, "at most one search method may be forced");
     return HS_OK;
 }
 
@@ -196,6 +213,72 @@ hs_status ensure_topk_scratch(hs_sketch *h, uint64_t k) {
     return HS_OK;
 }
 
+void free_dir(hs_sketch *h) {
+    void *ps[] = {h->xbits, h->hot_list, h->hot_cnt, h->dir_cursor, h->scan_scratch};
+    for (void *p : ps)
+        if (p) cudaFree(p);
+    for (int r = 0; r < kMaxRows; ++r) {
+        if (h->dir_off[r]) cudaFree(h->dir_off[r]);
+        if (h->dir_rec[r]) cudaFree(h->dir_rec[r]);
+        h->dir_off[r] = nullptr;
+        h->dir_rec[r] = nullptr;
+    }
+    h->xbits = nullptr;
+    h->hot_list = nullptr;
+    h->hot_cnt = nullptr;
+    h->dir_cursor = nullptr;
+    h->scan_scratch = nullptr;
+}
+
+// rows whose hot buckets are enumerated: a passing cell is hot in one of them
+uint32_t enum_rows(const hs_sketch *h) {
+    uint32_t t = h->d.rows, need = t - (t - 1) / 2;
+    return t - need + 1;
+}
+
+// scratch of the directory search (not the directories themselves)
+hs_status ensure_dir_scratch(hs_sketch *h) {
+    if (h->xbits) return HS_OK;
+    uint64_t wpr = std::max<uint64_t>(h->d.W >> 5, 1);
+    h->dir_D = std::min<uint32_t>(h->d.log2w, 26);
+    h->hot_cap = std::min<uint64_t>(h->d.W, 1ull << 22);
+    uint64_t nslots = 1ull << h->dir_D;
+    HS_CUDA(cudaMalloc(&h->xbits, (size_t)h->d.rows * wpr * 4));
+    HS_CUDA(cudaMalloc(&h->hot_list, (size_t)enum_rows(h) * h->hot_cap * 4));
+    HS_CUDA(cudaMalloc(&h->hot_cnt, kMaxRows * sizeof(unsigned long long)));
+    HS_CUDA(cudaMalloc(&h->dir_cursor, (nslots + 1) * 4));
+    HS_CUDA(cudaMalloc(&h->scan_scratch, (nslots / 1024 + 4096) * 4));
+    return HS_OK;
+}
+
+// build (once) the directory of row r; false when memory is short
+bool ensure_dir(hs_sketch *h, int r) {
+    if (h->dir_off[r]) return true;
+    uint64_t lines = (uint64_t)h->d.G * h->d.G;
+    uint64_t nslots = 1ull << h->dir_D;
+    if (cudaMalloc(&h->dir_off[r], (nslots + 1) * 4) != cudaSuccess ||
+        cudaMalloc(&h->dir_rec[r], lines * sizeof(DirRecord)) != cudaSuccess) {
+        cudaGetLastError();
+        if (h->dir_off[r]) cudaFree(h->dir_off[r]);
+        h->dir_off[r] = nullptr;
+        h->dir_rec[r] = nullptr;
+        return false;
+    }
+    int launches = 0;
+    cudaError_t e = launch_dir_build(h->d, r, h->dir_D, h->dir_off[r], h->dir_cursor, h->dir_rec[r],
+                                     h->scan_scratch, h->num_sms * 8, h->stream, &launches);
+    h->stats.kernel_launches += launches;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(h->dir_off[r]);
+        cudaFree(h->dir_rec[r]);
+        h->dir_off[r] = nullptr;
+        h->dir_rec[r] = nullptr;
+        return false;
+    }
+    return true;
+}
+
 hs_status ensure_staging(hs_sketch *h) {
     if (h->stage[0]) return HS_OK;
     for (int i = 0; i < 2; ++i) {
@@ -234,32 +317,97 @@ hs_status launch_update_timed(hs_sketch *h, const float *xyz, uint64_t n, uint64
     return HS_OK;
 }
 
-// One full-search pass over lines [line_lo, line_hi); appends after *count_base.
+// Directory search of one pass; *used = false when it does not apply (too
+// many hot buckets, more work than the scan, or memory short).
+hs_status search_pass_dir(hs_sketch *h, int32_t theta, SearchMode mode, int64_t hot,
+                          uint64_t line_lo, uint64_t line_hi, SearchOut out, bool *used) {
+    *used = false;
+    const uint64_t G = h->d.G, lines = G * G;
+    if (h->dir_failed || lines >= (1ull << 32)) return HS_OK;
+    if (ensure_dir_scratch(h) != HS_OK) {
+        cudaGetLastError();
+        free_dir(h);
+        h->dir_failed = true;
+        return HS_OK;
+    }
+    const uint32_t F = enum_rows(h);
+    HS_CUDA(launch_hot_bitmap(h->C, h->d, h->d.log2w, (int32_t)std::min<int64_t>(hot, INT32_MAX),
+                              h->xbits, h->num_sms * 8, h->stream));
+    HS_CUDA(cudaMemsetAsync(h->hot_cnt, 0, kMaxRows * sizeof(unsigned long long), h->stream));
+    for (uint32_t r = 0; r < F; ++r)
+        HS_CUDA(launch_hot_list(h->xbits, h->d, (int)r, h->hot_list + r * h->hot_cap,
+                                &h->hot_cnt[r], h->hot_cap, h->num_sms * 8, h->stream));
+    h->stats.kernel_launches += 1 + F;
+    unsigned long long cnt[kMaxRows];
+    HS_CUDA(cudaMemcpyAsync(cnt, h->hot_cnt, F * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, h->stream));
+    HS_CUDA(cudaStreamSynchronize(h->stream));
+    // relative costs: one scanned cell ~ 1; one (cx, hot bucket) query ~ 20
+    // units per directory line it reads; building a directory ~ 60 units/line
+    const double per_slot = (double)lines / (double)(1ull << h->dir_D);
+    double cost_dir = 0, cost_scan = (double)G * G * G;
+    for (uint32_t r = 0; r < F; ++r) {
+        if (cnt[r] > h->hot_cap) return HS_OK;
+        cost_dir += 20.0 * (double)G * (double)cnt[r] * (2.0 + 2.0 * per_slot);
+        if (!h->dir_off[r]) cost_dir += 60.0 * (double)lines;
+    }
+    const uint32_t force = h->p.flags & (HS_FLAG_SEARCH_SCAN | HS_FLAG_SEARCH_DIRECTORY);
+    if (force == HS_FLAG_SEARCH_SCAN) return HS_OK;
+    if (force != HS_FLAG_SEARCH_DIRECTORY && cost_dir >= cost_scan) return HS_OK;
+    for (uint32_t r = 0; r < F; ++r) {
+        if (!ensure_dir(h, (int)r)) {
+            free_dir(h);
+            h->dir_failed = true;
+            return HS_OK;
+        }
+    }
+    EventPair ev = take_events(h);
+    cudaEventRecord(ev.a, h->stream);
+    for (uint32_t r = 0; r < F; ++r) {
+        HS_CUDA(launch_dir_query(h->C, h->d, (int)r, h->dir_D, h->dir_off[r], h->dir_rec[r],
+                                 h->hot_list + r * h->hot_cap, cnt[r], h->xbits, theta, mode,
+                                 line_lo, line_hi, out, h->num_sms * 16, h->stream));
+    }
+    cudaEventRecord(ev.b, h->stream);
+    h->pending_search.push_back(ev);
+    h->stats.search_launches += 1;
+    h->stats.kernel_launches += F;
+    *used = true;
+    return HS_OK;
+}
+
+// One full-search pass over lines [line_lo, line_hi); appends after count_base.
 // Returns the new candidate count (possibly above cap).
 hs_status search_pass(hs_sketch *h, int32_t theta, SearchMode mode, uint64_t line_lo,
                       uint64_t line_hi, unsigned long long count_base,
                       unsigned long long *count_out) {
     int64_t hot = (int64_t)theta + (mode == kGT ? 1 : 0);
     int prune = hot >= 1;
-    if (prune) {
-        HS_CUDA(launch_hot_bitmap(h->C, h->d, h->nb, (int32_t)std::min<int64_t>(hot, INT32_MAX),
-                                  h->bitmap, h->num_sms * 8, h->stream));
-        h->stats.kernel_launches += 1;
-    }
+    if (mode == kGT && theta == INT32_MAX) line_hi = line_lo;   // nothing above the largest int32
     HS_CUDA(cudaMemcpyAsync(&h->counters[0], &count_base, sizeof(count_base),
                             cudaMemcpyHostToDevice, h->stream));
     SearchOut out{h->cand_key, h->cand_est, &h->counters[0], h->cap};
-    if (mode == kGT && theta == INT32_MAX) {
-        line_hi = line_lo;   // nothing is above the largest int32
+    bool used = false;
+    if (prune && line_hi > line_lo) {
+        hs_status st = search_pass_dir(h, theta, mode, hot, line_lo, line_hi, out, &used);
+        if (st != HS_OK) return st;
     }
-    EventPair ev = take_events(h);
-    cudaEventRecord(ev.a, h->stream);
-    HS_CUDA(launch_full_search(h->C, h->d, theta, mode, h->bitmap, h->nb, prune, line_lo, line_hi,
-                               out, h->num_sms, h->stream));
-    cudaEventRecord(ev.b, h->stream);
-    h->pending_search.push_back(ev);
-    h->stats.search_launches += 1;
-    h->stats.kernel_launches += 1;
+    if (!used) {
+        if (prune) {
+            HS_CUDA(launch_hot_bitmap(h->C, h->d, h->nb,
+                                      (int32_t)std::min<int64_t>(hot, INT32_MAX), h->bitmap,
+                                      h->num_sms * 8, h->stream));
+            h->stats.kernel_launches += 1;
+        }
+        EventPair ev = take_events(h);
+        cudaEventRecord(ev.a, h->stream);
+        HS_CUDA(launch_full_search(h->C, h->d, theta, mode, h->bitmap, h->nb, prune, line_lo,
+                                   line_hi, out, h->num_sms, h->stream));
+        cudaEventRecord(ev.b, h->stream);
+        h->pending_search.push_back(ev);
+        h->stats.search_launches += 1;
+        h->stats.kernel_launches += 1;
+    }
     h->stats.last_passes += 1;
     h->stats.last_threshold = theta;
     unsigned long long c = 0;
@@ -350,6 +498,7 @@ hs_status sketch_destroy(hs_sketch *h) {
     if (!h) return HS_OK;
     cudaStreamSynchronize(h->stream);
     free_topk_scratch(h);
+    free_dir(h);
     if (h->C) cudaFree(h->C);
     if (h->probe) cudaFree(h->probe);
     if (h->q_keys) cudaFree(h->q_keys);

@@ -48,6 +48,26 @@ cudaError_t launch_probe_distinct(const uint64_t *probe, uint64_t m, uint64_t *s
                                   unsigned long long *n_distinct, uint32_t *overflow,
                                   cudaStream_t s);
 
+// ---- output-sensitive full search (k_dir.cu) ----
+struct DirRecord {           // one mesh line of a row's directory
+    uint64_t L;              // a1*cy + a2*cz + b of that row (mod 2^64)
+    uint32_t cy, cz;
+};
+// directory of the G^2 lines of row r bucketed by the top D bits of L
+cudaError_t launch_dir_build(const SketchDesc &d, int r, uint32_t D, uint32_t *offsets,
+                             uint32_t *cursor, DirRecord *rec, uint32_t *scan_scratch,
+                             int max_blocks, cudaStream_t s, int *launches);
+// bucket indices of the set bits of row r of an exact (one bit per bucket) hot bitmap
+cudaError_t launch_hot_list(const uint32_t *bits, const SketchDesc &d, int r, uint32_t *list,
+                            unsigned long long *count, uint64_t cap, int max_blocks,
+                            cudaStream_t s);
+// cells first hot in row r, with at least `need` hot rows and a passing estimate
+cudaError_t launch_dir_query(const int32_t *C, const SketchDesc &d, int r, uint32_t D,
+                             const uint32_t *offsets, const DirRecord *rec, const uint32_t *hot,
+                             uint64_t n_hot, const uint32_t *bits, int32_t theta, SearchMode mode,
+                             uint64_t line_lo, uint64_t line_hi, SearchOut out, int max_blocks,
+                             cudaStream_t s);
+
 // ---- ranking (k_select.cu) ----
 struct SelectState {
     uint32_t hi;        // decided digits of the estimate part

@@ -1,0 +1,253 @@
+// k_dir.cu - output-sensitive full search (estimate mode of Algorithm 1,
+// arXiv:1711.00975) for large meshes.
+//
+// The full search must find every cell whose median estimate reaches theta.
+// With theta > 0 such a cell has at least need = t - floor((t-1)/2) rows with
+// |C[r][bucket_r]| >= theta ("hot" rows), so it is hot in at least one of the
+// first F = t - need + 1 rows.  Each cell is therefore reported from the first
+// row r < F in which it is hot, and only from there.
+//
+// Row r's multiply-shift value of cell (cx, cy, cz) splits as
+//     v_r = a0*cx + L_r(cy, cz),   L_r = a1*cy + a2*cz + b   (mod 2^64),
+// so the cells of a hot bucket h with a given cx are exactly the mesh lines
+// (cy, cz) whose L_r falls in the interval [h*2^s - a0*cx, (h+1)*2^s - a0*cx),
+// s = 64 - log2W.  A directory of all G^2 lines bucketed by the top D bits of
+// L_r (counting sort: count, scan, scatter) answers each such interval by
+// reading at most two directory slots.  The work is proportional to
+// F * (G^2 + G * |hot buckets|) instead of G^3, and every cell that could pass
+// is still examined exactly once, so the result equals the exhaustive search.
+#include "hs_device.cuh"
+#include "hs_kernels.h"
+
+namespace hs {
+
+namespace {
+
+__device__ __forceinline__ uint64_t line_value(const RowSeed &s, uint32_t cy, uint32_t cz) {
+    return s.b + mul_lo64(s.a1, cy) + mul_lo64(s.a2, cz);
+}
+
+__device__ __forceinline__ bool exact_hot(const uint32_t *__restrict__ bits, uint64_t words_per_row,
+                                          int r, uint32_t bucket) {
+    return (__ldg(bits + (uint64_t)r * words_per_row + (bucket >> 5)) >> (bucket & 31)) & 1u;
+}
+
+__global__ void k_dir_count(const SketchDesc d, int r, uint32_t D, uint32_t *__restrict__ cnt) {
+    const uint64_t lines = (uint64_t)d.G * d.G;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t line = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; line < lines;
+         line += stride) {
+        uint32_t cy = (uint32_t)(line % d.G), cz = (uint32_t)(line / d.G);
+        uint64_t L = line_value(d.seed[r], cy, cz);
+        atomicAdd(&cnt[L >> (64 - D)], 1u);
+    }
+}
+
+__global__ void k_dir_scatter(const SketchDesc d, int r, uint32_t D, uint32_t *__restrict__ cursor,
+                              DirRecord *__restrict__ rec) {
+    const uint64_t lines = (uint64_t)d.G * d.G;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t line = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; line < lines;
+         line += stride) {
+        uint32_t cy = (uint32_t)(line % d.G), cz = (uint32_t)(line / d.G);
+        uint64_t L = line_value(d.seed[r], cy, cz);
+        uint32_t pos = atomicAdd(&cursor[L >> (64 - D)], 1u);
+        rec[pos] = DirRecord{L, cy, cz};
+    }
+}
+
+// ---- exclusive scan of uint32 counts (three-phase, recursive over block sums) ----
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 2 * kScanThreads;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s_warp,
+                                                         uint32_t *total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t s = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xFFFFFFFFu, s, o);
+            if (lane >= o) s += y;
+        }
+        s_warp[lane] = s;   // inclusive warp-sum prefix
+    }
+    __syncthreads();
+    uint32_t warp_off = w ? s_warp[w - 1] : 0;
+    *total = s_warp[(blockDim.x >> 5) - 1];
+    return warp_off + x - v;
+}
+
+// out[i] = sum of in[0..i) within each block of kScanItems; sums[b] = block total
+__global__ void k_scan_block(const uint32_t *__restrict__ in, uint32_t *__restrict__ out,
+                             uint64_t n, uint32_t *__restrict__ sums) {
+    __shared__ uint32_t s_warp[32];
+    uint64_t base = (uint64_t)blockIdx.x * kScanItems + 2 * threadIdx.x;
+    uint32_t a = base < n ? in[base] : 0;
+    uint32_t b = base + 1 < n ? in[base + 1] : 0;
+    uint32_t total;
+    uint32_t ex = block_exclusive_scan(a + b, s_warp, &total);
+    if (base < n) out[base] = ex;
+    if (base + 1 < n) out[base + 1] = ex + a;
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void k_scan_add(uint32_t *__restrict__ out, uint64_t n, const uint32_t *__restrict__ off) {
+    uint64_t base = (uint64_t)blockIdx.x * kScanItems + 2 * threadIdx.x;
+    uint32_t o = off[blockIdx.x];
+    if (base < n) out[base] += o;
+    if (base + 1 < n) out[base + 1] += o;
+}
+
+cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *scratch,
+                           cudaStream_t s, int *launches) {
+    uint64_t nb = (n + kScanItems - 1) / kScanItems;
+    k_scan_block<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, scratch);
+    *launches += 1;
+    if (nb > 1) {
+        cudaError_t e = exclusive_scan(scratch, scratch, nb, scratch + nb, s, launches);
+        if (e != cudaSuccess) return e;
+        k_scan_add<<<(unsigned)nb, kScanThreads, 0, s>>>(out, n, scratch);
+        *launches += 1;
+    }
+    return cudaGetLastError();
+}
+
+// list of the set bits of row r's exact hot bitmap (bucket indices)
+__global__ void k_hot_list(const uint32_t *__restrict__ bits, uint64_t words_per_row, int r,
+                           uint32_t *__restrict__ list, unsigned long long *__restrict__ count,
+                           uint64_t cap) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words_per_row;
+         w += stride) {
+        uint32_t x = bits[(uint64_t)r * words_per_row + w];
+        if (!x) continue;
+        unsigned long long base = atomicAdd(count, (unsigned long long)__popc(x));
+        while (x) {
+            int b = __ffs(x) - 1;
+            x &= x - 1;
+            if (base < cap) list[base] = (uint32_t)(w * 32 + b);
+            ++base;
+        }
+    }
+}
+
+// one thread per (cx, hot bucket of row r)
+template <int T>
+__global__ void __launch_bounds__(256)
+    k_dir_query(const int32_t *__restrict__ C, const SketchDesc d, int r, uint32_t D,
+                const uint32_t *__restrict__ offsets, const DirRecord *__restrict__ rec,
+                const uint32_t *__restrict__ hot, uint64_t n_hot,
+                const uint32_t *__restrict__ bits, int32_t theta, uint32_t mode, uint64_t line_lo,
+                uint64_t line_hi, SearchOut out) {
+    const uint32_t rows = T > 0 ? (uint32_t)T : d.rows;
+    const uint32_t need = rows - (rows - 1) / 2;
+    const uint64_t words_per_row = d.W >> 5 ? d.W >> 5 : 1;
+    const uint32_t s = 64 - d.log2w;
+    const uint64_t nslots = 1ull << D;
+    const uint64_t total = n_hot * d.G;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += stride) {
+        const uint32_t h = hot[q / d.G];
+        const uint32_t cx = (uint32_t)(q % d.G);
+        const uint64_t Tx = d.seed[r].a0 * (uint64_t)cx;
+        const uint64_t lo = ((uint64_t)h << s) - Tx;
+        const uint64_t slot0 = lo >> (64 - D);
+        for (int j = 0; j < 2; ++j) {
+            const uint64_t slot = (slot0 + j) & (nslots - 1);
+            const uint32_t e0 = offsets[slot], e1 = offsets[slot + 1];
+            for (uint32_t e = e0; e < e1; ++e) {
+                const DirRecord R = rec[e];
+                if (((R.L + Tx) >> s) != h) continue;
+                const uint64_t line = (uint64_t)R.cy + (uint64_t)d.G * R.cz;
+                if (line < line_lo || line >= line_hi) continue;
+                // reported from the first hot row only; count the hot rows
+                uint64_t v[T > 0 ? T : kMaxRows];
+                bool first = true;
+                uint32_t nhot = 1;
+                for (uint32_t rr = 0; rr < rows; ++rr) {
+                    v[rr] = row_value(d.seed[rr], cx, R.cy, R.cz);
+                    if ((int)rr == r) continue;
+                    bool hh = exact_hot(bits, words_per_row, (int)rr, bucket_of(v[rr], d.log2w));
+                    if ((int)rr < r && hh) first = false;
+                    nhot += hh;
+                }
+                if (!first || nhot < need) continue;
+                int32_t ev[T > 0 ? T : kMaxRows];
+                for (uint32_t rr = 0; rr < rows; ++rr)
+                    ev[rr] = signed_count(__ldg(C + rr * d.W + bucket_of(v[rr], d.log2w)), v[rr],
+                                          d.log2w);
+                int32_t est = T == 5 ? median5(ev[0], ev[1], ev[2], ev[3], ev[4])
+                                     : lower_median_dyn(ev, (int)rows);
+                bool pass = mode == kGE ? est >= theta : (mode == kGT ? est > theta : est == theta);
+                if (!pass) continue;
+                unsigned long long idx = atomicAdd(out.count, 1ull);
+                if (idx < out.cap) {
+                    out.key[idx] = key_of(cx, R.cy, R.cz, d.G);
+                    out.est[idx] = est;
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_dir_build(const SketchDesc &d, int r, uint32_t D, uint32_t *offsets,
+                             uint32_t *cursor, DirRecord *rec, uint32_t *scan_scratch,
+                             int max_blocks, cudaStream_t s, int *launches) {
+    const uint64_t nslots = 1ull << D;
+    cudaError_t e = cudaMemsetAsync(cursor, 0, (nslots + 1) * 4, s);
+    if (e != cudaSuccess) return e;
+    const uint64_t lines = (uint64_t)d.G * d.G;
+    uint64_t blocks = (lines + 255) / 256;
+    if (blocks > (uint64_t)max_blocks) blocks = (uint64_t)max_blocks;
+    k_dir_count<<<(unsigned)blocks, 256, 0, s>>>(d, r, D, cursor);
+    *launches += 1;
+    e = exclusive_scan(cursor, offsets, nslots + 1, scan_scratch, s, launches);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(cursor, offsets, nslots * 4, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    k_dir_scatter<<<(unsigned)blocks, 256, 0, s>>>(d, r, D, cursor, rec);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hot_list(const uint32_t *bits, const SketchDesc &d, int r, uint32_t *list,
+                            unsigned long long *count, uint64_t cap, int max_blocks,
+                            cudaStream_t s) {
+    uint64_t wpr = d.W >> 5 ? d.W >> 5 : 1;
+    uint64_t blocks = (wpr + 255) / 256;
+    if (blocks > (uint64_t)max_blocks) blocks = (uint64_t)max_blocks;
+    k_hot_list<<<(unsigned)blocks, 256, 0, s>>>(bits, wpr, r, list, count, cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dir_query(const int32_t *C, const SketchDesc &d, int r, uint32_t D,
+                             const uint32_t *offsets, const DirRecord *rec, const uint32_t *hot,
+                             uint64_t n_hot, const uint32_t *bits, int32_t theta, SearchMode mode,
+                             uint64_t line_lo, uint64_t line_hi, SearchOut out, int max_blocks,
+                             cudaStream_t s) {
+    uint64_t total = n_hot * d.G;
+    if (total == 0) return cudaSuccess;
+    uint64_t blocks = (total + 255) / 256;
+    if (blocks > (uint64_t)max_blocks) blocks = (uint64_t)max_blocks;
+    if (d.rows == 5)
+        k_dir_query<5><<<(unsigned)blocks, 256, 0, s>>>(C, d, r, D, offsets, rec, hot, n_hot, bits,
+                                                       theta, mode, line_lo, line_hi, out);
+    else
+        k_dir_query<0><<<(unsigned)blocks, 256, 0, s>>>(C, d, r, D, offsets, rec, hot, n_hot, bits,
+                                                       theta, mode, line_lo, line_hi, out);
+    return cudaGetLastError();
+}
+
+}  // namespace hs

@@ -16,6 +16,9 @@ import numpy as np
 _lock = threading.Lock()
 _lib = None
 
+HS_FLAG_SEARCH_SCAN = 1
+HS_FLAG_SEARCH_DIRECTORY = 2
+
 HS_OK, HS_ERR_ARG, HS_ERR_CUDA, HS_ERR_OOM, HS_ERR_TABLE_FULL, HS_ERR_TIMEOUT, HS_ERR_STATE = range(7)
 _NAMES = ["HS_OK", "HS_ERR_ARG", "HS_ERR_CUDA", "HS_ERR_OOM", "HS_ERR_TABLE_FULL",
           "HS_ERR_TIMEOUT", "HS_ERR_STATE"]
@@ -123,8 +126,8 @@ def _stream_ptr(stream) -> int:
 
 
 def make_params(rows: int, log2_width: int, box: float, cell: float, hash_seed: int = 0,
-                sample_seed: int = 0) -> hs_params:
-    return hs_params(rows, log2_width, box, cell, hash_seed, sample_seed, 0, 0)
+                sample_seed: int = 0, flags: int = 0) -> hs_params:
+    return hs_params(rows, log2_width, box, cell, hash_seed, sample_seed, flags, 0)
 
 
 # ---- the C entry points ----
@@ -202,8 +205,8 @@ class Sketch:
     """Owns one library handle; methods forward to the entry points above."""
 
     def __init__(self, rows: int, log2_width: int, box: float, cell: float, hash_seed: int = 0,
-                 sample_seed: int = 0, stream=None):
-        self.params = make_params(rows, log2_width, box, cell, hash_seed, sample_seed)
+                 sample_seed: int = 0, stream=None, flags: int = 0):
+        self.params = make_params(rows, log2_width, box, cell, hash_seed, sample_seed, flags)
         self.h = sketch_create(self.params, stream)
         info = sketch_info(self.h)
         self.rows, self.width, self.G, self.n_cells = info.rows, info.width, info.grid, info.n_cells

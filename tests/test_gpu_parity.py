@@ -29,8 +29,11 @@ def small():
     return spec, synth.HaloBox(spec).generate()
 
 
-def _pair(hs, rows, log2w, box, cell, hash_seed, sample_seed=0):
-    sk = hs.Sketch(rows, log2w, box, cell, hash_seed, sample_seed)
+SEARCH = {"auto": 0, "scan": 1, "directory": 2}
+
+
+def _pair(hs, rows, log2w, box, cell, hash_seed, sample_seed=0, flags=0):
+    sk = hs.Sketch(rows, log2w, box, cell, hash_seed, sample_seed, flags=flags)
     p = oracle.Params(rows, log2w, box, cell, hash_seed, sample_seed)
     return sk, p
 
@@ -151,9 +154,10 @@ def test_point_query(hs, small):
         sk.query(np.array([p.n_cells], np.uint64))
 
 
-def test_topk_small_box_bitexact(hs, small):
+@pytest.mark.parametrize("search", list(SEARCH))
+def test_topk_small_box_bitexact(hs, small, search):
     spec, xyz = small
-    sk, p = _pair(hs, 5, 16, spec.box, 0.1, 13)
+    sk, p = _pair(hs, 5, 16, spec.box, 0.1, 13, flags=SEARCH[search])
     sk.update(_dev(xyz))
     C = sk.counters()
     assert np.array_equal(C, oracle.sketch_update(oracle.new_counters(p), p, xyz, nthreads=NT))
@@ -165,11 +169,12 @@ def test_topk_small_box_bitexact(hs, small):
 @pytest.mark.parametrize("rows,log2w,G,k", [(5, 6, 16, 50), (5, 8, 40, 4000), (3, 7, 24, 300),
                                             (4, 5, 20, 100), (1, 9, 30, 77), (7, 10, 36, 500),
                                             (5, 4, 12, 1728), (5, 4, 12, 5000)])
-def test_topk_small_dictionaries_bitexact(hs, rows, log2w, G, k):
+@pytest.mark.parametrize("search", list(SEARCH))
+def test_topk_small_dictionaries_bitexact(hs, rows, log2w, G, k, search):
     # narrow sketches: many collisions, ties and negative estimates
     rng = np.random.default_rng(rows * 1000 + G)
     box = G * 0.1
-    sk, p = _pair(hs, rows, log2w, box, 0.1, 50 + G)
+    sk, p = _pair(hs, rows, log2w, box, 0.1, 50 + G, flags=SEARCH[search])
     centres = rng.uniform(0, box, (6, 3))
     pts = centres[rng.integers(0, 6, 20000)] + rng.normal(0, box / 20, (20000, 3))
     pts = np.mod(pts, box).astype(np.float32)
@@ -181,11 +186,12 @@ def test_topk_small_dictionaries_bitexact(hs, rows, log2w, G, k):
     assert np.array_equal(keys, wk) and np.array_equal(est, we)
 
 
-def test_topk_loaded_random_counters(hs):
+@pytest.mark.parametrize("search", list(SEARCH))
+def test_topk_loaded_random_counters(hs, search):
     # arbitrary counters (any sign, any magnitude) through the same search
     rng = np.random.default_rng(77)
     for rows, log2w, G, k in [(5, 10, 50, 2000), (5, 12, 64, 3000), (6, 9, 33, 1000)]:
-        sk, p = _pair(hs, rows, log2w, G * 0.1, 0.1, rows + G)
+        sk, p = _pair(hs, rows, log2w, G * 0.1, 0.1, rows + G, flags=SEARCH[search])
         C = rng.integers(-50, 50, size=(rows, 1 << log2w)).astype(np.int32)
         C[:, ::97] = rng.integers(-2**31, 2**31 - 1, size=C[:, ::97].shape)
         sk.load_counters(C)
@@ -217,9 +223,10 @@ def test_topk_single_heavy_cell_many_ties(hs):
     assert np.array_equal(oracle.estimate(C, p, keys), est)
 
 
-def test_topk_after_reset_and_requery(hs, small):
+@pytest.mark.parametrize("search", list(SEARCH))
+def test_topk_after_reset_and_requery(hs, small, search):
     spec, xyz = small
-    sk, p = _pair(hs, 5, 16, spec.box, 0.1, 21)
+    sk, p = _pair(hs, 5, 16, spec.box, 0.1, 21, flags=SEARCH[search])
     sk.update(_dev(xyz[:500000]))
     k1 = sk.topk(200)
     k1b = sk.topk(200)
@@ -230,3 +237,36 @@ def test_topk_after_reset_and_requery(hs, small):
     keys, est = sk.topk(300)
     wk, we = oracle.topk_full(C, p, 300, nthreads=NT)
     assert np.array_equal(keys, wk) and np.array_equal(est, we)
+
+
+@pytest.mark.parametrize("search", ["scan", "directory"])
+def test_topk_heavy_ties_at_positive_threshold(hs, search):
+    # many cells share the k-th estimate (every occupied cell has count 3):
+    # the positive-threshold tie path must return the smallest keys among them
+    rng = np.random.default_rng(5)
+    sk, p = _pair(hs, 5, 20, 30.0, 0.1, 9, flags=SEARCH[search])
+    cells = rng.choice(300 ** 3, size=4000, replace=False)
+    cx, cy, cz = cells % 300, (cells // 300) % 300, cells // 90000
+    pts = (np.stack([cx, cy, cz], 1).astype(np.float64) * 0.1 + 0.05).astype(np.float32)
+    pts = np.repeat(pts, 3, axis=0)
+    sk.update(_dev(pts))
+    C = sk.counters()
+    keys, est = sk.topk(1500)
+    wk, we = oracle.topk_full(C, p, 1500, nthreads=NT)
+    assert np.array_equal(keys, wk) and np.array_equal(est, we)
+
+
+@pytest.mark.parametrize("search", list(SEARCH))
+def test_topk_overflow_tie_path_positive_threshold(hs, search):
+    # all counters 1: every estimate is +1 or -1 and about 8.4e6 of the 2^24
+    # cells tie at +1, more than the candidate buffer holds - the search must
+    # raise its threshold, fail to separate the ties, and take them in key order
+    sk, p = _pair(hs, 5, 16, 25.6, 0.1, 31, flags=SEARCH[search])
+    C = np.ones((5, 1 << 16), np.int32)
+    sk.load_counters(C)
+    keys, est = sk.topk(2000)
+    wk, we = oracle.topk_full(C, p, 2000, nthreads=NT)
+    assert np.array_equal(keys, wk) and np.array_equal(est, we)
+    assert (we == 1).all()
+    st = sk.stats()
+    assert st["last_passes"] >= 3
