@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="override the particle count")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-red", action="store_true", help="skip the L2 atomic-rate probe")
     ap.add_argument("--second-rate", type=float, default=0.1,
                     help="also time this sample rate (0 to skip)")
     return ap.parse_args()
@@ -202,6 +203,7 @@ def run_ours(args):
     def step(src, rate):
         hs.sketch_reset(sk.h)
         hs.sketch_update(sk.h, src, n, rate)
+        hs.sketch_flush(sk.h)
         return hs.topk_extract(sk.h, k, keys, ests)
 
     def barrier():
@@ -222,6 +224,7 @@ def run_ours(args):
             hs.sketch_reset(sk.h)
             a.record(stream)
             hs.sketch_update(sk.h, src, n, rate)
+            hs.sketch_flush(sk.h)
             b.record(stream)
             hs.topk_extract(sk.h, k, keys, ests)
             upd.append((a, b))
@@ -268,13 +271,15 @@ def run_ours(args):
                   "stream_frac": 12.0 * n / (u2avg * 1e-3) / 1e9 / hbm}
 
     red = None
-    try:
-        ops = hs.hs_measure_red_rate(WORKLOAD["rows"] << WORKLOAD["log2_width"], 1 << 31)
-        red = {"ops_per_s": ops, "table_counters": WORKLOAD["rows"] << WORKLOAD["log2_width"],
-               "needed_ops_per_particle": WORKLOAD["rows"] * args.rate,
-               "particles_per_s_bound": ops / (WORKLOAD["rows"] * args.rate)}
-    except hs.HSError as e:
-        red = {"error": str(e)}
+    if not args.no_red:
+        try:
+            tab = 1 << ((WORKLOAD["rows"] << WORKLOAD["log2_width"]) - 1).bit_length()
+            ops = hs.hs_measure_red_rate(tab, 1 << 31)
+            red = {"ops_per_s": ops, "table_counters": tab,
+                   "needed_ops_per_particle": WORKLOAD["rows"] * args.rate,
+                   "particles_per_s_bound": ops / (WORKLOAD["rows"] * args.rate)}
+        except hs.HSError as e:
+            red = {"error": str(e)}
 
     e2e = None
     if not args.no_e2e:
@@ -314,7 +319,8 @@ def run_ours(args):
                        "cell_mpc_h": WORKLOAD["cell"], "grid": G, "rows": WORKLOAD["rows"],
                        "width": 1 << WORKLOAD["log2_width"], "k": k, "sample_rate": args.rate,
                        "l2": "inputs (12 GB) larger than L2", "generation_s": gen_s},
-            "breakdown": {"update_ms": upd_avg, "topk_ms": topk_per_step,
+            "breakdown": {"update_ms": upd_avg, "flush_ms": st["flush_ms"] / args.steps,
+                          "topk_ms": topk_per_step,
                           "full_search_ms": search_per_step,
                           "stream_gbs": stream_gbs, "stream_frac": stream_gbs / hbm,
                           "candidates": st["last_candidates"], "threshold": st["last_threshold"],

@@ -70,9 +70,16 @@ typedef enum {
  * these flags force one (for testing; both give the same result). */
 #define HS_FLAG_SEARCH_SCAN 1u
 #define HS_FLAG_SEARCH_DIRECTORY 2u
+/* The update adds each kept particle's t counter increments either directly
+ * with global atomics or, for large calls, by binning them and accumulating
+ * each bin in shared memory (the bins are drained into the counters before
+ * any read of the counters); these flags force one (same counters). */
+#define HS_FLAG_UPDATE_DIRECT 4u
+#define HS_FLAG_UPDATE_BINNED 8u
 
 /* Sketch parameters.  rows in [1, 32]; log2_width in [1, 30]; box > 0 and
- * cell > 0 with 1 <= round(box / cell) <= 2^21; flags: 0 or one HS_FLAG_*. */
+ * cell > 0 with 1 <= round(box / cell) <= 2^21; flags: 0, or at most one
+ * HS_FLAG_SEARCH_* and at most one HS_FLAG_UPDATE_* value. */
 typedef struct {
     uint32_t rows;        /* t: number of independent rows (Sec. 2.2)         */
     uint32_t log2_width;  /* b = W = 2^log2_width counters per row            */
@@ -80,7 +87,7 @@ typedef struct {
     double cell;          /* mesh cell size (Sec. 2.1)                         */
     uint64_t hash_seed;   /* seeds the row hash functions                     */
     uint64_t sample_seed; /* seeds the sampling hash                          */
-    uint32_t flags;       /* 0 or one HS_FLAG_SEARCH_* value                  */
+    uint32_t flags;       /* HS_FLAG_* bits (0 = automatic choices)           */
     uint32_t reserved;    /* must be 0                                        */
 } hs_params;
 
@@ -107,6 +114,8 @@ typedef struct {
     uint64_t last_candidates;   /* candidates collected by the last query      */
     int32_t last_threshold;     /* pruning threshold of the last query's pass  */
     uint32_t last_passes;       /* full-search passes of the last query        */
+    uint64_t flush_launches;    /* launches accumulating binned increments     */
+    double flush_ms;            /* their summed device time (part of update_ms)*/
 } hs_stats;
 
 /*
@@ -175,6 +184,11 @@ hs_status sketch_merge(hs_sketch *dst, hs_sketch *src);
 
 /* Describe h. */
 hs_status sketch_info(const hs_sketch *h, hs_info *out);
+
+/* Apply binned, not yet accumulated increments to the counters (asynchronous
+ * on the handle's stream).  Every call that reads the counters does this
+ * itself; it is exposed so a caller can time the whole update. */
+hs_status sketch_flush(hs_sketch *h);
 
 /* Block until the handle's stream has finished its work. */
 hs_status sketch_synchronize(hs_sketch *h);

@@ -42,6 +42,9 @@ constexpr uint64_t kProbeCap = 1ull << 20;        // keys of the first 2^20 part
 constexpr uint32_t kProbeSlotsLog2 = 21;
 constexpr uint64_t kStageParticles = 1ull << 23;  // 96 MiB per staging buffer
 constexpr size_t kSearchSmemBudget = 192 * 1024;
+constexpr size_t kBinSmemBudget = 224 * 1024;
+constexpr uint64_t kBinBudgetBytes = 4ull << 30;   // global bins, at most
+constexpr double kBinnedMinUpdates = 1 << 20;      // smaller calls add directly
 
 struct EventPair {
     cudaEvent_t a, b;
@@ -102,9 +105,17 @@ struct hs_sketch {
     uint32_t *scan_scratch = nullptr;
     bool dir_failed = false;
 
+    // binned update: codes waiting in global bins until the next drain
+    BinLayout bl{};
+    uint16_t *bins = nullptr;
+    uint32_t *bin_cursor = nullptr;
+    uint32_t bin_cap = 0;
+    double pending = 0;          // kept particles binned since the last drain
+    double pending_limit = 0;    // drain before the expected bin load passes this
+
     // benchmarking
     hs_stats stats;
-    std::vector<EventPair> pending_update, pending_search, pool;
+    std::vector<EventPair> pending_update, pending_search, pending_flush, pool;
 };
 
 namespace {
@@ -129,11 +140,14 @@ hs_status check_params(const hs_params *p) {
     double g = std::llround(p->box / p->cell);
     if (g < 1 || g > (double)(1u << 21))
         return fail(HS_ERR_ARG, "grid round(box/cell)=%.0f outside [1, 2^21]", g);
-    if ((p->flags & ~(uint32_t)(HS_FLAG_SEARCH_SCAN | HS_FLAG_SEARCH_DIRECTORY)) != 0 ||
-        p->reserved != 0)
+    const uint32_t known = HS_FLAG_SEARCH_SCAN | HS_FLAG_SEARCH_DIRECTORY | HS_FLAG_UPDATE_DIRECT |
+                           HS_FLAG_UPDATE_BINNED;
+    if ((p->flags & ~known) != 0 || p->reserved != 0)
         return fail(HS_ERR_ARG, "unknown flags or reserved != 0");
     if ((p->flags & HS_FLAG_SEARCH_SCAN) && (p->flags & HS_FLAG_SEARCH_DIRECTORY))
         return fail(HS_ERR_ARG, "at most one search method may be forced");
+    if ((p->flags & HS_FLAG_UPDATE_DIRECT) && (p->flags & HS_FLAG_UPDATE_BINNED))
+        return fail(HS_ERR_ARG, "at most one update method may be forced");
     return HS_OK;
 }
 
@@ -163,6 +177,15 @@ void drain_timings(hs_sketch *h) {
         h->pool.push_back(e);
     }
     h->pending_search.clear();
+    for (auto &e : h->pending_flush) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) {
+            h->stats.flush_ms += ms;
+            h->stats.update_ms += ms;
+        }
+        h->pool.push_back(e);
+    }
+    h->pending_flush.clear();
     cudaGetLastError();
 }
 
@@ -304,8 +327,92 @@ hs_status ensure_query_scratch(hs_sketch *h, uint64_t m) {
     return HS_OK;
 }
 
+hs_status launch_update_direct(hs_sketch *h, const float *xyz, uint64_t n, uint64_t g0,
+                               double rate);
+
+// add every binned code to the counters (before anything reads them)
+hs_status drain(hs_sketch *h) {
+    if (h->pending <= 0) return HS_OK;
+    EventPair ev = take_events(h);
+    cudaEventRecord(ev.a, h->stream);
+    HS_CUDA(launch_bin_accumulate(h->bl, h->bins, h->bin_cursor, h->bin_cap, h->C, h->stream));
+    cudaEventRecord(ev.b, h->stream);
+    h->pending_flush.push_back(ev);
+    h->stats.kernel_launches += 1;
+    h->stats.flush_launches += 1;
+    h->pending = 0;
+    return HS_OK;
+}
+
+// drop binned codes that were never drained (reset / load)
+hs_status discard_pending(hs_sketch *h) {
+    if (h->pending > 0 && h->bin_cursor)
+        HS_CUDA(cudaMemsetAsync(h->bin_cursor, 0, (size_t)h->bl.nbins * 4, h->stream));
+    h->pending = 0;
+    return HS_OK;
+}
+
+bool want_binned(hs_sketch *h, uint64_t n, double rate) {
+    if (h->p.flags & HS_FLAG_UPDATE_DIRECT) return false;
+    if (h->bl.slot == 0) return false;
+    if (h->p.flags & HS_FLAG_UPDATE_BINNED) return true;
+    return (double)n * rate * h->d.rows >= kBinnedMinUpdates;
+}
+
+hs_status ensure_bins(hs_sketch *h, uint64_t n, double rate) {
+    if (h->bins) return HS_OK;
+    const double per_bin = (double)(1ull << (h->d.log2w - h->bl.S));   // bins per row
+    uint64_t want = (uint64_t)(1.3 * (double)n * rate / per_bin) + 8192;
+    uint64_t most = kBinBudgetBytes / (2ull * h->bl.nbins);
+    uint64_t cap = std::min(want, most);
+    cap = std::max<uint64_t>(cap, 4096);
+    cap = std::min<uint64_t>(cap, 0xFFFFFFF0ull);
+    cap = (cap + 15) & ~15ull;
+    HS_CUDA(cudaMalloc(&h->bins, (size_t)h->bl.nbins * cap * 2));
+    HS_CUDA(cudaMalloc(&h->bin_cursor, (size_t)h->bl.nbins * 4));
+    HS_CUDA(cudaMemsetAsync(h->bin_cursor, 0, (size_t)h->bl.nbins * 4, h->stream));
+    h->bin_cap = (uint32_t)cap;
+    // expected codes per bin = kept particles / bins per row; keep a margin of
+    // 20 % and 6 standard deviations below the capacity
+    double c = (double)cap;
+    double safe = c - 6.0 * std::sqrt(c) - 4096.0;
+    h->pending_limit = std::max(0.0, 0.8 * safe) * per_bin;
+    return HS_OK;
+}
+
 hs_status launch_update_timed(hs_sketch *h, const float *xyz, uint64_t n, uint64_t g0,
                               double rate) {
+    if (want_binned(h, n, rate)) {
+        hs_status st = ensure_bins(h, n, rate);
+        if (st != HS_OK) return st;
+        if (h->pending_limit >= 1.0) {
+            // launches small enough that no bin is expected to fill
+            uint64_t piece = (uint64_t)std::max(1.0, h->pending_limit / rate);
+            for (uint64_t off = 0; off < n; off += piece) {
+                uint64_t cnt = std::min(piece, n - off);
+                if (h->pending + (double)cnt * rate > h->pending_limit) {
+                    st = drain(h);
+                    if (st != HS_OK) return st;
+                }
+                EventPair ev = take_events(h);
+                cudaEventRecord(ev.a, h->stream);
+                HS_CUDA(launch_bin_scatter(xyz + 3 * off, cnt, g0 + off, h->d, h->C, rate,
+                                           h->p.sample_seed, h->probe, kProbeCap, h->bl, h->bins,
+                                           h->bin_cursor, h->bin_cap, h->num_sms, h->stream));
+                cudaEventRecord(ev.b, h->stream);
+                h->pending_update.push_back(ev);
+                h->pending += (double)cnt * rate;
+                h->stats.update_launches += 1;
+                h->stats.kernel_launches += 1;
+            }
+            return HS_OK;
+        }
+    }
+    return launch_update_direct(h, xyz, n, g0, rate);
+}
+
+hs_status launch_update_direct(hs_sketch *h, const float *xyz, uint64_t n, uint64_t g0,
+                               double rate) {
     EventPair ev = take_events(h);
     cudaEventRecord(ev.a, h->stream);
     HS_CUDA(launch_update(xyz, n, g0, h->d, h->C, rate, h->p.sample_seed, h->probe, kProbeCap, 0,
@@ -475,6 +582,7 @@ hs_status sketch_create(const hs_params *params, void *cuda_stream, hs_sketch **
         d.seed[r].b = splitmix64_at(params->hash_seed, 4 * r + 3);
     }
     h->n_cells = (uint64_t)d.G * d.G * d.G;
+    h->bl = bin_layout(d, kBinSmemBudget);
     h->key_bits = 1;
     while (h->key_bits < 64 && (1ull << h->key_bits) < h->n_cells) ++h->key_bits;
     cudaError_t e = cudaGetDevice(&h->device);
@@ -499,6 +607,8 @@ hs_status sketch_destroy(hs_sketch *h) {
     cudaStreamSynchronize(h->stream);
     free_topk_scratch(h);
     free_dir(h);
+    if (h->bins) cudaFree(h->bins);
+    if (h->bin_cursor) cudaFree(h->bin_cursor);
     if (h->C) cudaFree(h->C);
     if (h->probe) cudaFree(h->probe);
     if (h->q_keys) cudaFree(h->q_keys);
@@ -510,7 +620,7 @@ hs_status sketch_destroy(hs_sketch *h) {
         if (h->ev_free[i]) cudaEventDestroy(h->ev_free[i]);
     }
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
-    for (auto *v : {&h->pending_update, &h->pending_search, &h->pool})
+    for (auto *v : {&h->pending_update, &h->pending_search, &h->pending_flush, &h->pool})
         for (auto &e : *v) {
             cudaEventDestroy(e.a);
             cudaEventDestroy(e.b);
@@ -556,7 +666,9 @@ hs_status sketch_query(hs_sketch *h, const uint64_t *keys, uint64_t m, int32_t *
     if (m == 0) return HS_OK;
     if (!keys || !est) return fail(HS_ERR_ARG, "keys/est is NULL");
     bool kd = is_device_ptr(keys), ed = is_device_ptr(est);
-    hs_status st = ensure_query_scratch(h, (kd && ed) ? 0 : m);
+    hs_status st = drain(h);
+    if (st != HS_OK) return st;
+    st = ensure_query_scratch(h, (kd && ed) ? 0 : m);
     if (st != HS_OK) return st;
     const uint64_t *dk = keys;
     int32_t *de = est;
@@ -580,7 +692,9 @@ hs_status topk_extract(hs_sketch *h, uint32_t k, uint64_t *keys, int32_t *est, u
     if (!h) return fail(HS_ERR_ARG, "handle is NULL");
     if (k == 0 || !keys || !est || !n_out) return fail(HS_ERR_ARG, "k == 0 or NULL output");
     const uint64_t kk = std::min<uint64_t>(k, h->n_cells);
-    hs_status st = ensure_topk_scratch(h, kk);
+    hs_status st = drain(h);
+    if (st != HS_OK) return st;
+    st = ensure_topk_scratch(h, kk);
     if (st != HS_OK) return st;
     h->stats.last_passes = 0;
     EventPair whole = take_events(h);
@@ -680,6 +794,8 @@ hs_status topk_extract(hs_sketch *h, uint32_t k, uint64_t *keys, int32_t *est, u
 
 hs_status sketch_reset(hs_sketch *h) {
     if (!h) return fail(HS_ERR_ARG, "handle is NULL");
+    hs_status st = discard_pending(h);
+    if (st != HS_OK) return st;
     HS_CUDA(cudaMemsetAsync(h->C, 0, (size_t)h->d.rows * h->d.W * 4, h->stream));
     HS_CUDA(cudaMemsetAsync(h->probe, 0xFF, kProbeCap * 8, h->stream));
     h->n_seen = 0;
@@ -688,6 +804,8 @@ hs_status sketch_reset(hs_sketch *h) {
 
 hs_status sketch_counters(hs_sketch *h, int32_t *out) {
     if (!h || !out) return fail(HS_ERR_ARG, "NULL argument");
+    hs_status st = drain(h);
+    if (st != HS_OK) return st;
     HS_CUDA(cudaMemcpyAsync(out, h->C, (size_t)h->d.rows * h->d.W * 4, cudaMemcpyDefault,
                             h->stream));
     HS_CUDA(cudaStreamSynchronize(h->stream));
@@ -696,6 +814,8 @@ hs_status sketch_counters(hs_sketch *h, int32_t *out) {
 
 hs_status sketch_load_counters(hs_sketch *h, const int32_t *in) {
     if (!h || !in) return fail(HS_ERR_ARG, "NULL argument");
+    hs_status st = discard_pending(h);
+    if (st != HS_OK) return st;
     HS_CUDA(cudaMemcpyAsync(h->C, in, (size_t)h->d.rows * h->d.W * 4, cudaMemcpyDefault,
                             h->stream));
     HS_CUDA(cudaStreamSynchronize(h->stream));
@@ -709,6 +829,9 @@ hs_status sketch_merge(hs_sketch *dst, hs_sketch *src) {
         dst->d.G != src->d.G || dst->d.inv_cell != src->d.inv_cell)
         return fail(HS_ERR_ARG, "sketches were built with different parameters");
     if (dst == src) return fail(HS_ERR_ARG, "cannot merge a sketch into itself");
+    hs_status st = drain(src);
+    if (st == HS_OK) st = drain(dst);
+    if (st != HS_OK) return st;
     cudaEvent_t ev;
     HS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     HS_CUDA(cudaEventRecord(ev, src->stream));
@@ -730,6 +853,11 @@ hs_status sketch_info(const hs_sketch *h, hs_info *out) {
     out->n_cells = h->n_cells;
     out->n_seen = h->n_seen;
     return HS_OK;
+}
+
+hs_status sketch_flush(hs_sketch *h) {
+    if (!h) return fail(HS_ERR_ARG, "handle is NULL");
+    return drain(h);
 }
 
 hs_status sketch_synchronize(hs_sketch *h) {

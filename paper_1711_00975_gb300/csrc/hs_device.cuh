@@ -46,10 +46,32 @@ __device__ __forceinline__ uint64_t mul_lo64(uint64_t a, uint32_t x) {
     return lo + ((uint64_t)hi << 32);
 }
 
+// c + a * b with a 64-bit accumulator in one wide multiply-add.
+__device__ __forceinline__ uint64_t mad_wide(uint32_t a, uint32_t b, uint64_t c) {
+    uint64_t d;
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+    return d;
+}
+
+// High 32 bits of v = (a0*cx + a1*cy + a2*cz + b) mod 2^64: the low halves of
+// the multipliers go through a 64-bit multiply-add chain starting at b; the
+// high halves only reach the top word, so they add in 32-bit arithmetic.
+__device__ __forceinline__ uint32_t row_value_hi(const RowSeed &s, uint32_t cx, uint32_t cy,
+                                                 uint32_t cz, uint32_t &lo) {
+    uint64_t acc = mad_wide((uint32_t)s.a0, cx, s.b);
+    acc = mad_wide((uint32_t)s.a1, cy, acc);
+    acc = mad_wide((uint32_t)s.a2, cz, acc);
+    lo = (uint32_t)acc;
+    return (uint32_t)(acc >> 32) + (uint32_t)(s.a0 >> 32) * cx + (uint32_t)(s.a1 >> 32) * cy +
+           (uint32_t)(s.a2 >> 32) * cz;
+}
+
 // v = (a0*cx + a1*cy + a2*cz + b) mod 2^64 (vector multiply-shift before the shift)
 __device__ __forceinline__ uint64_t row_value(const RowSeed &s, uint32_t cx, uint32_t cy,
                                               uint32_t cz) {
-    return s.b + mul_lo64(s.a0, cx) + mul_lo64(s.a1, cy) + mul_lo64(s.a2, cz);
+    uint32_t lo;
+    uint32_t hi = row_value_hi(s, cx, cy, cz, lo);
+    return ((uint64_t)hi << 32) | lo;
 }
 
 __device__ __forceinline__ uint32_t bucket_of(uint64_t v, uint32_t log2w) {
@@ -67,20 +89,22 @@ __device__ __forceinline__ int32_t signed_count(int32_t c, uint64_t v, uint32_t 
     return ((v >> (63 - log2w)) & 1ull) ? (int32_t)(0u - u) : (int32_t)u;
 }
 
-// One axis of the mesh reduction: floor(fl32(x * inv)) reduced into [0, G).
-// Returns false when the scaled coordinate is not a finite value in [-2^31, 2^31).
-__device__ __forceinline__ bool axis_cell(float x, float inv, uint32_t G, uint32_t &c) {
-    float p = __fmul_rn(x, inv);
-    float f = floorf(p);
-    if (!(f >= -2147483648.0f && f < 2147483648.0f)) return false;
-    int i = (int)f;
-    if ((unsigned)i < G) {
-        c = (uint32_t)i;
-        return true;
-    }
+// Periodic reduction of a cell index outside [0, G) (rare: only particles
+// outside the box); kept out of line so the common path stays short.
+static __device__ __noinline__ uint32_t wrap_cell(int i, uint32_t G) {
     int m = i % (int)G;
     if (m < 0) m += (int)G;
-    c = (uint32_t)m;
+    return (uint32_t)m;
+}
+
+// One axis of the mesh reduction: floor(fl32(x * inv)) reduced into [0, G).
+// Returns false when the scaled coordinate is not a finite value in
+// [-2^31, 2^31) (then floor(p) is outside int32 or p is NaN/inf).
+__device__ __forceinline__ bool axis_cell(float x, float inv, uint32_t G, uint32_t &c) {
+    float p = __fmul_rn(x, inv);
+    if (!(p >= -2147483648.0f && p < 2147483648.0f)) return false;
+    int i = __float2int_rd(p);      // floor, exact for p in range
+    c = (unsigned)i < G ? (uint32_t)i : wrap_cell(i, G);
     return true;
 }
 

@@ -13,6 +13,21 @@ cudaError_t launch_update(const float *xyz, uint64_t n, uint64_t g0, const Sketc
                           int32_t *C, double rate, uint64_t sample_seed, uint64_t *probe,
                           uint64_t probe_cap, uint32_t band_lo, uint32_t band_hi, int max_blocks,
                           cudaStream_t s);
+// ---- update mode with shared-memory accumulation (k_binned.cu) ----
+struct BinLayout {
+    uint32_t S;        // log2 counters per bin
+    uint32_t nbins;    // rows * W / 2^S
+    uint32_t slot;     // shared-memory staging entries per bin (0: binning unavailable)
+    size_t smem;       // dynamic shared memory of the scatter kernel
+};
+BinLayout bin_layout(const SketchDesc &d, size_t smem_budget);
+cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const SketchDesc &d,
+                               int32_t *C, double rate, uint64_t sample_seed, uint64_t *probe,
+                               uint64_t probe_cap, const BinLayout &L, uint16_t *bins,
+                               uint32_t *cursor, uint32_t cap, int blocks, cudaStream_t s);
+cudaError_t launch_bin_accumulate(const BinLayout &L, uint16_t *bins, uint32_t *cursor,
+                                  uint32_t cap, int32_t *C, cudaStream_t s);
+
 // dst[i] += src[i] (int32 wrap-around), the merge of two sketches
 cudaError_t launch_add_counters(int32_t *dst, const int32_t *src, uint64_t n, cudaStream_t s);
 cudaError_t launch_red_rate(uint32_t *table, uint64_t n_counters, uint64_t ops_per_thread,

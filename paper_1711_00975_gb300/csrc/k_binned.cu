@@ -1,0 +1,439 @@
+// k_binned.cu - update mode with shared-memory accumulation (Add of
+// arXiv:1711.00975 Sec. 2.2 applied to every kept particle of the stream).
+//
+// The paper notes that the random counter updates become the bottleneck once
+// hashing runs on the GPU (Sec. 3.1, "CPU + hashes on GPU").  On GB300 one
+// random 32-bit add resolves in L2 at about 2e11/s (less once the sketch is
+// larger than L2), well below the particle stream's HBM rate.  So the update
+// is split in two passes over compact 16-bit codes:
+//
+//  1. scatter: read the particles once; for each kept particle and row, the
+//     flat counter index i = r*W + bucket is split into bin = i >> S and a code
+//     ((i mod 2^S) << 1 | sign bit).  Codes are write-combined per bin in
+//     shared memory and flushed to the bin's global array in 32-byte units.
+//  2. accumulate: one block per bin adds its codes into 2^S shared-memory
+//     counters with shared atomics, then adds them to the bin's counter range.
+//
+// Integer addition commutes, so the counters equal those of the direct update
+// bit for bit.  Whatever does not fit - a full shared-memory buffer or a full
+// global bin - is added directly with a global atomic, so nothing is dropped.
+#include "hs_device.cuh"
+#include "hs_kernels.h"
+
+namespace hs {
+
+namespace {
+
+struct ScatterArgs {
+    uint64_t n;
+    uint64_t g0;
+    uint64_t thr;
+    uint64_t sample_seed;
+    uint64_t *probe;
+    uint64_t probe_cap;
+    uint32_t keep_all;
+    uint32_t S;           // log2 of counters per bin
+    uint32_t nbins;
+    uint32_t slot;        // shared-memory entries per bin (power of two)
+    uint32_t unit;        // flush granule (entries), slot / 2
+    uint32_t cap;         // global entries per bin
+    uint32_t hshift;      // 31 - log2W: top log2W+1 bits of v = bucket and sign bit
+    uint32_t code_mask;   // 2^(S+1) - 1
+    uint32_t bins_per_row;
+    uint32_t log2_slot;
+    uint16_t *bins;       // nbins x cap codes
+    uint32_t *cursor;     // fill of each global bin (may exceed cap)
+};
+
+__device__ __noinline__ void direct_add(uint32_t *C, const ScatterArgs &a, uint32_t bin,
+                                        uint16_t code) {
+    uint64_t idx = ((uint64_t)bin << a.S) | (uint64_t)(code >> 1);
+    atomicAdd(&C[idx], (code & 1) ? 0xFFFFFFFFu : 1u);
+}
+
+// Bin and code of row r for cell (cx, cy, cz).  The top 32 bits of
+// v = a0*cx + a1*cy + a2*cz + b (mod 2^64) are the high word of
+// b + lo(a0)*cx + lo(a1)*cy + lo(a2)*cz plus hi(a0)*cx + hi(a1)*cy + hi(a2)*cz
+// (mod 2^32): three wide multiply-adds and three narrow ones.  Its top
+// log2W + 1 bits h are (bucket << 1 | sign bit); the flat counter index is
+// r*W + bucket, so bin = r * (W / 2^S) + (h >> (S + 1)) and code = h mod 2^(S+1).
+__device__ __forceinline__ void bin_code(const RowSeed &sd, uint32_t cx, uint32_t cy, uint32_t cz,
+                                         uint32_t r, const ScatterArgs &a, uint32_t &bin,
+                                         uint32_t &code) {
+    uint32_t lo;
+    uint32_t h = row_value_hi(sd, cx, cy, cz, lo) >> a.hshift;
+    code = h & a.code_mask;
+    bin = (h >> (a.S + 1)) + r * a.bins_per_row;
+}
+
+__device__ __noinline__ void write_probe(uint64_t *probe, uint64_t g, bool valid, uint32_t cx,
+                                         uint32_t cy, uint32_t cz, uint32_t G) {
+    probe[g] = valid ? key_of(cx, cy, cz, G) : kInvalidKey;
+}
+
+// Mesh reduction, sampling and probe entry of one particle; true when it is
+// kept, with its cell packed as cx | cy << 21 | cz << 42 (G <= 2^21).
+__device__ __forceinline__ bool prep_particle(float x, float y, float z, uint64_t g,
+                                              const SketchDesc &d, const ScatterArgs &a,
+                                              uint64_t &cell) {
+    bool keep = a.keep_all || splitmix64_at(a.sample_seed, g) < a.thr;
+    uint32_t cx = 0, cy = 0, cz = 0;
+    bool valid = axis_cell(x, d.inv_cell, d.G, cx);
+    valid &= axis_cell(y, d.inv_cell, d.G, cy);
+    valid &= axis_cell(z, d.inv_cell, d.G, cz);
+    if (g < a.probe_cap) write_probe(a.probe, g, valid, cx, cy, cz, d.G);
+    cell = (uint64_t)cx | ((uint64_t)cy << 21) | ((uint64_t)cz << 42);
+    return keep && valid;
+}
+
+// Shared-memory staging of bin b: a ring of `slot` (32) codes.  s_fill[b]
+// packs the ring's rotation (high 16 bits) and the number of codes staged
+// since its last flush (low 16 bits), so one shared atomic returns both.  Code
+// number j sits at ring position (j + rot) mod slot; the initial rotations
+// differ between bins, which spreads concurrent stores over the banks, and a
+// flush of the first half advances the rotation instead of moving the rest.
+// The lane that stages code number unit-1 (the first full half) marks the bin
+// due in a bitmap (a fire-and-forget shared atomic on a random word).
+__device__ __forceinline__ void stage_one(uint32_t bin, uint32_t code, const ScatterArgs &a,
+                                          uint32_t w, uint16_t *s_buf, uint32_t *s_due,
+                                          uint32_t *C) {
+    const uint32_t slot = w & 0xFFFFu, rot = w >> 16;
+    if (slot < a.slot) {
+        s_buf[(bin << a.log2_slot) + ((slot + rot) & (a.slot - 1))] = (uint16_t)code;
+        if (slot == a.unit - 1) atomicOr(&s_due[bin >> 5], 1u << (bin & 31));
+    } else {
+        direct_add(C, a, bin, (uint16_t)code);
+    }
+}
+
+template <int T>
+__device__ __forceinline__ void stage_cell(uint64_t cell, const SketchDesc &d, const ScatterArgs &a,
+                                           uint32_t *s_fill, uint16_t *s_buf, uint32_t *s_due,
+                                           uint32_t *C) {
+    const uint32_t cx = (uint32_t)(cell & 0x1FFFFF), cy = (uint32_t)((cell >> 21) & 0x1FFFFF),
+                   cz = (uint32_t)(cell >> 42);
+    if (T > 0) {
+        uint32_t bin[T > 0 ? T : 1], code[T > 0 ? T : 1], w[T > 0 ? T : 1];
+#pragma unroll
+        for (int r = 0; r < T; ++r) bin_code(d.seed[r], cx, cy, cz, (uint32_t)r, a, bin[r], code[r]);
+#pragma unroll
+        for (int r = 0; r < T; ++r) w[r] = atomicAdd(&s_fill[bin[r]], 1u);
+#pragma unroll
+        for (int r = 0; r < T; ++r) stage_one(bin[r], code[r], a, w[r], s_buf, s_due, C);
+    } else {
+        for (uint32_t r = 0; r < d.rows; ++r) {
+            uint32_t bin, code;
+            bin_code(d.seed[r], cx, cy, cz, r, a, bin, code);
+            stage_one(bin, code, a, atomicAdd(&s_fill[bin], 1u), s_buf, s_due, C);
+        }
+    }
+}
+
+// Copy `cnt` (a multiple of 8) codes of a bin's ring, starting at even ring
+// position p0, to global memory at position g of the bin's array.
+__device__ __forceinline__ void flush_ring(uint32_t *C, const ScatterArgs &a, uint32_t bin,
+                                           const uint16_t *ring, uint32_t p0, uint32_t cnt,
+                                           uint32_t g) {
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(ring);
+    const uint32_t wmask = (a.slot >> 1) - 1;
+    uint16_t *dst = a.bins + (uint64_t)bin * a.cap;
+    const bool fits = g < a.cap && cnt <= a.cap - g;
+    const bool aligned = (reinterpret_cast<uintptr_t>(dst + g) & 15u) == 0;
+    if (fits && aligned) {
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst + g);
+        for (uint32_t j = 0; j < cnt / 8; ++j) {
+            uint32_t q0 = (p0 >> 1) + 4 * j;
+            d4[j] = make_uint4(w[q0 & wmask], w[(q0 + 1) & wmask], w[(q0 + 2) & wmask],
+                               w[(q0 + 3) & wmask]);
+        }
+    } else {
+        for (uint32_t j = 0; j < cnt; ++j) {
+            uint16_t c = ring[(p0 + j) & (a.slot - 1)];
+            if (g + j < a.cap) dst[g + j] = c;
+            else direct_add(C, a, bin, c);
+        }
+    }
+}
+
+#ifndef HS_SCATTER_THREADS
+#define HS_SCATTER_THREADS 1024
+#endif
+constexpr int kScatterThreads = HS_SCATTER_THREADS;
+constexpr int kQueuePerWarp = 128;     // 32 lanes x 4 particles
+
+// Up to kMaxFlushPerThread due-bitmap words per warp in the flush phase
+// (nbins <= kMaxFlushPerThread * 32 * warps per block).
+constexpr int kMaxFlushPerThread = 6;
+
+template <int T, bool VEC>
+__global__ void __launch_bounds__(kScatterThreads, 1)
+    k_bin_scatter(const float *__restrict__ xyz, const SketchDesc d, const ScatterArgs a,
+                  uint32_t *__restrict__ C) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t *s_fill = reinterpret_cast<uint32_t *>(smem);
+    const uint32_t fill_bytes = (a.nbins * 4 + 15) & ~15u;
+    uint16_t *s_buf = reinterpret_cast<uint16_t *>(smem + fill_bytes);
+    const uint32_t buf_bytes = (a.nbins * a.slot * 2 + 15) & ~15u;
+    uint64_t *s_queue = reinterpret_cast<uint64_t *>(smem + fill_bytes + buf_bytes);
+    uint32_t *s_due = reinterpret_cast<uint32_t *>(smem + fill_bytes + buf_bytes +
+                                                   (kScatterThreads / 32) * kQueuePerWarp * 8);
+    const uint32_t ndue = (a.nbins + 31) / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t *q = s_queue + warp * kQueuePerWarp;
+    for (uint32_t b = threadIdx.x; b < a.nbins; b += blockDim.x)
+        s_fill[b] = ((2u * (b >> 1)) & (a.slot - 1)) << 16;   // rotation, nothing staged
+    for (uint32_t i = threadIdx.x; i < ndue; i += blockDim.x) s_due[i] = 0;
+    __syncthreads();
+
+    // Tiles of 4 particles per thread (VEC: one 48-byte group as three float4,
+    // the next tile's group loaded before this one is processed).  Kept cells
+    // are compacted into a per-warp queue so the row updates run with every
+    // lane busy whatever the sample rate.
+    const uint64_t per_tile = (uint64_t)blockDim.x * 4;
+    const uint64_t ntiles = (a.n + per_tile - 1) / per_tile;
+    const uint64_t full_groups = a.n >> 2;
+    const float4 *p4 = reinterpret_cast<const float4 *>(xyz);
+    float4 nu = make_float4(0, 0, 0, 0), nv = nu, nw = nu;
+    uint64_t tile = blockIdx.x;
+    if (VEC && tile < ntiles) {
+        uint64_t g4 = tile * blockDim.x + threadIdx.x;
+        if (g4 < full_groups) {
+            nu = __ldcs(p4 + 3 * g4);
+            nv = __ldcs(p4 + 3 * g4 + 1);
+            nw = __ldcs(p4 + 3 * g4 + 2);
+        }
+    }
+    const unsigned lt = (1u << lane) - 1u;
+    for (; tile < ntiles; tile += gridDim.x) {
+        uint64_t cell[4];
+        bool ok[4];
+        const uint64_t g4 = tile * blockDim.x + threadIdx.x;     // this thread's group
+        if (VEC) {
+            float4 u = nu, v = nv, w = nw;
+            const uint64_t gn = (tile + gridDim.x) * blockDim.x + threadIdx.x;
+            if (tile + gridDim.x < ntiles && gn < full_groups) {
+                nu = __ldcs(p4 + 3 * gn);
+                nv = __ldcs(p4 + 3 * gn + 1);
+                nw = __ldcs(p4 + 3 * gn + 2);
+            }
+            if (g4 < full_groups) {
+                uint64_t g = a.g0 + 4 * g4;
+                ok[0] = prep_particle(u.x, u.y, u.z, g, d, a, cell[0]);
+                ok[1] = prep_particle(u.w, v.x, v.y, g + 1, d, a, cell[1]);
+                ok[2] = prep_particle(v.z, v.w, w.x, g + 2, d, a, cell[2]);
+                ok[3] = prep_particle(w.y, w.z, w.w, g + 3, d, a, cell[3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    uint64_t i = 4 * g4 + j;
+                    ok[j] = i < a.n && prep_particle(__ldcs(xyz + 3 * i), __ldcs(xyz + 3 * i + 1),
+                                                     __ldcs(xyz + 3 * i + 2), a.g0 + i, d, a,
+                                                     cell[j]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                uint64_t i = 4 * g4 + j;
+                ok[j] = i < a.n && prep_particle(__ldcs(xyz + 3 * i), __ldcs(xyz + 3 * i + 1),
+                                                 __ldcs(xyz + 3 * i + 2), a.g0 + i, d, a, cell[j]);
+            }
+        }
+        if (__all_sync(0xFFFFFFFFu, ok[0] & ok[1] & ok[2] & ok[3])) {
+            // every particle of the warp is kept: stage straight from registers
+#pragma unroll
+            for (int j = 0; j < 4; ++j) stage_cell<T>(cell[j], d, a, s_fill, s_buf, s_due, C);
+        } else {
+            uint32_t nq = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                unsigned m = __ballot_sync(0xFFFFFFFFu, ok[j]);
+                if (ok[j]) q[nq + __popc(m & lt)] = cell[j];
+                nq += __popc(m);
+            }
+            __syncwarp();
+            for (uint32_t i = lane; i < nq; i += 32)
+                stage_cell<T>(q[i], d, a, s_fill, s_buf, s_due, C);
+        }
+        __syncthreads();
+        // flush the due bins: warp w reads due words w, w + nwarps, ... (one
+        // broadcast load each) and lane l flushes the bin of bit l.  All global
+        // reservations of a lane are issued before its copies.
+        const uint32_t nwarps = blockDim.x >> 5;
+        uint32_t wd[kMaxFlushPerThread], gp[kMaxFlushPerThread], nf[kMaxFlushPerThread];
+#pragma unroll
+        for (int k = 0; k < kMaxFlushPerThread; ++k) {
+            const uint32_t wi = warp + k * nwarps;
+            nf[k] = 0;
+            if (wi >= ndue) break;
+            const uint32_t bits = s_due[wi];
+            if ((bits >> lane) & 1u) {
+                const uint32_t b = wi * 32 + lane;
+                wd[k] = s_fill[b];
+                const uint32_t f = min(wd[k] & 0xFFFFu, a.slot);
+                nf[k] = f >= a.slot ? a.slot : a.unit;   // due: f >= unit
+                gp[k] = atomicAdd(&a.cursor[b], nf[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kMaxFlushPerThread; ++k) {
+            const uint32_t wi = warp + k * nwarps;
+            if (wi >= ndue) break;
+            if (nf[k]) {
+                const uint32_t b = wi * 32 + lane, rot = wd[k] >> 16;
+                const uint32_t f = min(wd[k] & 0xFFFFu, a.slot);
+                flush_ring(C, a, b, s_buf + (b << a.log2_slot), rot, nf[k], gp[k]);
+                s_fill[b] = (((rot + nf[k]) & (a.slot - 1)) << 16) | (f - nf[k]);
+            }
+            if (lane == 0) s_due[wi] = 0;
+        }
+        __syncthreads();
+    }
+    // what is left in shared memory
+    for (uint32_t b = threadIdx.x; b < a.nbins; b += blockDim.x) {
+        uint32_t w = s_fill[b];
+        uint32_t f = min(w & 0xFFFFu, a.slot);
+        if (f) {
+            const uint16_t *ring = s_buf + (b << a.log2_slot);
+            uint32_t g = atomicAdd(&a.cursor[b], f);
+            uint16_t *dst = a.bins + (uint64_t)b * a.cap;
+            for (uint32_t j = 0; j < f; ++j) {
+                uint16_t c = ring[((w >> 16) + j) & (a.slot - 1)];
+                if (g + j < a.cap) dst[g + j] = c;
+                else direct_add(C, a, b, c);
+            }
+        }
+    }
+}
+
+// one block per bin: shared-memory accumulation, then C[bin range] += acc
+__global__ void __launch_bounds__(1024)
+    k_bin_accumulate(const uint16_t *__restrict__ bins, uint32_t *__restrict__ cursor, uint32_t cap,
+                     uint32_t S, uint32_t *__restrict__ C) {
+    extern __shared__ __align__(16) int32_t acc[];
+    const uint32_t nacc = 1u << S;
+    const uint32_t bin = blockIdx.x;
+    for (uint32_t i = threadIdx.x; i < nacc; i += blockDim.x) acc[i] = 0;
+    __syncthreads();
+    const uint32_t len = min(cursor[bin], cap);
+    const uint16_t *src = bins + (uint64_t)bin * cap;
+    const uint32_t n8 = len / 8;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);   // cap is a multiple of 8
+    // eight 16-byte loads in flight per thread before the shared-memory adds
+    for (uint32_t j0 = 0; j0 < n8; j0 += 8 * blockDim.x) {
+        uint4 w[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            uint32_t j = j0 + u * blockDim.x + threadIdx.x;
+            w[u] = j < n8 ? __ldcs(s4 + j) : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu,
+                                                        0xFFFFFFFFu);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (j0 + u * blockDim.x + threadIdx.x >= n8) continue;
+            uint32_t ws[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t c0 = ws[q] & 0xFFFFu, c1 = ws[q] >> 16;
+                atomicAdd(&acc[c0 >> 1], (c0 & 1) ? -1 : 1);
+                atomicAdd(&acc[c1 >> 1], (c1 & 1) ? -1 : 1);
+            }
+        }
+    }
+    for (uint32_t j = n8 * 8 + threadIdx.x; j < len; j += blockDim.x) {
+        uint32_t c = src[j];
+        atomicAdd(&acc[c >> 1], (c & 1) ? -1 : 1);
+    }
+    __syncthreads();
+    uint32_t *dst = C + ((uint64_t)bin << S);
+    for (uint32_t i = threadIdx.x; i < nacc; i += blockDim.x) {
+        int32_t v = acc[i];
+        if (v) dst[i] += (uint32_t)v;
+    }
+    if (threadIdx.x == 0) cursor[bin] = 0;
+}
+
+}  // namespace
+
+BinLayout bin_layout(const SketchDesc &d, size_t smem_budget) {
+    BinLayout L{};
+    L.S = d.log2w < 15 ? d.log2w : 15;
+    uint64_t nb = (uint64_t)d.rows << (d.log2w - L.S);
+    L.nbins = (uint32_t)nb;
+    L.slot = 0;
+    const size_t queue = (size_t)(kScatterThreads / 32) * kQueuePerWarp * 8;
+    for (uint32_t slot = 32; slot >= 16; slot >>= 1) {
+        size_t need = ((nb * 4 + 15) & ~15ull) + ((nb * slot * 2 + 15) & ~15ull) + queue +
+                      ((nb + 31) / 32) * 4;
+        // flush phase: each warp covers at most kMaxFlushPerThread due words
+        if (nb <= (uint64_t)kMaxFlushPerThread * kScatterThreads && need <= smem_budget) {
+            L.slot = slot;
+            L.smem = need;
+            break;
+        }
+    }
+    return L;
+}
+
+cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const SketchDesc &d,
+                               int32_t *C, double rate, uint64_t sample_seed, uint64_t *probe,
+                               uint64_t probe_cap, const BinLayout &L, uint16_t *bins,
+                               uint32_t *cursor, uint32_t cap, int blocks, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    // bin arrays are read and written as 16-byte vectors: every bin must start
+    // on a 16-byte boundary
+    if ((cap & 7u) != 0 || (reinterpret_cast<uintptr_t>(bins) & 15u) != 0 || L.slot == 0)
+        return cudaErrorInvalidValue;
+    ScatterArgs a;
+    a.n = n;
+    a.g0 = g0;
+    a.keep_all = rate >= 1.0 ? 1u : 0u;
+    a.thr = rate >= 1.0 ? 0 : (uint64_t)ldexp(rate, 64);
+    a.sample_seed = sample_seed;
+    a.probe = probe;
+    a.probe_cap = probe ? probe_cap : 0;
+    a.S = L.S;
+    a.nbins = L.nbins;
+    a.slot = L.slot;
+    a.unit = L.slot / 2;
+    a.cap = cap;
+    a.hshift = 31 - d.log2w;
+    a.code_mask = (2u << L.S) - 1u;
+    a.bins_per_row = 1u << (d.log2w - L.S);
+    a.log2_slot = 0;
+    while ((1u << a.log2_slot) < L.slot) ++a.log2_slot;
+    a.bins = bins;
+    a.cursor = cursor;
+    uint32_t *Cu = reinterpret_cast<uint32_t *>(C);
+    const int threads = kScatterThreads;
+    bool vec = (reinterpret_cast<uintptr_t>(xyz) & 15u) == 0;
+    uint64_t per_tile = (uint64_t)threads * 4;
+    uint64_t need_blocks = (n + per_tile - 1) / per_tile;
+    if (need_blocks < (uint64_t)blocks) blocks = (int)need_blocks;
+    if (blocks < 1) blocks = 1;
+    auto launch = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+        kern<<<blocks, threads, L.smem, s>>>(xyz, d, a, Cu);
+    };
+    if (d.rows == 5) {
+        if (vec) launch(k_bin_scatter<5, true>);
+        else launch(k_bin_scatter<5, false>);
+    } else {
+        if (vec) launch(k_bin_scatter<0, true>);
+        else launch(k_bin_scatter<0, false>);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_accumulate(const BinLayout &L, uint16_t *bins, uint32_t *cursor,
+                                  uint32_t cap, int32_t *C, cudaStream_t s) {
+    if ((cap & 7u) != 0 || (reinterpret_cast<uintptr_t>(bins) & 15u) != 0)
+        return cudaErrorInvalidValue;
+    size_t smem = (size_t)4 << L.S;
+    cudaFuncSetAttribute(k_bin_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_bin_accumulate<<<L.nbins, 1024, smem, s>>>(bins, cursor, cap, L.S,
+                                                reinterpret_cast<uint32_t *>(C));
+    return cudaGetLastError();
+}
+
+}  // namespace hs

@@ -18,6 +18,8 @@ _lib = None
 
 HS_FLAG_SEARCH_SCAN = 1
 HS_FLAG_SEARCH_DIRECTORY = 2
+HS_FLAG_UPDATE_DIRECT = 4
+HS_FLAG_UPDATE_BINNED = 8
 
 HS_OK, HS_ERR_ARG, HS_ERR_CUDA, HS_ERR_OOM, HS_ERR_TABLE_FULL, HS_ERR_TIMEOUT, HS_ERR_STATE = range(7)
 _NAMES = ["HS_OK", "HS_ERR_ARG", "HS_ERR_CUDA", "HS_ERR_OOM", "HS_ERR_TABLE_FULL",
@@ -49,7 +51,8 @@ class hs_stats(ctypes.Structure):
                 ("update_ms", ctypes.c_double), ("search_launches", ctypes.c_uint64),
                 ("search_ms", ctypes.c_double), ("topk_ms", ctypes.c_double),
                 ("topk_calls", ctypes.c_uint64), ("last_candidates", ctypes.c_uint64),
-                ("last_threshold", ctypes.c_int32), ("last_passes", ctypes.c_uint32)]
+                ("last_threshold", ctypes.c_int32), ("last_passes", ctypes.c_uint32),
+                ("flush_launches", ctypes.c_uint64), ("flush_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -86,6 +89,7 @@ def lib():
                 "sketch_merge": [vp, vp],
                 "sketch_info": [vp, ctypes.POINTER(hs_info)],
                 "sketch_synchronize": [vp],
+                "sketch_flush": [vp],
                 "sketch_stats": [vp, ctypes.POINTER(hs_stats), ci],
                 "hs_measure_red_rate": [u64, u64, ctypes.POINTER(f64)],
             }
@@ -183,6 +187,10 @@ def sketch_info(h) -> hs_info:
     return info
 
 
+def sketch_flush(h) -> None:
+    _check(lib().sketch_flush(h), "sketch_flush")
+
+
 def sketch_synchronize(h) -> None:
     _check(lib().sketch_synchronize(h), "sketch_synchronize")
 
@@ -267,3 +275,6 @@ class Sketch:
 
     def synchronize(self):
         sketch_synchronize(self.h)
+
+    def flush(self):
+        sketch_flush(self.h)

@@ -30,6 +30,7 @@ def small():
 
 
 SEARCH = {"auto": 0, "scan": 1, "directory": 2}
+UPDATE = {"auto": 0, "direct": 4, "binned": 8}
 
 
 def _pair(hs, rows, log2w, box, cell, hash_seed, sample_seed=0, flags=0):
@@ -45,20 +46,22 @@ def _dev(x):
 # ---------------------------------------------------------------- update mode
 
 @pytest.mark.parametrize("rate", [1.0, 0.1, 1.0 / 16])
-def test_update_small_box_bitexact(hs, small, rate):
+@pytest.mark.parametrize("update", list(UPDATE))
+def test_update_small_box_bitexact(hs, small, rate, update):
     spec, xyz = small
-    sk, p = _pair(hs, 5, 16, spec.box, 0.1, 11, 22)
+    sk, p = _pair(hs, 5, 16, spec.box, 0.1, 11, 22, flags=UPDATE[update])
     sk.update(_dev(xyz), rate=rate)
     want = oracle.sketch_update(oracle.new_counters(p), p, xyz, rate=rate, nthreads=NT)
     assert np.array_equal(sk.counters(), want)
     assert sk.info().n_seen == len(xyz)
 
 
-def test_update_ragged_calls_and_alignment(hs, small):
+@pytest.mark.parametrize("update", list(UPDATE))
+def test_update_ragged_calls_and_alignment(hs, small, update):
     # uneven call sizes keep the global particle index running across calls;
     # the 1-particle offsets give 12-byte (unaligned) starts
     spec, xyz = small
-    sk, p = _pair(hs, 5, 12, spec.box, 0.1, 5, 9)
+    sk, p = _pair(hs, 5, 12, spec.box, 0.1, 5, 9, flags=UPDATE[update])
     d = _dev(xyz)
     sizes = [0, 1, 3, 4, 5, 1023, 100003, 7, 64, 250001]
     off = 0
@@ -82,17 +85,19 @@ def test_update_from_host_buffers(hs, small):
     assert np.array_equal(sk.counters(), want)
 
 
-@pytest.mark.parametrize("rows,log2w", [(1, 10), (3, 14), (4, 8), (7, 18), (32, 6)])
-def test_update_other_shapes(hs, small, rows, log2w):
+@pytest.mark.parametrize("rows,log2w", [(1, 10), (3, 14), (4, 8), (7, 18), (32, 6), (5, 24)])
+@pytest.mark.parametrize("update", ["direct", "binned"])
+def test_update_other_shapes(hs, small, rows, log2w, update):
     spec, xyz = small
-    sk, p = _pair(hs, rows, log2w, spec.box, 0.1, 100 + rows, 1)
+    sk, p = _pair(hs, rows, log2w, spec.box, 0.1, 100 + rows, 1, flags=UPDATE[update])
     sk.update(_dev(xyz[:300000]), rate=0.7)
     want = oracle.sketch_update(oracle.new_counters(p), p, xyz[:300000], rate=0.7, nthreads=NT)
     assert np.array_equal(sk.counters(), want)
 
 
-def test_update_edge_coordinates(hs):
-    sk, p = _pair(hs, 5, 10, 100.0, 0.1, 1)
+@pytest.mark.parametrize("update", ["direct", "binned"])
+def test_update_edge_coordinates(hs, update):
+    sk, p = _pair(hs, 5, 10, 100.0, 0.1, 1, flags=UPDATE[update])
     pts = np.array([[0, 0, 0], [100.0, 99.99999, -0.05], [0.7, 0.3, 250.0], [-1e-30, 5e9, 1],
                     [np.nan, 1, 1], [1, np.inf, 2], [3e9, -3e9, 1], [1, 2, 3]], np.float32)
     pts = np.repeat(pts, 3, axis=0)
@@ -101,8 +106,9 @@ def test_update_edge_coordinates(hs):
     assert np.array_equal(sk.counters(), want)
 
 
-def test_counter_wraparound(hs):
-    sk, p = _pair(hs, 3, 4, 0.1, 0.1, 0)               # one cell
+@pytest.mark.parametrize("update", ["direct", "binned"])
+def test_counter_wraparound(hs, update):
+    sk, p = _pair(hs, 3, 4, 0.1, 0.1, 0, flags=UPDATE[update])    # one cell
     c = np.zeros((3, 16), np.int32)
     for r in range(3):
         b, s = oracle.hash_row(p, r, (0, 0, 0))
@@ -126,6 +132,39 @@ def test_merge_is_the_sketch_of_the_union(hs, small):
     c, _ = _pair(hs, 5, 13, spec.box, 0.1, 8, 8)
     with pytest.raises(hs.HSError):
         a.merge(c)
+
+
+def test_binned_skew_overflows_to_direct_adds(hs):
+    # every particle in a handful of cells: the shared-memory buffers of those
+    # bins overflow on every tile and the excess goes through global atomics
+    rng = np.random.default_rng(3)
+    sk, p = _pair(hs, 5, 20, 100.0, 0.1, 12, flags=UPDATE["binned"])
+    cells = np.array([[10.05, 20.05, 30.05], [70.05, 5.05, 99.95], [0.05, 0.05, 0.05]], np.float32)
+    pts = np.concatenate([cells[rng.integers(0, 3, 3_000_000)],
+                          rng.uniform(0, 100, (200_000, 3)).astype(np.float32)])
+    sk.update(_dev(pts), rate=0.9)
+    want = oracle.sketch_update(oracle.new_counters(p), p, pts, rate=0.9, nthreads=NT)
+    assert np.array_equal(sk.counters(), want)
+
+
+def test_binned_pending_across_calls_and_readers(hs, small):
+    # increments stay in the bins across calls; every reader drains them first
+    spec, xyz = small
+    sk, p = _pair(hs, 5, 16, spec.box, 0.1, 77, 5, flags=UPDATE["binned"])
+    want = oracle.new_counters(p)
+    d = _dev(xyz)
+    sk.update(d[:300000], 300000, rate=0.5)
+    oracle.sketch_update(want, p, xyz[:300000], g0=0, rate=0.5, nthreads=NT)
+    keys = oracle.keys_of(xyz[:1000], p)
+    assert np.array_equal(sk.query(keys), oracle.estimate(want, p, keys))
+    sk.update(d[300000:], len(xyz) - 300000, rate=0.5)
+    oracle.sketch_update(want, p, xyz[300000:], g0=300000, rate=0.5, nthreads=NT)
+    k1, e1 = sk.topk(500)
+    wk, we = oracle.topk_full(want, p, 500, nthreads=NT)
+    assert np.array_equal(k1, wk) and np.array_equal(e1, we)
+    sk.update(d[:1000], 1000)
+    sk.reset()                                   # pending codes are dropped, not applied
+    assert not sk.counters().any()
 
 
 def test_reset(hs, small):
