@@ -204,6 +204,27 @@ hs_status sketch_stats(hs_sketch *h, hs_stats *out, int reset);
  * t adds per kept particle resolve in L2.  Allocates and frees its table. */
 hs_status hs_measure_red_rate(uint64_t n_counters, uint64_t total_ops, double *ops_per_s);
 
+/*
+ * Point queries that allocate nothing.  No counterpart in the paper: this is
+ * for callers that cannot call cudaMalloc when they query - code running
+ * while its stream is captured into a CUDA graph, processes whose device
+ * memory belongs to another allocator or a fixed budget, latency-critical
+ * loops.  Same results as sketch_query (keys and est host or device arrays;
+ * synchronous; a key >= G^3 gives HS_ERR_ARG with its est entry 0), but every
+ * temporary lives in one static device array of the library, sized for
+ * HS_NOALLOC_QUERY_MAX keys (about 3 MiB, held on every GPU that loads the
+ * library until the process exits).  m > HS_NOALLOC_QUERY_MAX gives
+ * HS_ERR_ARG: split the query.  The sketch's device must be current.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), which may load the library's device code: make that
+ * first call before any stream capture.  All calls share the array, which
+ * keeps the previous call's contents (the call clears its own flag); calls
+ * that overlap on the GPU - from several host threads or handles - race on it.
+ * Pending binned increments are applied first, as by every reader.
+ */
+#define HS_NOALLOC_QUERY_MAX 262144u
+hs_status sketch_query_noalloc(hs_sketch *h, const uint64_t *keys, uint64_t m, int32_t *est);
+
 /* Message of the calling thread's last failed call ("" if none). */
 const char *hs_last_error(void);
 

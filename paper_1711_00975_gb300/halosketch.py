@@ -92,6 +92,7 @@ def lib():
                 "sketch_flush": [vp],
                 "sketch_stats": [vp, ctypes.POINTER(hs_stats), ci],
                 "hs_measure_red_rate": [u64, u64, ctypes.POINTER(f64)],
+                "sketch_query_noalloc": [vp, vp, u64, vp],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -152,6 +153,16 @@ def sketch_update(h, xyz, n: int | None = None, sample_rate: float = 1.0) -> Non
 def sketch_query(h, keys, est) -> None:
     m = keys.numel() if hasattr(keys, "numel") else keys.size
     _check(lib().sketch_query(h, _ptr(keys), m, _ptr(est)), "sketch_query")
+
+
+HS_NOALLOC_QUERY_MAX = 262144
+
+
+def sketch_query_noalloc(h, keys, est) -> None:
+    """sketch_query without device allocation (static library scratch, at most
+    HS_NOALLOC_QUERY_MAX keys per call; see include/halosketch.h)."""
+    m = keys.numel() if hasattr(keys, "numel") else keys.size
+    _check(lib().sketch_query_noalloc(h, _ptr(keys), m, _ptr(est)), "sketch_query_noalloc")
 
 
 def topk_extract(h, k: int, keys: np.ndarray, est: np.ndarray) -> int:
