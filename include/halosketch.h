@@ -166,6 +166,11 @@ hs_status sketch_destroy(hs_sketch *h);
 
 /* ---- extensions ---- */
 
+/* Set the global index of the next particle (a shard of a longer stream that
+ * starts at particle number n_seen keeps its sampling decisions; Sec. 5's sum of
+ * sketches then reproduces the whole stream's sketch).  Counters are kept. */
+hs_status sketch_seek(hs_sketch *h, uint64_t n_seen);
+
 /* Zero the counters and n_seen (asynchronous on the handle's stream). */
 hs_status sketch_reset(hs_sketch *h);
 

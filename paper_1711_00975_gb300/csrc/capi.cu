@@ -63,6 +63,7 @@ struct hs_sketch {
     cudaStream_t stream = nullptr;
     int32_t *C = nullptr;
     uint64_t *probe = nullptr;
+    uint64_t probe_base = 0;    // global index of probe slot 0
     uint64_t n_seen = 0;
 
     // staging for host particle buffers
@@ -398,7 +399,8 @@ hs_status launch_update_timed(hs_sketch *h, const float *xyz, uint64_t n, uint64
                 EventPair ev = take_events(h);
                 cudaEventRecord(ev.a, h->stream);
                 HS_CUDA(launch_bin_scatter(xyz + 3 * off, cnt, g0 + off, h->d, h->C, rate,
-                                           h->p.sample_seed, h->probe, kProbeCap, h->bl, h->bins,
+                                           h->p.sample_seed, h->probe, h->probe_base, kProbeCap,
+                                           h->bl, h->bins,
                                            h->bin_cursor, h->bin_cap, h->num_sms, h->stream));
                 cudaEventRecord(ev.b, h->stream);
                 h->pending_update.push_back(ev);
@@ -416,7 +418,8 @@ hs_status launch_update_direct(hs_sketch *h, const float *xyz, uint64_t n, uint6
                                double rate) {
     EventPair ev = take_events(h);
     cudaEventRecord(ev.a, h->stream);
-    HS_CUDA(launch_update(xyz, n, g0, h->d, h->C, rate, h->p.sample_seed, h->probe, kProbeCap, 0,
+    HS_CUDA(launch_update(xyz, n, g0, h->d, h->C, rate, h->p.sample_seed, h->probe,
+                          h->probe_base, kProbeCap, 0,
                           (uint32_t)h->d.W, h->num_sms * 8, h->stream));
     cudaEventRecord(ev.b, h->stream);
     h->pending_update.push_back(ev);
@@ -705,7 +708,7 @@ hs_status topk_extract(hs_sketch *h, uint32_t k, uint64_t *keys, int32_t *est, u
     // 1. a lower bound on the k-th estimate: the k-th best estimate among the
     //    distinct cells of the first particles of the stream
     int32_t theta = INT32_MIN;
-    uint64_t m_probe = std::min<uint64_t>(h->n_seen, kProbeCap);
+    uint64_t m_probe = std::min<uint64_t>(h->n_seen - h->probe_base, kProbeCap);
     if (m_probe >= kk) {
         HS_CUDA(cudaMemsetAsync(h->counters, 0, 4 * sizeof(unsigned long long), h->stream));
         HS_CUDA(cudaMemsetAsync(h->flags, 0, 4 * sizeof(uint32_t), h->stream));
@@ -800,6 +803,7 @@ hs_status sketch_reset(hs_sketch *h) {
     HS_CUDA(cudaMemsetAsync(h->C, 0, (size_t)h->d.rows * h->d.W * 4, h->stream));
     HS_CUDA(cudaMemsetAsync(h->probe, 0xFF, kProbeCap * 8, h->stream));
     h->n_seen = 0;
+    h->probe_base = 0;
     return HS_OK;
 }
 
@@ -853,6 +857,14 @@ hs_status sketch_info(const hs_sketch *h, hs_info *out) {
     out->width = h->d.W;
     out->n_cells = h->n_cells;
     out->n_seen = h->n_seen;
+    return HS_OK;
+}
+
+hs_status sketch_seek(hs_sketch *h, uint64_t n_seen) {
+    if (!h) return fail(HS_ERR_ARG, "handle is NULL");
+    HS_CUDA(cudaMemsetAsync(h->probe, 0xFF, kProbeCap * 8, h->stream));
+    h->n_seen = n_seen;
+    h->probe_base = n_seen;
     return HS_OK;
 }
 

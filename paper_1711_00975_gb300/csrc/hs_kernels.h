@@ -11,7 +11,8 @@ namespace hs {
 // ---- update mode (k_update.cu) ----
 cudaError_t launch_update(const float *xyz, uint64_t n, uint64_t g0, const SketchDesc &d,
                           int32_t *C, double rate, uint64_t sample_seed, uint64_t *probe,
-                          uint64_t probe_cap, uint32_t band_lo, uint32_t band_hi, int max_blocks,
+                          uint64_t probe_base, uint64_t probe_cap, uint32_t band_lo,
+                          uint32_t band_hi, int max_blocks,
                           cudaStream_t s);
 // ---- update mode with shared-memory accumulation (k_binned.cu) ----
 struct BinLayout {
@@ -23,7 +24,8 @@ struct BinLayout {
 BinLayout bin_layout(const SketchDesc &d, size_t smem_budget);
 cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const SketchDesc &d,
                                int32_t *C, double rate, uint64_t sample_seed, uint64_t *probe,
-                               uint64_t probe_cap, const BinLayout &L, uint16_t *bins,
+                               uint64_t probe_base, uint64_t probe_cap, const BinLayout &L,
+                               uint16_t *bins,
                                uint32_t *cursor, uint32_t cap, int blocks, cudaStream_t s);
 cudaError_t launch_bin_accumulate(const BinLayout &L, uint16_t *bins, uint32_t *cursor,
                                   uint32_t cap, int32_t *C, cudaStream_t s);

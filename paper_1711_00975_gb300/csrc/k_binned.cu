@@ -30,7 +30,8 @@ struct ScatterArgs {
     uint64_t thr;
     uint64_t sample_seed;
     uint64_t *probe;
-    uint64_t probe_cap;
+    uint64_t probe_base;  // probe[g - probe_base] = key for probe_base <= g < probe_end
+    uint64_t probe_end;
     uint32_t keep_all;
     uint32_t S;           // log2 of counters per bin
     uint32_t nbins;
@@ -81,7 +82,8 @@ __device__ __forceinline__ bool prep_particle(float x, float y, float z, uint64_
     bool valid = axis_cell(x, d.inv_cell, d.G, cx);
     valid &= axis_cell(y, d.inv_cell, d.G, cy);
     valid &= axis_cell(z, d.inv_cell, d.G, cz);
-    if (g < a.probe_cap) write_probe(a.probe, g, valid, cx, cy, cz, d.G);
+    if (g - a.probe_base < a.probe_end - a.probe_base)
+        write_probe(a.probe, g - a.probe_base, valid, cx, cy, cz, d.G);
     cell = (uint64_t)cx | ((uint64_t)cy << 21) | ((uint64_t)cz << 42);
     return keep && valid;
 }
@@ -377,7 +379,7 @@ BinLayout bin_layout(const SketchDesc &d, size_t smem_budget) {
 
 cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const SketchDesc &d,
                                int32_t *C, double rate, uint64_t sample_seed, uint64_t *probe,
-                               uint64_t probe_cap, const BinLayout &L, uint16_t *bins,
+                               uint64_t probe_base, uint64_t probe_cap, const BinLayout &L, uint16_t *bins,
                                uint32_t *cursor, uint32_t cap, int blocks, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     // bin arrays are read and written as 16-byte vectors: every bin must start
@@ -391,7 +393,8 @@ cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const 
     a.thr = rate >= 1.0 ? 0 : (uint64_t)ldexp(rate, 64);
     a.sample_seed = sample_seed;
     a.probe = probe;
-    a.probe_cap = probe ? probe_cap : 0;
+    a.probe_base = probe_base;
+    a.probe_end = probe ? probe_base + probe_cap : probe_base;
     a.S = L.S;
     a.nbins = L.nbins;
     a.slot = L.slot;

@@ -21,8 +21,9 @@ struct UpdateArgs {
     uint64_t g0;           // global index of particle 0 of this launch
     uint64_t thr;          // keep iff splitmix64(g) < thr (unless keep_all)
     uint64_t sample_seed;
-    uint64_t *probe;       // probe[g] = key for g < probe_cap
-    uint64_t probe_cap;
+    uint64_t *probe;       // probe[g - probe_base] = key for probe_base <= g < probe_end
+    uint64_t probe_base;
+    uint64_t probe_end;
     uint32_t keep_all;
     uint32_t band_lo;      // only buckets in [band_lo, band_hi) are updated
     uint32_t band_hi;
@@ -37,7 +38,8 @@ __device__ __forceinline__ void add_particle(float x, float y, float z, uint64_t
     bool valid = axis_cell(x, d.inv_cell, d.G, cx);
     valid &= axis_cell(y, d.inv_cell, d.G, cy);
     valid &= axis_cell(z, d.inv_cell, d.G, cz);
-    if (g < a.probe_cap) a.probe[g] = valid ? key_of(cx, cy, cz, d.G) : kInvalidKey;
+    if (g - a.probe_base < a.probe_end - a.probe_base)
+        a.probe[g - a.probe_base] = valid ? key_of(cx, cy, cz, d.G) : kInvalidKey;
     if (!(keep && valid)) return;
     constexpr int kRows = T > 0 ? T : kMaxRows;
 #pragma unroll
@@ -119,7 +121,7 @@ cudaError_t launch_add_counters(int32_t *dst, const int32_t *src, uint64_t n, cu
 
 cudaError_t launch_update(const float *xyz, uint64_t n, uint64_t g0, const SketchDesc &d,
                           int32_t *C, double rate, uint64_t sample_seed, uint64_t *probe,
-                          uint64_t probe_cap, uint32_t band_lo, uint32_t band_hi, int max_blocks,
+                          uint64_t probe_base, uint64_t probe_cap, uint32_t band_lo, uint32_t band_hi, int max_blocks,
                           cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     UpdateArgs a;
@@ -129,8 +131,8 @@ cudaError_t launch_update(const float *xyz, uint64_t n, uint64_t g0, const Sketc
     a.thr = rate >= 1.0 ? 0 : (uint64_t)ldexp(rate, 64);
     a.sample_seed = sample_seed;
     a.probe = probe;
-    // probe slots that this launch can touch: global indices below probe_cap
-    a.probe_cap = probe ? probe_cap : 0;
+    a.probe_base = probe_base;
+    a.probe_end = probe ? probe_base + probe_cap : probe_base;
     a.band_lo = band_lo;
     a.band_hi = band_hi;
     uint32_t *Cu = reinterpret_cast<uint32_t *>(C);

@@ -90,6 +90,7 @@ def lib():
                 "sketch_info": [vp, ctypes.POINTER(hs_info)],
                 "sketch_synchronize": [vp],
                 "sketch_flush": [vp],
+                "sketch_seek": [vp, u64],
                 "sketch_stats": [vp, ctypes.POINTER(hs_stats), ci],
                 "hs_measure_red_rate": [u64, u64, ctypes.POINTER(f64)],
                 "sketch_query_noalloc": [vp, vp, u64, vp],
@@ -198,6 +199,10 @@ def sketch_info(h) -> hs_info:
     return info
 
 
+def sketch_seek(h, n_seen: int) -> None:
+    _check(lib().sketch_seek(h, n_seen), "sketch_seek")
+
+
 def sketch_flush(h) -> None:
     _check(lib().sketch_flush(h), "sketch_flush")
 
@@ -289,3 +294,6 @@ class Sketch:
 
     def flush(self):
         sketch_flush(self.h)
+
+    def seek(self, n_seen: int):
+        sketch_seek(self.h, n_seen)

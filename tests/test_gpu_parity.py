@@ -167,6 +167,28 @@ def test_binned_pending_across_calls_and_readers(hs, small):
     assert not sk.counters().any()
 
 
+def test_shards_with_seek_merge_to_the_whole_stream(hs, small):
+    # each shard keeps its global indices (sampling unchanged) and its own probe
+    spec, xyz = small
+    whole, p = _pair(hs, 5, 16, spec.box, 0.1, 44, 6)
+    a, _ = _pair(hs, 5, 16, spec.box, 0.1, 44, 6)
+    b, _ = _pair(hs, 5, 16, spec.box, 0.1, 44, 6)
+    whole.update(_dev(xyz), rate=0.3)
+    cut = 654321
+    a.update(_dev(xyz[:cut]), rate=0.3)
+    b.seek(cut)
+    b.update(_dev(xyz[cut:]), rate=0.3)
+    kb, eb = b.topk(100)                        # uses b's own probe (no global index < 2^20)
+    Cb = b.counters()
+    wk, we = oracle.topk_full(Cb, p, 100, nthreads=NT)
+    assert np.array_equal(kb, wk) and np.array_equal(eb, we)
+    a.merge(b)
+    assert np.array_equal(a.counters(), whole.counters())
+    k1, e1 = a.topk(300)
+    k2, e2 = whole.topk(300)
+    assert np.array_equal(k1, k2) and np.array_equal(e1, e2)
+
+
 def test_reset(hs, small):
     spec, xyz = small
     sk, p = _pair(hs, 5, 12, spec.box, 0.1, 2)
