@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-red", action="store_true", help="skip the L2 atomic-rate probe")
+    ap.add_argument("--no-batch", action="store_true", help="skip the sub-volume batch leg")
     ap.add_argument("--second-rate", type=float, default=0.1,
                     help="also time this sample rate (0 to skip)")
     return ap.parse_args()
@@ -148,6 +149,63 @@ def cpu_sample_rates(xyz_host: np.ndarray, n_update: int, n_cells: int, k: int, 
     oracle.topk_full(C, p, k, nthreads=cores, key_lo=0, key_hi=n_cells)
     t2 = time.perf_counter()
     return n_update / (t1 - t0), n_cells / (t2 - t1), cores, t2 - t0
+
+
+def run_batched(steps: int, warmup: int):
+    """64 sub-volumes of uneven size (2^16..2^26 particles, about 3e8 in all),
+    each with its own 5 x 2^18 sketch and top-500, updated as one batch."""
+    import torch
+
+    import synth
+    from paper_1711_00975_gb300 import halosketch as hs
+
+    specs = synth.subvolume_specs(seed=3)
+    counts = [s.n for s in specs]
+    offsets = np.concatenate([[0], np.cumsum(counts)]).astype(np.uint64)
+    total = int(offsets[-1])
+    host = torch.empty((total, 3), dtype=torch.float32).pin_memory()
+    t0 = time.time()
+    for s_, o in zip(specs, offsets[:-1]):
+        synth.HaloBox(s_).generate_into_ptr(host.data_ptr() + int(o) * 12, 0, s_.n)
+    gen_s = time.time() - t0
+    dev = host.cuda()
+    stream = torch.cuda.Stream()        # a batch's graph needs a non-legacy stream
+    torch.cuda.synchronize()
+    b = hs.Batch(5, 18, [s_.box for s_ in specs], 0.1, hash_seed=3, sample_seed=4, stream=stream)
+    tune = b.autotune(dev, offsets, 1.0)
+
+    def step():
+        b.reset()
+        b.update(dev, offsets, 1.0)
+        return b.topk(500)
+
+    for _ in range(warmup):
+        step()
+    b.stats(reset=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ups = []
+    e0.record(stream)
+    for _ in range(steps):
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b.reset()
+        a.record(stream)
+        b.update(dev, offsets, 1.0)
+        c.record(stream)
+        b.topk(500)
+        ups.append((a, c))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    upd = float(np.mean([a.elapsed_time(c) for a, c in ups]))
+    st = b.stats(reset=True)
+    b.close()
+    return {"workload": "subvolumes-64", "volumes": len(specs), "particles": total,
+            "particles_per_s": total / (ms * 1e-3), "ms_per_step": ms, "update_ms": upd,
+            "update_stream_gbs": 12.0 * total / (upd * 1e-3) / 1e9,
+            "topk_ms_per_step": ms - upd, "k": 500, "sketch": "5 x 2^18 int32 per volume",
+            "autotune": tune, "gpu_launches_per_step": st["kernel_launches"] / steps,
+            "generation_s": gen_s}
 
 
 def run_reference(args):
@@ -326,6 +384,12 @@ def run_ours(args):
                "h2d_bytes_per_step": 12 * n, "d2h_bytes_per_step": 12 * k,
                "ms_per_step": max(ems, wall * 1e3)}
 
+    batched = None
+    if not args.no_batch:
+        del dev
+        torch.cuda.empty_cache()
+        batched = run_batched(max(3, args.steps // 2), args.warmup)
+
     cpu = None
     if not args.no_cpu and rank == 0:
         n_upd = min(n, 1 << 27)
@@ -352,7 +416,7 @@ def run_ours(args):
                           "candidates": st["last_candidates"], "threshold": st["last_threshold"],
                           "passes": st["last_passes"]},
             "roofline": roof, "search": search_roof, "red_rate": red, "second_rate": second, "e2e": e2e,
-            "cpu_baseline": cpu, "clocks": clocks,
+            "batched": batched, "cpu_baseline": cpu, "clocks": clocks,
             "gpu_launches": int(st["kernel_launches"])}
     if rank == 0:
         print(json.dumps(line), flush=True)

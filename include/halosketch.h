@@ -230,6 +230,51 @@ hs_status hs_measure_red_rate(uint64_t n_counters, uint64_t total_ops, double *o
 #define HS_NOALLOC_QUERY_MAX 262144u
 hs_status sketch_query_noalloc(hs_sketch *h, const uint64_t *keys, uint64_t m, int32_t *est);
 
+/* ---- batches of independent sub-volumes (many small snapshots or sub-boxes) ----
+ *
+ * A batch holds n_volumes independent Count Sketches with the same rows, width
+ * and hash seeds; volume v has its own box (boxes[v], mesh G_v =
+ * round(boxes[v] / cell) <= 65535), its own particle stream (global indices
+ * from 0 per volume; sample_seed shared) and its own top-k.  batch_update
+ * processes the particles of all volumes, concatenated in one DEVICE buffer
+ * with volume v at particles [offsets[v], offsets[v+1]) (offsets: host array of
+ * n_volumes+1 entries, offsets[0] = 0), in one persistent scatter launch and one
+ * accumulation launch, replayed as a CUDA graph while xyz, the total count and
+ * the rate stay the same.  Every call is Add (Sec. 2.2) per particle of every
+ * volume; results equal n_volumes separate sketches.  The batch's stream must
+ * not be the legacy default stream (NULL creates a private stream).
+ */
+typedef struct hs_batch hs_batch;
+
+/* Scatter configuration chosen by batch_autotune. */
+typedef struct {
+    uint32_t threads;        /* threads per block of the scatter kernel           */
+    uint32_t slot;           /* shared-memory ring depth (codes per bin)          */
+    uint32_t configs_tried;
+    float best_ms;           /* its time for the tuning data                      */
+} hs_tune;
+
+/* params: rows, log2_width, cell, hash_seed, sample_seed, flags as for
+ * sketch_create (params->box is ignored; boxes[v] gives each volume's box). */
+hs_status batch_create(const hs_params *params, uint32_t n_volumes, const double *boxes,
+                       void *cuda_stream, hs_batch **out);
+hs_status batch_update(hs_batch *b, const float *xyz, const uint64_t *offsets, double sample_rate);
+/* Top-k of every volume (Algorithm 1 per volume): volume v's min(k, G_v^3)
+ * entries go to keys/est[v*k ...] (HOST arrays of n_volumes*k), their number to
+ * n_out[v].  Synchronous. */
+hs_status batch_topk(hs_batch *b, uint32_t k, uint64_t *keys, int32_t *est, uint32_t *n_out);
+/* Counters of one volume (rows x W int32, host or device out); synchronous. */
+hs_status batch_counters(hs_batch *b, uint32_t volume, int32_t *out);
+hs_status batch_reset(hs_batch *b);
+hs_status batch_volume_info(const hs_batch *b, uint32_t volume, hs_info *out);
+hs_status batch_stats(hs_batch *b, hs_stats *out, int reset);
+/* Time the scatter's block size and shared-memory ring depth on the given
+ * particles and keep the fastest for later updates.  The tuning runs update the
+ * sketches, so the batch is reset afterwards. */
+hs_status batch_autotune(hs_batch *b, const float *xyz, const uint64_t *offsets,
+                         double sample_rate, hs_tune *out);
+hs_status batch_destroy(hs_batch *b);
+
 /* Message of the calling thread's last failed call ("" if none). */
 const char *hs_last_error(void);
 

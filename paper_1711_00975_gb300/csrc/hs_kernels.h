@@ -15,6 +15,17 @@ cudaError_t launch_update(const float *xyz, uint64_t n, uint64_t g0, const Sketc
                           uint32_t band_hi, int max_blocks,
                           cudaStream_t s);
 // ---- update mode with shared-memory accumulation (k_binned.cu) ----
+// One sub-volume of a batch: particles [start, next start) of the concatenated
+// buffer, its own stream index g0, mesh (G, inv_cell) and first bin.
+struct VolumeDesc {
+    uint64_t start;
+    uint64_t g0;
+    uint64_t probe_base;
+    float inv_cell;
+    uint32_t G;
+    uint32_t bin0;
+    uint32_t pad;
+};
 struct BinLayout {
     uint32_t S;        // log2 counters per bin
     uint32_t nbins;    // rows * W / 2^S
@@ -25,8 +36,9 @@ BinLayout bin_layout(const SketchDesc &d, size_t smem_budget);
 cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const SketchDesc &d,
                                int32_t *C, double rate, uint64_t sample_seed, uint64_t *probe,
                                uint64_t probe_base, uint64_t probe_cap, const BinLayout &L,
-                               uint16_t *bins,
-                               uint32_t *cursor, uint32_t cap, int blocks, cudaStream_t s);
+                               uint16_t *bins, uint32_t *cursor, uint32_t cap, int blocks,
+                               cudaStream_t s, const VolumeDesc *vols = nullptr, uint32_t nvol = 0,
+                               uint32_t probe_per_vol = 0, int threads = 1024);
 cudaError_t launch_bin_accumulate(const BinLayout &L, uint16_t *bins, uint32_t *cursor,
                                   uint32_t cap, int32_t *C, cudaStream_t s);
 

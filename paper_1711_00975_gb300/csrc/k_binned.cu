@@ -44,6 +44,9 @@ struct ScatterArgs {
     uint32_t log2_slot;
     uint16_t *bins;       // nbins x cap codes
     uint32_t *cursor;     // fill of each global bin (may exceed cap)
+    const VolumeDesc *vols;   // batch: one entry per volume (nullptr for one sketch)
+    uint32_t nvol;
+    uint32_t probe_per_vol;   // batch: probe window of each volume
 };
 
 __device__ __noinline__ void direct_add(uint32_t *C, const ScatterArgs &a, uint32_t bin,
@@ -108,16 +111,61 @@ __device__ __forceinline__ void stage_one(uint32_t bin, uint32_t code, const Sca
     }
 }
 
-template <int T>
+// Volume holding particle i of the concatenated buffer (binary search).
+__device__ __forceinline__ uint32_t vol_of(const ScatterArgs &a, uint64_t i) {
+    uint32_t lo = 0, hi = a.nvol;
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (a.vols[mid].start <= i) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Batch variant of prep_particle: particle i of the concatenated buffer
+// belongs to volume v (vols[v].start <= i < vols[v+1].start, found from the
+// hint v upward); it is sampled with its index inside that volume's stream and
+// quantised on that volume's mesh.  The packed cell carries the volume's first
+// bin: cx | cy << 16 | cz << 32 | bin0 << 48 (G < 2^16, bins < 2^16).
+__device__ __forceinline__ bool prep_particle_batch(float x, float y, float z, uint64_t i,
+                                                    const ScatterArgs &a, uint32_t &v,
+                                                    uint64_t &cell) {
+    while (v + 1 < a.nvol && i >= a.vols[v + 1].start) ++v;
+    const VolumeDesc &V = a.vols[v];
+    const uint64_t g = V.g0 + (i - V.start);
+    bool keep = a.keep_all || splitmix64_at(a.sample_seed, g) < a.thr;
+    uint32_t cx = 0, cy = 0, cz = 0;
+    bool valid = axis_cell(x, V.inv_cell, V.G, cx);
+    valid &= axis_cell(y, V.inv_cell, V.G, cy);
+    valid &= axis_cell(z, V.inv_cell, V.G, cz);
+    if (a.probe && g - V.probe_base < a.probe_per_vol)
+        write_probe(a.probe + (uint64_t)v * a.probe_per_vol, g - V.probe_base, valid, cx, cy, cz,
+                    V.G);
+    cell = (uint64_t)cx | ((uint64_t)cy << 16) | ((uint64_t)cz << 32) | ((uint64_t)V.bin0 << 48);
+    return keep && valid;
+}
+
+template <int T, bool BATCH>
 __device__ __forceinline__ void stage_cell(uint64_t cell, const SketchDesc &d, const ScatterArgs &a,
                                            uint32_t *s_fill, uint16_t *s_buf, uint32_t *s_due,
                                            uint32_t *C) {
-    const uint32_t cx = (uint32_t)(cell & 0x1FFFFF), cy = (uint32_t)((cell >> 21) & 0x1FFFFF),
-                   cz = (uint32_t)(cell >> 42);
+    uint32_t cx, cy, cz, bin0 = 0;
+    if (BATCH) {
+        cx = (uint32_t)(cell & 0xFFFF);
+        cy = (uint32_t)((cell >> 16) & 0xFFFF);
+        cz = (uint32_t)((cell >> 32) & 0xFFFF);
+        bin0 = (uint32_t)(cell >> 48);
+    } else {
+        cx = (uint32_t)(cell & 0x1FFFFF);
+        cy = (uint32_t)((cell >> 21) & 0x1FFFFF);
+        cz = (uint32_t)(cell >> 42);
+    }
     if (T > 0) {
         uint32_t bin[T > 0 ? T : 1], code[T > 0 ? T : 1], w[T > 0 ? T : 1];
 #pragma unroll
-        for (int r = 0; r < T; ++r) bin_code(d.seed[r], cx, cy, cz, (uint32_t)r, a, bin[r], code[r]);
+        for (int r = 0; r < T; ++r) {
+            bin_code(d.seed[r], cx, cy, cz, (uint32_t)r, a, bin[r], code[r]);
+            bin[r] += bin0;
+        }
 #pragma unroll
         for (int r = 0; r < T; ++r) w[r] = atomicAdd(&s_fill[bin[r]], 1u);
 #pragma unroll
@@ -126,6 +174,7 @@ __device__ __forceinline__ void stage_cell(uint64_t cell, const SketchDesc &d, c
         for (uint32_t r = 0; r < d.rows; ++r) {
             uint32_t bin, code;
             bin_code(d.seed[r], cx, cy, cz, r, a, bin, code);
+            bin += bin0;
             stage_one(bin, code, a, atomicAdd(&s_fill[bin], 1u), s_buf, s_due, C);
         }
     }
@@ -157,18 +206,15 @@ __device__ __forceinline__ void flush_ring(uint32_t *C, const ScatterArgs &a, ui
     }
 }
 
-#ifndef HS_SCATTER_THREADS
-#define HS_SCATTER_THREADS 1024
-#endif
-constexpr int kScatterThreads = HS_SCATTER_THREADS;
+constexpr int kScatterThreads = 1024;  // largest block; the queue area is sized for it
 constexpr int kQueuePerWarp = 128;     // 32 lanes x 4 particles
 
 // Up to kMaxFlushPerThread due-bitmap words per warp in the flush phase
 // (nbins <= kMaxFlushPerThread * 32 * warps per block).
 constexpr int kMaxFlushPerThread = 6;
 
-template <int T, bool VEC>
-__global__ void __launch_bounds__(kScatterThreads, 1)
+template <int T, bool VEC, bool BATCH, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1)
     k_bin_scatter(const float *__restrict__ xyz, const SketchDesc d, const ScatterArgs a,
                   uint32_t *__restrict__ C) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -219,32 +265,53 @@ __global__ void __launch_bounds__(kScatterThreads, 1)
                 nw = __ldcs(p4 + 3 * gn + 2);
             }
             if (g4 < full_groups) {
-                uint64_t g = a.g0 + 4 * g4;
-                ok[0] = prep_particle(u.x, u.y, u.z, g, d, a, cell[0]);
-                ok[1] = prep_particle(u.w, v.x, v.y, g + 1, d, a, cell[1]);
-                ok[2] = prep_particle(v.z, v.w, w.x, g + 2, d, a, cell[2]);
-                ok[3] = prep_particle(w.y, w.z, w.w, g + 3, d, a, cell[3]);
+                if (BATCH) {
+                    uint32_t vh = vol_of(a, 4 * g4);
+                    ok[0] = prep_particle_batch(u.x, u.y, u.z, 4 * g4, a, vh, cell[0]);
+                    ok[1] = prep_particle_batch(u.w, v.x, v.y, 4 * g4 + 1, a, vh, cell[1]);
+                    ok[2] = prep_particle_batch(v.z, v.w, w.x, 4 * g4 + 2, a, vh, cell[2]);
+                    ok[3] = prep_particle_batch(w.y, w.z, w.w, 4 * g4 + 3, a, vh, cell[3]);
+                } else {
+                    uint64_t g = a.g0 + 4 * g4;
+                    ok[0] = prep_particle(u.x, u.y, u.z, g, d, a, cell[0]);
+                    ok[1] = prep_particle(u.w, v.x, v.y, g + 1, d, a, cell[1]);
+                    ok[2] = prep_particle(v.z, v.w, w.x, g + 2, d, a, cell[2]);
+                    ok[3] = prep_particle(w.y, w.z, w.w, g + 3, d, a, cell[3]);
+                }
             } else {
+                uint32_t vh = BATCH ? vol_of(a, 4 * g4 < a.n ? 4 * g4 : a.n - 1) : 0;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     uint64_t i = 4 * g4 + j;
-                    ok[j] = i < a.n && prep_particle(__ldcs(xyz + 3 * i), __ldcs(xyz + 3 * i + 1),
-                                                     __ldcs(xyz + 3 * i + 2), a.g0 + i, d, a,
-                                                     cell[j]);
+                    if (BATCH)
+                        ok[j] = i < a.n &&
+                                prep_particle_batch(__ldcs(xyz + 3 * i), __ldcs(xyz + 3 * i + 1),
+                                                    __ldcs(xyz + 3 * i + 2), i, a, vh, cell[j]);
+                    else
+                        ok[j] = i < a.n &&
+                                prep_particle(__ldcs(xyz + 3 * i), __ldcs(xyz + 3 * i + 1),
+                                              __ldcs(xyz + 3 * i + 2), a.g0 + i, d, a, cell[j]);
                 }
             }
         } else {
+            uint32_t vh = BATCH ? vol_of(a, 4 * g4 < a.n ? 4 * g4 : a.n - 1) : 0;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 uint64_t i = 4 * g4 + j;
-                ok[j] = i < a.n && prep_particle(__ldcs(xyz + 3 * i), __ldcs(xyz + 3 * i + 1),
-                                                 __ldcs(xyz + 3 * i + 2), a.g0 + i, d, a, cell[j]);
+                if (BATCH)
+                    ok[j] = i < a.n &&
+                            prep_particle_batch(__ldcs(xyz + 3 * i), __ldcs(xyz + 3 * i + 1),
+                                                __ldcs(xyz + 3 * i + 2), i, a, vh, cell[j]);
+                else
+                    ok[j] = i < a.n && prep_particle(__ldcs(xyz + 3 * i), __ldcs(xyz + 3 * i + 1),
+                                                     __ldcs(xyz + 3 * i + 2), a.g0 + i, d, a,
+                                                     cell[j]);
             }
         }
         if (__all_sync(0xFFFFFFFFu, ok[0] & ok[1] & ok[2] & ok[3])) {
             // every particle of the warp is kept: stage straight from registers
 #pragma unroll
-            for (int j = 0; j < 4; ++j) stage_cell<T>(cell[j], d, a, s_fill, s_buf, s_due, C);
+            for (int j = 0; j < 4; ++j) stage_cell<T, BATCH>(cell[j], d, a, s_fill, s_buf, s_due, C);
         } else {
             uint32_t nq = 0;
 #pragma unroll
@@ -255,7 +322,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1)
             }
             __syncwarp();
             for (uint32_t i = lane; i < nq; i += 32)
-                stage_cell<T>(q[i], d, a, s_fill, s_buf, s_due, C);
+                stage_cell<T, BATCH>(q[i], d, a, s_fill, s_buf, s_due, C);
         }
         __syncthreads();
         // flush the due bins: warp w reads due words w, w + nwarps, ... (one
@@ -380,7 +447,9 @@ BinLayout bin_layout(const SketchDesc &d, size_t smem_budget) {
 cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const SketchDesc &d,
                                int32_t *C, double rate, uint64_t sample_seed, uint64_t *probe,
                                uint64_t probe_base, uint64_t probe_cap, const BinLayout &L, uint16_t *bins,
-                               uint32_t *cursor, uint32_t cap, int blocks, cudaStream_t s) {
+                               uint32_t *cursor, uint32_t cap, int blocks, cudaStream_t s,
+                               const VolumeDesc *vols, uint32_t nvol, uint32_t probe_per_vol,
+                               int threads) {
     if (n == 0) return cudaSuccess;
     // bin arrays are read and written as 16-byte vectors: every bin must start
     // on a 16-byte boundary
@@ -407,8 +476,12 @@ cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const 
     while ((1u << a.log2_slot) < L.slot) ++a.log2_slot;
     a.bins = bins;
     a.cursor = cursor;
+    a.vols = vols;
+    a.nvol = vols ? nvol : 0;
+    a.probe_per_vol = probe_per_vol;
     uint32_t *Cu = reinterpret_cast<uint32_t *>(C);
-    const int threads = kScatterThreads;
+    // the flush phase covers kMaxFlushPerThread due words per warp
+    if (threads != 512 || L.nbins > (uint32_t)kMaxFlushPerThread * 512) threads = kScatterThreads;
     bool vec = (reinterpret_cast<uintptr_t>(xyz) & 15u) == 0;
     uint64_t per_tile = (uint64_t)threads * 4;
     uint64_t need_blocks = (n + per_tile - 1) / per_tile;
@@ -418,13 +491,28 @@ cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const 
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
         kern<<<blocks, threads, L.smem, s>>>(xyz, d, a, Cu);
     };
-    if (d.rows == 5) {
-        if (vec) launch(k_bin_scatter<5, true>);
-        else launch(k_bin_scatter<5, false>);
-    } else {
-        if (vec) launch(k_bin_scatter<0, true>);
-        else launch(k_bin_scatter<0, false>);
+#define HS_SCATTER_DISPATCH(TH)                                                            \
+    if (vols) {                                                                            \
+        if (d.rows == 5) {                                                                 \
+            if (vec) launch(k_bin_scatter<5, true, true, TH>);                            \
+            else launch(k_bin_scatter<5, false, true, TH>);                               \
+        } else {                                                                           \
+            if (vec) launch(k_bin_scatter<0, true, true, TH>);                            \
+            else launch(k_bin_scatter<0, false, true, TH>);                               \
+        }                                                                                  \
+    } else if (d.rows == 5) {                                                              \
+        if (vec) launch(k_bin_scatter<5, true, false, TH>);                               \
+        else launch(k_bin_scatter<5, false, false, TH>);                                  \
+    } else {                                                                               \
+        if (vec) launch(k_bin_scatter<0, true, false, TH>);                               \
+        else launch(k_bin_scatter<0, false, false, TH>);                                  \
     }
+    if (threads == 512) {
+        HS_SCATTER_DISPATCH(512)
+    } else {
+        HS_SCATTER_DISPATCH(1024)
+    }
+#undef HS_SCATTER_DISPATCH
     return cudaGetLastError();
 }
 

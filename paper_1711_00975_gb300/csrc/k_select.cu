@@ -131,6 +131,54 @@ __global__ void k_rank_place(const uint64_t *__restrict__ tk, const int32_t *__r
     }
 }
 
+// The whole radix select in one block, for small entry counts: each digit pass
+// builds its histogram in shared memory and thread 0 picks the digit.
+__global__ void __launch_bounds__(1024)
+    k_select_small(const uint64_t *__restrict__ key, const int32_t *__restrict__ est, uint64_t m,
+                   uint64_t k, uint64_t lo_fixed, uint32_t fixed_bytes, SelectState *st) {
+    __shared__ unsigned int sh[256];
+    __shared__ uint32_t s_hi;
+    __shared__ uint64_t s_lo, s_k;
+    if (threadIdx.x == 0) {
+        s_hi = 0;
+        s_lo = lo_fixed;
+        s_k = k;
+    }
+    for (int p = 0; p < 12; ++p) {
+        if (p >= 4 && (uint32_t)(p - 4) < fixed_bytes) continue;
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) sh[i] = 0;
+        __syncthreads();
+        const uint32_t mh = hi_mask(p);
+        const uint64_t ml = lo_mask(p);
+        const uint32_t ph = s_hi & mh;
+        const uint64_t pl = s_lo & ml;
+        for (uint64_t i = threadIdx.x; i < m; i += blockDim.x) {
+            uint32_t hi = rank_hi(est[i]);
+            uint64_t lo = rank_lo(key[i]);
+            if ((hi & mh) == ph && (lo & ml) == pl) atomicAdd(&sh[digit_of(hi, lo, p)], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint64_t above = 0;
+            int d = 255;
+            for (; d > 0; --d) {
+                if (above + sh[d] >= s_k) break;
+                above += sh[d];
+            }
+            s_k -= above;
+            if (p < 4) s_hi |= (uint32_t)d << (24 - 8 * p);
+            else s_lo |= (uint64_t)d << (56 - 8 * (p - 4));
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        st->hi = s_hi;
+        st->pad = 0;
+        st->lo = s_lo;
+        st->k_rem = s_k;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_select_kth(const uint64_t *key, const int32_t *est, uint64_t m, uint64_t k,
@@ -140,6 +188,11 @@ cudaError_t launch_select_kth(const uint64_t *key, const int32_t *est, uint64_t 
     // them are decided up front and their passes skipped.
     uint32_t fixed_bytes = key_bits >= 64 ? 0 : (64 - key_bits) / 8;
     uint64_t lo_fixed = fixed_bytes ? (~0ull << (64 - 8 * fixed_bytes)) : 0ull;
+    if (m <= (1ull << 17)) {     // one block: a few hundred entries per thread at most
+        k_select_small<<<1, 1024, 0, s>>>(key, est, m, k, lo_fixed, fixed_bytes, state);
+        *launches += 1;
+        return cudaGetLastError();
+    }
     k_select_init<<<1, 1, 0, s>>>(state, k, lo_fixed);
     cudaError_t e = cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;

@@ -46,6 +46,11 @@ class hs_info(ctypes.Structure):
                 ("n_seen", ctypes.c_uint64)]
 
 
+class hs_tune(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_uint32), ("slot", ctypes.c_uint32),
+                ("configs_tried", ctypes.c_uint32), ("best_ms", ctypes.c_float)]
+
+
 class hs_stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_uint64), ("update_launches", ctypes.c_uint64),
                 ("update_ms", ctypes.c_double), ("search_launches", ctypes.c_uint64),
@@ -94,6 +99,15 @@ def lib():
                 "sketch_stats": [vp, ctypes.POINTER(hs_stats), ci],
                 "hs_measure_red_rate": [u64, u64, ctypes.POINTER(f64)],
                 "sketch_query_noalloc": [vp, vp, u64, vp],
+                "batch_create": [ctypes.POINTER(hs_params), u32, vp, vp, ctypes.POINTER(vp)],
+                "batch_update": [vp, vp, vp, f64],
+                "batch_topk": [vp, u32, vp, vp, vp],
+                "batch_counters": [vp, u32, vp],
+                "batch_reset": [vp],
+                "batch_volume_info": [vp, u32, ctypes.POINTER(hs_info)],
+                "batch_stats": [vp, ctypes.POINTER(hs_stats), ci],
+                "batch_autotune": [vp, vp, vp, f64, ctypes.POINTER(hs_tune)],
+                "batch_destroy": [vp],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -297,3 +311,105 @@ class Sketch:
 
     def seek(self, n_seen: int):
         sketch_seek(self.h, n_seen)
+
+
+# ---- batches of sub-volumes ----
+
+def batch_create(params: hs_params, boxes, stream=None) -> ctypes.c_void_p:
+    boxes = np.ascontiguousarray(boxes, np.float64)
+    h = ctypes.c_void_p()
+    _check(lib().batch_create(ctypes.byref(params), boxes.size, boxes.ctypes.data,
+                              _stream_ptr(stream), ctypes.byref(h)), "batch_create")
+    return h
+
+
+def batch_update(b, xyz, offsets, sample_rate: float = 1.0) -> None:
+    offsets = np.ascontiguousarray(offsets, np.uint64)
+    _check(lib().batch_update(b, _ptr(xyz), offsets.ctypes.data, sample_rate), "batch_update")
+
+
+def batch_topk(b, n_volumes: int, k: int):
+    keys = np.empty(n_volumes * k, np.uint64)
+    est = np.empty(n_volumes * k, np.int32)
+    n = np.empty(n_volumes, np.uint32)
+    _check(lib().batch_topk(b, k, keys.ctypes.data, est.ctypes.data, n.ctypes.data), "batch_topk")
+    return [(keys[v * k:v * k + n[v]], est[v * k:v * k + n[v]]) for v in range(n_volumes)]
+
+
+def batch_counters(b, volume: int, out) -> None:
+    _check(lib().batch_counters(b, volume, _ptr(out)), "batch_counters")
+
+
+def batch_reset(b) -> None:
+    _check(lib().batch_reset(b), "batch_reset")
+
+
+def batch_volume_info(b, volume: int) -> hs_info:
+    info = hs_info()
+    _check(lib().batch_volume_info(b, volume, ctypes.byref(info)), "batch_volume_info")
+    return info
+
+
+def batch_stats(b, reset: bool = False) -> dict:
+    s = hs_stats()
+    _check(lib().batch_stats(b, ctypes.byref(s), 1 if reset else 0), "batch_stats")
+    return s.as_dict()
+
+
+def batch_autotune(b, xyz, offsets, sample_rate: float = 1.0) -> dict:
+    offsets = np.ascontiguousarray(offsets, np.uint64)
+    t = hs_tune()
+    _check(lib().batch_autotune(b, _ptr(xyz), offsets.ctypes.data, sample_rate, ctypes.byref(t)),
+           "batch_autotune")
+    return {f: getattr(t, f) for f, _ in t._fields_}
+
+
+def batch_destroy(b) -> None:
+    _check(lib().batch_destroy(b), "batch_destroy")
+
+
+class Batch:
+    """Owns one batch handle (independent sketches of several sub-volumes)."""
+
+    def __init__(self, rows: int, log2_width: int, boxes, cell: float, hash_seed: int = 0,
+                 sample_seed: int = 0, stream=None, flags: int = 0):
+        self.boxes = np.ascontiguousarray(boxes, np.float64)
+        box0 = float(self.boxes[0]) if self.boxes.size else 1.0
+        self.params = make_params(rows, log2_width, box0, cell, hash_seed, sample_seed, flags)
+        self.h = batch_create(self.params, self.boxes, stream)
+        self.n = self.boxes.size
+        self.rows, self.width = rows, 1 << log2_width
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def update(self, xyz, offsets, rate: float = 1.0):
+        batch_update(self.h, xyz, offsets, rate)
+
+    def topk(self, k: int):
+        return batch_topk(self.h, self.n, k)
+
+    def counters(self, volume: int) -> np.ndarray:
+        out = np.empty((self.rows, self.width), np.int32)
+        batch_counters(self.h, volume, out)
+        return out
+
+    def reset(self):
+        batch_reset(self.h)
+
+    def info(self, volume: int) -> hs_info:
+        return batch_volume_info(self.h, volume)
+
+    def stats(self, reset=False) -> dict:
+        return batch_stats(self.h, reset)
+
+    def autotune(self, xyz, offsets, rate: float = 1.0) -> dict:
+        return batch_autotune(self.h, xyz, offsets, rate)
