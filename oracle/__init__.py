@@ -64,6 +64,14 @@ def _load():
                 "or_topk_range": ([vp, u32, u32, vp, u32, u64, u64, u32, vp, vp, ci], u64),
                 "or_topk_full": ([vp, u32, u32, vp, u32, u32, vp, vp, ci], u64),
                 "or_exact_counts": ([vp, u64, u64, f32, u32, u64, f64, vp, vp, u64], u64),
+                "or_coarse_hist": ([vp, u64, u64, f32, u32, u32, u64, f64, vp], None),
+                "or_bf16": ([f32], ctypes.c_uint16),
+                "or_feature_of": ([i32], ctypes.c_uint16),
+                "or_features": ([vp, u32, vp, u64, vp], None),
+                "or_mlp_forward_f32": ([vp, vp, u64, vp], None),
+                "or_learned_update": ([vp, u32, u32, vp, vp, u64, u64, f32, u32, u64, f64, vp, u32,
+                                       vp, vp, u64], u64),
+                "or_topk_unrouted": ([vp, u32, u32, vp, u32, vp, u32, u32, vp, vp], u64),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(lib, name)

@@ -438,3 +438,149 @@ uint64_t or_exact_counts(const float *xyz, uint64_t n, uint64_t g0, float inv, u
     free(m.cnt);
     return D;
 }
+
+/* ======================================================================
+ * Learned router (an addition to the paper's method; the paper finds heavy
+ * cells with the Count Sketch alone).  Coarse cell = fine cell / R per axis.
+ * ====================================================================== */
+
+#define OR_MLP_IN 27
+#define OR_MLP_H 64
+#define OR_MLP_PARAMS (OR_MLP_H * OR_MLP_IN + OR_MLP_H + OR_MLP_H * OR_MLP_H + OR_MLP_H + OR_MLP_H + 1)
+
+/* sample counts of the coarse cells (feature pass) */
+void or_coarse_hist(const float *xyz, uint64_t n, uint64_t g0, float inv, uint32_t G, uint32_t R,
+                    uint64_t feature_seed, double feature_rate, int32_t *counts) {
+    uint32_t Gc = G / R;
+    for (uint64_t i = 0; i < n; ++i) {
+        if (!or_keep(g0 + i, feature_seed, feature_rate)) continue;
+        uint32_t c[3];
+        if (!or_cell(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], inv, G, c)) continue;
+        uint64_t ck = (uint64_t)(c[0] / R) + (uint64_t)Gc * ((uint64_t)(c[1] / R) + (uint64_t)Gc * (c[2] / R));
+        counts[ck] += 1;
+    }
+}
+
+/* bf16 bit pattern of a float: round to nearest, ties to even */
+uint16_t or_bf16(float f) {
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7FFFu + lsb;
+    return (uint16_t)(u >> 16);
+}
+
+static float or_from_bf16(uint16_t b) {
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
+/* feature of a count: bf16(float(log10(1 + n))) */
+uint16_t or_feature_of(int32_t n) { return or_bf16((float)log10(1.0 + (double)n)); }
+
+/* 27 features of each coarse key: neighbour (dx, dy, dz) at (dz+1)*9 + (dy+1)*3 + (dx+1) */
+void or_features(const int32_t *counts, uint32_t Gc, const uint64_t *keys, uint64_t m, uint16_t *out) {
+    for (uint64_t s = 0; s < m; ++s) {
+        int64_t x = (int64_t)(keys[s] % Gc), y = (int64_t)((keys[s] / Gc) % Gc),
+                z = (int64_t)(keys[s] / ((uint64_t)Gc * Gc));
+        int f = 0;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx, ++f) {
+                    int64_t xx = (x + dx + Gc) % Gc, yy = (y + dy + Gc) % Gc, zz = (z + dz + Gc) % Gc;
+                    out[s * OR_MLP_IN + f] = or_feature_of(counts[xx + (int64_t)Gc * (yy + (int64_t)Gc * zz)]);
+                }
+    }
+}
+
+/* Forward pass in the kernel's precision: bf16 weights, inputs and hidden
+ * activations; each neuron a float32 fmaf chain in index order from its bias. */
+void or_mlp_forward_f32(const float *P, const uint16_t *feats, uint64_t m, float *logits) {
+    float w[OR_MLP_PARAMS];
+    for (int i = 0; i < OR_MLP_PARAMS; ++i) w[i] = or_from_bf16(or_bf16(P[i]));
+    const float *w1 = w, *b1 = w1 + OR_MLP_H * OR_MLP_IN, *w2 = b1 + OR_MLP_H,
+                *b2 = w2 + OR_MLP_H * OR_MLP_H, *w3 = b2 + OR_MLP_H, *b3 = w3 + OR_MLP_H;
+    for (uint64_t s = 0; s < m; ++s) {
+        float x[OR_MLP_IN], h1[OR_MLP_H], h2[OR_MLP_H];
+        for (int i = 0; i < OR_MLP_IN; ++i) x[i] = or_from_bf16(feats[s * OR_MLP_IN + i]);
+        for (int j = 0; j < OR_MLP_H; ++j) {
+            float a = b1[j];
+            for (int i = 0; i < OR_MLP_IN; ++i) a = fmaf(w1[j * OR_MLP_IN + i], x[i], a);
+            h1[j] = or_from_bf16(or_bf16(a > 0.0f ? a : 0.0f));
+        }
+        for (int j = 0; j < OR_MLP_H; ++j) {
+            float a = b2[j];
+            for (int i = 0; i < OR_MLP_H; ++i) a = fmaf(w2[j * OR_MLP_H + i], h1[i], a);
+            h2[j] = or_from_bf16(or_bf16(a > 0.0f ? a : 0.0f));
+        }
+        float z = b3[0];
+        for (int i = 0; i < OR_MLP_H; ++i) z = fmaf(w3[i], h2[i], z);
+        logits[s] = z;
+    }
+}
+
+static int or_routed(const uint8_t *routed, const uint32_t *c3, uint32_t R, uint32_t Gc) {
+    uint64_t ck = (uint64_t)(c3[0] / R) + (uint64_t)Gc * ((uint64_t)(c3[1] / R) + (uint64_t)Gc * (c3[2] / R));
+    return routed[ck] != 0;
+}
+
+/*
+ * The learned update: each kept particle in a routed coarse cell increments
+ * its fine cell's exact count; every other kept particle is added to the
+ * sketch (Add, Sec. 2.2).  routed: one byte per coarse cell.  Returns the
+ * number of distinct routed fine cells; when <= cap, keys/counts hold them
+ * sorted by key.
+ */
+uint64_t or_learned_update(int32_t *C, uint32_t t, uint32_t log2w, const uint64_t *seeds,
+                           const float *xyz, uint64_t n, uint64_t g0, float inv, uint32_t G,
+                           uint64_t sample_seed, double rate, const uint8_t *routed, uint32_t R,
+                           uint64_t *keys_out, uint32_t *cnt_out, uint64_t cap) {
+    uint32_t Gc = G / R;
+    or_map m = {0, 0, 0, 0};
+    if (or_map_grow(&m)) return 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        if (!or_keep(g0 + i, sample_seed, rate)) continue;
+        uint32_t c[3];
+        if (!or_cell(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], inv, G, c)) continue;
+        if (or_routed(routed, c, R, Gc)) or_map_add(&m, or_key_of(c, G), 1);
+        else or_add(C, t, log2w, seeds, c);
+    }
+    uint64_t D = m.used;
+    if (D <= cap) {
+        or_entry *e = (or_entry *)malloc(sizeof(or_entry) * (D ? D : 1));
+        uint64_t q = 0;
+        for (uint64_t i = 0; i < m.cap; ++i)
+            if (m.keys[i]) { e[q].key = m.keys[i] - 1; e[q].est = (int32_t)m.cnt[i]; ++q; }
+        qsort(e, D, sizeof(or_entry), or_cmp_key);
+        for (uint64_t i = 0; i < D; ++i) { keys_out[i] = e[i].key; cnt_out[i] = (uint32_t)e[i].est; }
+        free(e);
+    }
+    free(m.keys);
+    free(m.cnt);
+    return D;
+}
+
+/* CSFS over the cells of [key_lo, key_hi) that are not in routed coarse cells */
+uint64_t or_topk_unrouted(const int32_t *C, uint32_t t, uint32_t log2w, const uint64_t *seeds,
+                          uint32_t G, const uint8_t *routed, uint32_t R, uint32_t k,
+                          uint64_t *keys_out, int32_t *est_out) {
+    uint64_t n = (uint64_t)G * G * G;
+    uint32_t Gc = G / R;
+    or_entry *h = (or_entry *)malloc(sizeof(or_entry) * (k ? k : 1));
+    uint64_t cnt = 0;
+    for (uint64_t key = 0; key < n; ++key) {
+        uint32_t c[3];
+        or_key_decode(key, G, c);
+        if (or_routed(routed, c, R, Gc)) continue;
+        or_entry e;
+        e.est = or_estimate_cell(C, t, log2w, seeds, c);
+        e.key = key;
+        or_offer(h, &cnt, k, e);
+    }
+    qsort(h, cnt, sizeof(or_entry), or_cmp_rank);
+    for (uint64_t i = 0; i < cnt; ++i) { keys_out[i] = h[i].key; est_out[i] = h[i].est; }
+    free(h);
+    return cnt;
+}
