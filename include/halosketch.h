@@ -275,6 +275,95 @@ hs_status batch_autotune(hs_batch *b, const float *xyz, const uint64_t *offsets,
                          double sample_rate, hs_tune *out);
 hs_status batch_destroy(hs_batch *b);
 
+/* ---- learned router (an addition to the paper's method) ----
+ *
+ * A small MLP predicts, from coarse-mesh densities, which coarse cells hold
+ * heavy fine cells; the fine cells of those coarse cells are counted exactly
+ * (the exact algorithm of Sec. 4.2 restricted to them) and every other
+ * particle goes to the Count Sketch (Sec. 2.2).  The top-k merges the exact
+ * counts with the sketch's full search over the cells that are not routed.
+ *
+ * MLP: 27 -> 64 -> 64 -> 1 with ReLU; HS_MLP_PARAMS float32 parameters in the
+ * order w1[64][27], b1[64], w2[64][64], b2[64], w3[64], b3.  The forward pass
+ * rounds weights, biases, inputs and hidden activations to bf16 and
+ * accumulates each neuron as a float32 fused multiply-add chain over its
+ * inputs in index order, starting from the bias.  Features are bf16 bit
+ * patterns, 27 per sample.  Loss: weighted binary cross-entropy on the logit,
+ * sum(w (softplus(z) - y z)) / sum(w).
+ */
+#define HS_MLP_PARAMS 6017
+typedef struct hs_mlp hs_mlp;
+hs_status mlp_create(uint64_t seed, void *cuda_stream, hs_mlp **out);
+hs_status mlp_set_params(hs_mlp *m, const float *params);   /* host or device; resets Adam */
+hs_status mlp_get_params(hs_mlp *m, float *params);
+/* logits[i] of features[i*27 .. i*27+26]; arrays host or device; synchronous */
+hs_status mlp_forward(hs_mlp *m, const uint16_t *features, uint64_t n, float *logits);
+/* summed (not averaged) gradient of sum(w (softplus(z) - y z)) and that loss;
+ * grad: HS_MLP_PARAMS floats.  The bf16 roundings pass gradients unchanged. */
+hs_status mlp_gradient(hs_mlp *m, const uint16_t *features, const float *y, const float *w,
+                       uint64_t n, float *grad, float *loss);
+/* one Adam step (beta 0.9 / 0.999, eps 1e-8) on the weight-averaged loss;
+ * *loss (if not NULL) receives that average. */
+hs_status mlp_train_step(hs_mlp *m, const uint16_t *features, const float *y, const float *w,
+                         uint64_t n, float lr, float *loss);
+hs_status mlp_destroy(hs_mlp *m);
+
+/* Exact per-cell counts of n particles (device xyz) on the box/cell mesh in an
+ * open-addressing table of 2^log2_slots entries (Sec. 4.2, the exact
+ * algorithm).  Writes up to cap (key, count) pairs in table order to keys /
+ * counts (host or device; NULL keys: count only) and the number of distinct
+ * cells to *n_out.  HS_ERR_TABLE_FULL when a key finds no free slot within 64
+ * probes.  Synchronous on cuda_stream. */
+hs_status exact_counts(const float *xyz, uint64_t n, double box, double cell, uint32_t log2_slots,
+                       void *cuda_stream, uint64_t *keys, int32_t *counts, uint64_t cap,
+                       uint64_t *n_out);
+
+/* Learned sketch: params describe the sketch of the cells that are not routed;
+ * coarse cells are R x R x R fine cells (R = coarse_factor, 1..64; the mesh must
+ * be a multiple of R and below 2^16).  The exact part has the memory of an
+ * open-addressing table of 2^table_log2 slots of (uint64 key, int32 count),
+ * 12 * 2^table_log2 bytes, held as dense blocks of R^3 int32 counters, one per
+ * routed coarse cell: at most B = floor(3 * 2^table_log2 / R^3) coarse cells are
+ * routed, so the exact part never overflows.  The features use a sample of the
+ * particles kept with probability feature_rate by a splitmix64 index hash
+ * seeded with feature_seed (indices 0.. of the particles given to
+ * learned_prepare). */
+typedef struct hs_learned hs_learned;
+hs_status learned_create(const hs_params *params, uint32_t coarse_factor, uint32_t table_log2,
+                         uint64_t feature_seed, double feature_rate, void *cuda_stream,
+                         hs_learned **out);
+/* B and the bytes of the dense blocks (either pointer may be NULL) */
+hs_status learned_capacity(hs_learned *L, uint64_t *max_routed, uint64_t *table_bytes);
+/* Sample pass -> coarse counts -> 27 features of every coarse cell with a
+ * sample: bf16(float(log10(1 + count))) of the cell and its 26 periodic
+ * neighbours, neighbour (dx, dy, dz) at index (dz+1)*9 + (dy+1)*3 + (dx+1) ->
+ * MLP -> a coarse cell is routed iff its logit > 0 and it is among the B cells
+ * of largest logit (ties: smaller coarse key first).  Device xyz.  Zeroes the
+ * exact counters; call it before the updates (a fresh or reset sketch). */
+hs_status learned_prepare(hs_learned *L, const float *xyz, uint64_t n, hs_mlp *mlp,
+                          uint64_t *n_routed);
+/* Each kept particle of a routed coarse cell increments its fine cell's exact
+ * count; every other kept particle is added to the sketch (sketch_update). */
+hs_status learned_update(hs_learned *L, const float *xyz, uint64_t n, double sample_rate);
+/* The k best of: sketch estimates of cells that are not routed (full search,
+ * Algorithm 1) and exact counts of the fine cells of routed coarse cells with
+ * a particle; ranked by (value desc, key asc); HOST outputs. */
+hs_status learned_topk(hs_learned *L, uint32_t k, uint64_t *keys, int32_t *est, uint32_t *n_out);
+/* the non-zero exact counts (fine key, count), in block order; cap 0: count only */
+hs_status learned_table(hs_learned *L, uint64_t *keys, int32_t *counts, uint64_t cap,
+                        uint64_t *n_out);
+/* the routed coarse keys, ascending */
+hs_status learned_routed(hs_learned *L, uint64_t *coarse_keys, uint64_t cap, uint64_t *n_out);
+/* the coarse cells with a sample (keys) and their logits, in list order */
+hs_status learned_logits(hs_learned *L, uint64_t *coarse_keys, float *logits, uint64_t cap,
+                         uint64_t *n_out);
+hs_status learned_features(hs_learned *L, uint16_t *features, uint64_t cap, uint64_t *n_out);
+hs_status learned_coarse_counts(hs_learned *L, int32_t *out);
+hs_status learned_sketch(hs_learned *L, hs_sketch **out);
+/* zero the sketch and the exact counters (the routing is kept) */
+hs_status learned_reset(hs_learned *L);
+hs_status learned_destroy(hs_learned *L);
+
 /* Message of the calling thread's last failed call ("" if none). */
 const char *hs_last_error(void);
 

@@ -75,6 +75,7 @@ struct hs_sketch {
 
     // top-k scratch
     uint64_t cap = 0;               // candidate capacity
+    uint64_t min_cap = 0;           // extra candidates a learned top-k appends
     uint64_t *cand_key = nullptr;
     int32_t *cand_est = nullptr;
     unsigned long long *counters = nullptr;   // [0] candidates, [1] tmp, [2] distinct
@@ -110,6 +111,8 @@ struct hs_sketch {
     uint32_t dir_G[kMaxRows] = {};        // mesh the directory of row r was built for
     uint64_t dir_lines_cap[kMaxRows] = {};
     bool is_view = false;                 // counters and probe belong to a batch
+    bool routing = false;                 // learned router: routed cells go to a table
+    RouteTarget route{};
 
     // binned update: codes waiting in global bins until the next drain
     BinLayout bl{};
@@ -219,7 +222,7 @@ void free_topk_scratch(hs_sketch *h) {
 }
 
 hs_status ensure_topk_scratch(hs_sketch *h, uint64_t k) {
-    uint64_t want_cap = std::max<uint64_t>(1ull << 22, 8 * k);
+    uint64_t want_cap = std::max<uint64_t>(std::max<uint64_t>(1ull << 22, 8 * k), k + h->min_cap);
     if (h->cand_key && h->cap >= want_cap && h->out_cap >= k) return HS_OK;
     free_topk_scratch(h);
     h->cap = want_cap;
@@ -374,6 +377,7 @@ hs_status discard_pending(hs_sketch *h) {
 }
 
 bool want_binned(hs_sketch *h, uint64_t n, double rate) {
+    if (h->routing) return true;          // only the binned scatter routes
     if (h->p.flags & HS_FLAG_UPDATE_DIRECT) return false;
     if (h->bl.slot == 0) return false;
     if (h->p.flags & HS_FLAG_UPDATE_BINNED) return true;
@@ -406,6 +410,8 @@ hs_status launch_update_timed(hs_sketch *h, const float *xyz, uint64_t n, uint64
     if (want_binned(h, n, rate)) {
         hs_status st = ensure_bins(h, n, rate);
         if (st != HS_OK) return st;
+        if (h->routing && h->pending_limit < 1.0)
+            return fail(HS_ERR_STATE, "routing needs bins of useful capacity");
         if (h->pending_limit >= 1.0) {
             // launches small enough that no bin is expected to fill
             uint64_t piece = (uint64_t)std::max(1.0, h->pending_limit / rate);
@@ -419,8 +425,9 @@ hs_status launch_update_timed(hs_sketch *h, const float *xyz, uint64_t n, uint64
                 cudaEventRecord(ev.a, h->stream);
                 HS_CUDA(launch_bin_scatter(xyz + 3 * off, cnt, g0 + off, h->d, h->C, rate,
                                            h->p.sample_seed, h->probe, h->probe_base, kProbeCap,
-                                           h->bl, h->bins,
-                                           h->bin_cursor, h->bin_cap, h->num_sms, h->stream));
+                                           h->bl, h->bins, h->bin_cursor, h->bin_cap, h->num_sms,
+                                           h->stream, nullptr, 0, 0, 1024,
+                                           h->routing ? &h->route : nullptr));
                 cudaEventRecord(ev.b, h->stream);
                 h->pending_update.push_back(ev);
                 h->pending += (double)cnt * rate;
@@ -496,7 +503,8 @@ hs_status search_pass_dir(hs_sketch *h, int32_t theta, SearchMode mode, int64_t 
     for (uint32_t r = 0; r < F; ++r) {
         HS_CUDA(launch_dir_query(h->C, h->d, (int)r, h->dir_D, h->dir_off[r], h->dir_rec[r],
                                  h->hot_list + r * h->hot_cap, cnt[r], h->xbits, theta, mode,
-                                 line_lo, line_hi, out, h->num_sms * 16, h->stream));
+                                 line_lo, line_hi, out, h->num_sms * 16, h->stream,
+                                 h->route.filter));
     }
     cudaEventRecord(ev.b, h->stream);
     h->pending_search.push_back(ev);
@@ -532,7 +540,7 @@ hs_status search_pass(hs_sketch *h, int32_t theta, SearchMode mode, uint64_t lin
         EventPair ev = take_events(h);
         cudaEventRecord(ev.a, h->stream);
         HS_CUDA(launch_full_search(h->C, h->d, theta, mode, h->bitmap, h->nb, prune, line_lo,
-                                   line_hi, out, h->num_sms, h->stream));
+                                   line_hi, out, h->num_sms, h->stream, h->route.filter));
         cudaEventRecord(ev.b, h->stream);
         h->pending_search.push_back(ev);
         h->stats.search_launches += 1;
@@ -1480,6 +1488,539 @@ hs_status batch_autotune(hs_batch *b, const float *xyz, const uint64_t *offsets,
     out->slot = best_l.slot;
     out->configs_tried = (uint32_t)tried;
     out->best_ms = best;
+    return HS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Learned router: MLP objects, exact counting, and the learned sketch.
+// ---------------------------------------------------------------------------
+
+struct hs_mlp {
+    float *P = nullptr, *M = nullptr, *V = nullptr, *grad = nullptr, *loss = nullptr;
+    int step = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+};
+
+struct hs_learned {
+    hs_sketch *sk = nullptr;       // the sketch of the cells that are not routed
+    uint32_t R = 10, Gc = 0;
+    uint64_t ncoarse = 0, words = 0;
+    uint32_t coarse_key_bits = 1;
+    uint64_t feature_seed = 0;
+    double feature_rate = 1.0 / 64;
+    int32_t *coarse = nullptr;     // Gc^3 sample counts
+    uint64_t *clist = nullptr;     // coarse cells with a sample
+    uint64_t clist_cap = 0, n_list = 0, n_routed = 0;
+    uint16_t *feats = nullptr;
+    float *logits = nullptr;
+    int32_t *lrank = nullptr;      // routing rank of each listed cell
+    uint32_t *routed = nullptr;    // Gc^3 bits
+    uint32_t *prefix = nullptr;    // routed cells before each bitmap word
+    uint32_t *scan_scratch = nullptr;
+    uint64_t max_blocks = 0;       // routing budget: dense blocks of R^3 counters
+    int32_t *blocks = nullptr;
+    uint64_t *rlist = nullptr;     // coarse key of each block
+    unsigned long long *ctr = nullptr;   // [0] list length, [1] positive logits, [2] table entries
+    uint16_t *ftab = nullptr;      // bf16(log10(1 + n)) for n < kFeatTab
+};
+
+namespace {
+
+constexpr uint32_t kFeatTab = 65536;
+
+// float -> bf16 bits, round to nearest, ties to even (finite inputs)
+uint16_t host_bf16(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+bool host_is_device(const void *p) { return is_device_ptr(p); }
+
+// device copy of a host-or-device input (tmp is freed by the caller)
+template <typename T>
+hs_status device_input(const T *src, uint64_t count, cudaStream_t s, const T **dst, T **tmp) {
+    *tmp = nullptr;
+    if (host_is_device(src)) {
+        *dst = src;
+        return HS_OK;
+    }
+    HS_CUDA(cudaMalloc(tmp, std::max<uint64_t>(count, 1) * sizeof(T)));
+    HS_CUDA(cudaMemcpyAsync(*tmp, src, count * sizeof(T), cudaMemcpyHostToDevice, s));
+    *dst = *tmp;
+    return HS_OK;
+}
+
+void learned_free(hs_learned *L) {
+    void *ps[] = {L->coarse, L->clist,  L->feats,        L->logits, L->lrank, L->routed,
+                  L->prefix, L->scan_scratch, L->blocks, L->rlist, L->ctr,   L->ftab};
+    for (void *q : ps)
+        if (q) cudaFree(q);
+}
+
+}  // namespace
+
+extern "C" {
+
+hs_status mlp_destroy(hs_mlp *m) {
+    if (!m) return HS_OK;
+    void *ps[] = {m->P, m->M, m->V, m->grad, m->loss};
+    for (void *q : ps)
+        if (q) cudaFree(q);
+    delete m;
+    return HS_OK;
+}
+
+hs_status mlp_create(uint64_t seed, void *cuda_stream, hs_mlp **out) {
+    if (!out) return fail(HS_ERR_ARG, "out is NULL");
+    hs_mlp *m = new (std::nothrow) hs_mlp();
+    if (!m) return fail(HS_ERR_OOM, "host allocation failed");
+    m->stream = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaGetDevice(&m->device);
+    for (float **q : {&m->P, &m->M, &m->V, &m->grad})
+        if (e == cudaSuccess) e = cudaMalloc(q, kMlpParams * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&m->loss, 2 * 4);
+    if (e != cudaSuccess) {
+        mlp_destroy(m);
+        return fail(HS_ERR_OOM, "mlp_create: %s", cudaGetErrorString(e));
+    }
+    // uniform(-sqrt(6/fan_in), +sqrt(6/fan_in)) weights from splitmix64, zero biases
+    std::vector<float> P(kMlpParams, 0.0f);
+    uint64_t g = 0;
+    auto uni = [&](double a) {
+        uint64_t x = splitmix64_at(seed, g++);
+        return (float)(((double)(x >> 11) * 0x1p-53 * 2.0 - 1.0) * a);
+    };
+    size_t o = 0;
+    for (int i = 0; i < kMlpH * kMlpIn; ++i) P[o++] = uni(std::sqrt(6.0 / kMlpIn));
+    o += kMlpH;
+    for (int i = 0; i < kMlpH * kMlpH; ++i) P[o++] = uni(std::sqrt(6.0 / kMlpH));
+    o += kMlpH;
+    for (int i = 0; i < kMlpH; ++i) P[o++] = uni(std::sqrt(6.0 / kMlpH));
+    e = cudaMemcpyAsync(m->P, P.data(), kMlpParams * 4, cudaMemcpyHostToDevice, m->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->M, 0, kMlpParams * 4, m->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->V, 0, kMlpParams * 4, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) {
+        mlp_destroy(m);
+        return fail(HS_ERR_CUDA, "mlp_create: %s", cudaGetErrorString(e));
+    }
+    *out = m;
+    return HS_OK;
+}
+
+hs_status mlp_set_params(hs_mlp *m, const float *params) {
+    if (!m || !params) return fail(HS_ERR_ARG, "NULL argument");
+    HS_CUDA(cudaMemcpyAsync(m->P, params, kMlpParams * 4, cudaMemcpyDefault, m->stream));
+    HS_CUDA(cudaMemsetAsync(m->M, 0, kMlpParams * 4, m->stream));
+    HS_CUDA(cudaMemsetAsync(m->V, 0, kMlpParams * 4, m->stream));
+    HS_CUDA(cudaStreamSynchronize(m->stream));
+    m->step = 0;
+    return HS_OK;
+}
+
+hs_status mlp_get_params(hs_mlp *m, float *params) {
+    if (!m || !params) return fail(HS_ERR_ARG, "NULL argument");
+    HS_CUDA(cudaMemcpyAsync(params, m->P, kMlpParams * 4, cudaMemcpyDefault, m->stream));
+    HS_CUDA(cudaStreamSynchronize(m->stream));
+    return HS_OK;
+}
+
+hs_status mlp_forward(hs_mlp *m, const uint16_t *feats, uint64_t n, float *logits) {
+    if (!m || (n && (!feats || !logits))) return fail(HS_ERR_ARG, "NULL argument");
+    if (n == 0) return HS_OK;
+    const uint16_t *df;
+    uint16_t *tf = nullptr;
+    hs_status st = device_input(feats, n * kMlpIn, m->stream, &df, &tf);
+    if (st != HS_OK) return st;
+    const bool ld = host_is_device(logits);
+    float *dl = logits;
+    if (!ld && cudaMalloc(&dl, n * 4) != cudaSuccess) {
+        if (tf) cudaFree(tf);
+        return fail(HS_ERR_OOM, "mlp_forward: no memory for logits");
+    }
+    cudaError_t e = launch_mlp_forward(m->P, df, n, dl, m->stream);
+    if (e == cudaSuccess && !ld) e = cudaMemcpyAsync(logits, dl, n * 4, cudaMemcpyDeviceToHost, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (tf) cudaFree(tf);
+    if (!ld) cudaFree(dl);
+    if (e != cudaSuccess) return fail(HS_ERR_CUDA, "mlp_forward: %s", cudaGetErrorString(e));
+    return HS_OK;
+}
+
+static hs_status mlp_grad_common(hs_mlp *m, const uint16_t *feats, const float *y, const float *w,
+                                 uint64_t n) {
+    const uint16_t *df;
+    const float *dy, *dw;
+    uint16_t *tf = nullptr;
+    float *ty = nullptr, *tw = nullptr;
+    hs_status st = device_input(feats, n * kMlpIn, m->stream, &df, &tf);
+    if (st == HS_OK) st = device_input(y, n, m->stream, &dy, &ty);
+    if (st == HS_OK) st = device_input(w, n, m->stream, &dw, &tw);
+    cudaError_t e = st == HS_OK ? launch_mlp_grad(m->P, df, dy, dw, n, m->grad, m->loss, m->stream)
+                                : cudaSuccess;
+    if (tf || ty || tw) cudaStreamSynchronize(m->stream);
+    if (tf) cudaFree(tf);
+    if (ty) cudaFree(ty);
+    if (tw) cudaFree(tw);
+    if (st != HS_OK) return st;
+    HS_CUDA(e);
+    return HS_OK;
+}
+
+hs_status mlp_gradient(hs_mlp *m, const uint16_t *feats, const float *y, const float *w, uint64_t n,
+                       float *grad, float *loss) {
+    if (!m || !feats || !y || !w || !grad || !loss || n == 0) return fail(HS_ERR_ARG, "bad argument");
+    hs_status st = mlp_grad_common(m, feats, y, w, n);
+    if (st != HS_OK) return st;
+    HS_CUDA(cudaMemcpyAsync(grad, m->grad, kMlpParams * 4, cudaMemcpyDefault, m->stream));
+    HS_CUDA(cudaMemcpyAsync(loss, m->loss, 4, cudaMemcpyDefault, m->stream));
+    HS_CUDA(cudaStreamSynchronize(m->stream));
+    return HS_OK;
+}
+
+hs_status mlp_train_step(hs_mlp *m, const uint16_t *feats, const float *y, const float *w,
+                         uint64_t n, float lr, float *loss) {
+    if (!m || !feats || !y || !w || n == 0 || !(lr > 0)) return fail(HS_ERR_ARG, "bad argument");
+    hs_status st = mlp_grad_common(m, feats, y, w, n);
+    if (st != HS_OK) return st;
+    m->step += 1;
+    HS_CUDA(launch_adam(m->P, m->M, m->V, m->grad, m->loss + 1, lr, m->step, m->stream));
+    if (loss) {
+        float l[2];
+        HS_CUDA(cudaMemcpyAsync(l, m->loss, 8, cudaMemcpyDeviceToHost, m->stream));
+        HS_CUDA(cudaStreamSynchronize(m->stream));
+        *loss = l[1] > 0 ? l[0] / l[1] : 0.0f;
+    }
+    return HS_OK;
+}
+
+hs_status exact_counts(const float *xyz, uint64_t n, double box, double cell, uint32_t log2_slots,
+                       void *cuda_stream, uint64_t *keys, int32_t *counts, uint64_t cap,
+                       uint64_t *n_out) {
+    if (!n_out || (n && !xyz) || log2_slots < 4 || log2_slots > 34)
+        return fail(HS_ERR_ARG, "bad argument");
+    hs_params p{1, 1, box, cell, 0, 0, 0, 0};
+    hs_status st = check_params(&p);
+    if (st != HS_OK) return st;
+    if (n && !is_device_ptr(xyz)) return fail(HS_ERR_ARG, "xyz must be device memory");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    SketchDesc d{};
+    d.G = (uint32_t)std::llround(box / cell);
+    d.inv_cell = (float)(1.0 / cell);
+    const uint64_t slots = 1ull << log2_slots;
+    unsigned long long *tk = nullptr, *cnt = nullptr;
+    int32_t *tc = nullptr;
+    uint32_t *ovf = nullptr;
+    cudaError_t e = cudaMalloc(&tk, slots * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&tc, slots * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&ovf, 4);
+    if (e == cudaSuccess) e = cudaMalloc(&cnt, 8);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tk, 0xFF, slots * 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tc, 0, slots * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ovf, 0, 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, 8, s);
+    if (e == cudaSuccess) e = launch_exact_count(xyz, n, d, tk, tc, slots, ovf, s);
+    uint64_t *dk = keys;
+    int32_t *dc = counts;
+    const bool dev_out = keys && is_device_ptr(keys);
+    if (e == cudaSuccess && keys && !dev_out) {
+        e = cudaMalloc(&dk, std::max<uint64_t>(cap, 1) * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&dc, std::max<uint64_t>(cap, 1) * 4);
+    }
+    if (e == cudaSuccess && keys) e = launch_table_list(tk, tc, slots, dk, dc, cnt, cap, s);
+    unsigned long long nn = 0;
+    uint32_t of = 0;
+    if (e == cudaSuccess && !keys) {                 // only the number of distinct cells
+        e = launch_table_list(tk, tc, slots, nullptr, nullptr, cnt, 0, s);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nn, cnt, 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&of, ovf, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && keys && !dev_out) {
+        uint64_t m = std::min<uint64_t>(nn, cap);
+        e = cudaMemcpy(keys, dk, m * 8, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(counts, dc, m * 4, cudaMemcpyDeviceToHost);
+    }
+    if (keys && !dev_out) {
+        if (dk) cudaFree(dk);
+        if (dc) cudaFree(dc);
+    }
+    cudaFree(tk);
+    cudaFree(tc);
+    cudaFree(ovf);
+    cudaFree(cnt);
+    if (e != cudaSuccess) return fail(HS_ERR_CUDA, "exact_counts: %s", cudaGetErrorString(e));
+    *n_out = nn;
+    if (of) return fail(HS_ERR_TABLE_FULL, "exact_counts: 2^%u slots are too few", log2_slots);
+    return HS_OK;
+}
+
+hs_status learned_destroy(hs_learned *L) {
+    if (!L) return HS_OK;
+    if (L->sk) sketch_destroy(L->sk);
+    learned_free(L);
+    delete L;
+    return HS_OK;
+}
+
+hs_status learned_create(const hs_params *params, uint32_t coarse_factor, uint32_t table_log2,
+                         uint64_t feature_seed, double feature_rate, void *cuda_stream,
+                         hs_learned **out) {
+    if (!out || !params) return fail(HS_ERR_ARG, "NULL argument");
+    if (coarse_factor < 1 || coarse_factor > 64 || table_log2 < 4 || table_log2 > 32 ||
+        !(feature_rate > 0 && feature_rate <= 1))
+        return fail(HS_ERR_ARG, "bad coarse factor, table size or feature rate");
+    const uint64_t R3 = (uint64_t)coarse_factor * coarse_factor * coarse_factor;
+    const uint64_t max_blocks = (3ull << table_log2) / R3;   // 12-byte slots -> 4-byte counters
+    if (max_blocks == 0) return fail(HS_ERR_ARG, "the table holds no block of R^3 counters");
+    hs_sketch *sk = nullptr;
+    hs_status st = sketch_create(params, cuda_stream, &sk);
+    if (st != HS_OK) return st;
+    if (sk->d.G % coarse_factor != 0 || sk->d.G > 65535 || sk->bl.slot == 0) {
+        sketch_destroy(sk);
+        return fail(HS_ERR_ARG, "the mesh must be a multiple of the coarse factor, below 2^16, "
+                    "and the sketch must allow the binned update");
+    }
+    hs_learned *L = new (std::nothrow) hs_learned();
+    if (!L) {
+        sketch_destroy(sk);
+        return fail(HS_ERR_OOM, "host allocation failed");
+    }
+    L->sk = sk;
+    L->R = coarse_factor;
+    L->Gc = sk->d.G / coarse_factor;
+    L->ncoarse = (uint64_t)L->Gc * L->Gc * L->Gc;
+    L->words = (L->ncoarse + 31) / 32;
+    while (L->coarse_key_bits < 64 && (1ull << L->coarse_key_bits) < L->ncoarse) ++L->coarse_key_bits;
+    L->feature_seed = feature_seed;
+    L->feature_rate = feature_rate;
+    L->max_blocks = max_blocks;
+    cudaStream_t s = sk->stream;
+    cudaError_t e = cudaMalloc(&L->coarse, L->ncoarse * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&L->routed, L->words * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&L->prefix, L->words * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&L->scan_scratch, (L->words / 1024 + 4096) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&L->blocks, max_blocks * R3 * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&L->rlist, max_blocks * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&L->ctr, 4 * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&L->ftab, kFeatTab * 2);
+    if (e == cudaSuccess) {
+        std::vector<uint16_t> t(kFeatTab);
+        for (uint32_t c = 0; c < kFeatTab; ++c)
+            t[c] = host_bf16((float)std::log10(1.0 + (double)c));   // double -> float -> bf16
+        e = cudaMemcpy(L->ftab, t.data(), kFeatTab * 2, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(L->routed, 0, L->words * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L->prefix, 0, L->words * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L->blocks, 0, max_blocks * R3 * 4, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        learned_destroy(L);
+        return fail(HS_ERR_OOM, "learned_create: %s", cudaGetErrorString(e));
+    }
+    sk->route.filter = RouteFilter{L->routed, (uint32_t)((0x100000000ull + coarse_factor - 1) / coarse_factor),
+                                   L->Gc, coarse_factor};
+    sk->route.prefix = L->prefix;
+    sk->route.blocks = L->blocks;
+    sk->min_cap = max_blocks * R3;
+    *out = L;
+    return HS_OK;
+}
+
+hs_status learned_capacity(hs_learned *L, uint64_t *max_routed, uint64_t *table_bytes) {
+    if (!L) return fail(HS_ERR_ARG, "NULL handle");
+    if (max_routed) *max_routed = L->max_blocks;
+    if (table_bytes) *table_bytes = L->max_blocks * L->R * L->R * L->R * 4;
+    return HS_OK;
+}
+
+hs_status learned_prepare(hs_learned *L, const float *xyz, uint64_t n, hs_mlp *mlp,
+                          uint64_t *n_routed) {
+    if (!L || !mlp || (n && !xyz)) return fail(HS_ERR_ARG, "NULL argument");
+    if (n && !is_device_ptr(xyz)) return fail(HS_ERR_ARG, "xyz must be device memory");
+    hs_sketch *sk = L->sk;
+    cudaStream_t s = sk->stream;
+    int launches = 0;
+    HS_CUDA(cudaMemsetAsync(L->coarse, 0, L->ncoarse * 4, s));
+    HS_CUDA(cudaMemsetAsync(L->ctr, 0, 4 * 8, s));
+    HS_CUDA(launch_coarse_hist(xyz, n, 0, sk->d, L->R, L->Gc, L->feature_seed, L->feature_rate,
+                               L->coarse, s));
+    // list the coarse cells with a sample (size known only on the device: count first)
+    HS_CUDA(launch_coarse_list(L->coarse, L->ncoarse, nullptr, &L->ctr[0], 0, s));
+    unsigned long long nl = 0;
+    HS_CUDA(cudaMemcpyAsync(&nl, &L->ctr[0], 8, cudaMemcpyDeviceToHost, s));
+    HS_CUDA(cudaStreamSynchronize(s));
+    if (nl > L->clist_cap) {
+        void *old[] = {L->clist, L->feats, L->logits, L->lrank};
+        for (void *q : old)
+            if (q) cudaFree(q);
+        L->clist = nullptr;
+        L->feats = nullptr;
+        L->logits = nullptr;
+        L->lrank = nullptr;
+        L->clist_cap = std::max<uint64_t>(nl, 1024);
+        HS_CUDA(cudaMalloc(&L->clist, L->clist_cap * 8));
+        HS_CUDA(cudaMalloc(&L->feats, L->clist_cap * kMlpIn * 2));
+        HS_CUDA(cudaMalloc(&L->logits, L->clist_cap * 4));
+        HS_CUDA(cudaMalloc(&L->lrank, L->clist_cap * 4));
+    }
+    HS_CUDA(cudaMemsetAsync(&L->ctr[0], 0, 8, s));
+    HS_CUDA(launch_coarse_list(L->coarse, L->ncoarse, L->clist, &L->ctr[0], L->clist_cap, s));
+    HS_CUDA(launch_features(L->coarse, L->Gc, L->clist, nl, L->ftab, kFeatTab, L->feats, s));
+    HS_CUDA(launch_mlp_forward(mlp->P, L->feats, nl, L->logits, s));
+    HS_CUDA(launch_logit_rank(L->logits, nl, L->lrank, &L->ctr[1], s));
+    unsigned long long npos = 0;
+    HS_CUDA(cudaMemcpyAsync(&npos, &L->ctr[1], 8, cudaMemcpyDeviceToHost, s));
+    HS_CUDA(cudaStreamSynchronize(s));
+    launches += 6;
+    // over budget: keep the max_blocks cells of largest logit (ties: smaller key)
+    const int use_sel = npos > L->max_blocks;
+    if (use_sel) {
+        hs_status st = ensure_topk_scratch(sk, 1);
+        if (st != HS_OK) return st;
+        HS_CUDA(launch_select_kth(L->clist, L->lrank, nl, L->max_blocks, L->coarse_key_bits,
+                                  sk->sel, sk->hist, sk->num_sms * 4, s, &launches));
+    }
+    HS_CUDA(cudaMemsetAsync(L->routed, 0, L->words * 4, s));
+    HS_CUDA(launch_route(L->clist, L->lrank, nl, use_sel ? sk->sel : nullptr, use_sel, L->routed, s));
+    HS_CUDA(launch_word_popc(L->routed, L->words, L->prefix, s));
+    HS_CUDA(launch_exclusive_scan(L->prefix, L->prefix, L->words, L->scan_scratch, s, &launches));
+    HS_CUDA(launch_route_list(L->clist, nl, L->routed, L->prefix, L->rlist, s));
+    const uint64_t nr = use_sel ? L->max_blocks : npos;
+    const uint64_t R3 = (uint64_t)L->R * L->R * L->R;
+    HS_CUDA(cudaMemsetAsync(L->blocks, 0, L->max_blocks * R3 * 4, s));
+    HS_CUDA(cudaStreamSynchronize(s));
+    launches += 3;
+    sk->stats.kernel_launches += launches;
+    L->n_list = nl;
+    L->n_routed = nr;
+    sk->routing = true;
+    if (n_routed) *n_routed = nr;
+    return HS_OK;
+}
+
+hs_status learned_update(hs_learned *L, const float *xyz, uint64_t n, double sample_rate) {
+    if (!L) return fail(HS_ERR_ARG, "NULL handle");
+    if (!L->sk->routing) return fail(HS_ERR_STATE, "call learned_prepare first");
+    return sketch_update(L->sk, xyz, n, sample_rate);
+}
+
+hs_status learned_topk(hs_learned *L, uint32_t k, uint64_t *keys, int32_t *est, uint32_t *n_out) {
+    if (!L || k == 0 || !keys || !est || !n_out) return fail(HS_ERR_ARG, "bad argument");
+    hs_sketch *h = L->sk;
+    uint32_t n1 = 0;
+    hs_status st = topk_extract(h, k, keys, est, &n1);   // leaves the ranking in h->out_*
+    if (st != HS_OK) return st;
+    // candidates: the sketch's ranking, then every non-zero exact counter
+    HS_CUDA(cudaMemcpyAsync(h->cand_key, h->out_key, n1 * 8, cudaMemcpyDeviceToDevice, h->stream));
+    HS_CUDA(cudaMemcpyAsync(h->cand_est, h->out_est, n1 * 4, cudaMemcpyDeviceToDevice, h->stream));
+    HS_CUDA(cudaMemsetAsync(&L->ctr[2], 0, 8, h->stream));
+    HS_CUDA(launch_block_list(L->blocks, L->rlist, L->n_routed, L->R, L->Gc, h->d.G,
+                              h->cand_key + n1, h->cand_est + n1, &L->ctr[2], h->cap - n1,
+                              h->stream));
+    unsigned long long nt = 0;
+    HS_CUDA(cudaMemcpyAsync(&nt, &L->ctr[2], 8, cudaMemcpyDeviceToHost, h->stream));
+    HS_CUDA(cudaStreamSynchronize(h->stream));
+    h->stats.kernel_launches += 1;
+    if (nt > h->cap - n1) return fail(HS_ERR_STATE, "too many exact counts for the candidates");
+    const uint64_t m = n1 + nt;
+    const uint64_t kk = std::min<uint64_t>(k, m);
+    if (m == 0) {
+        *n_out = 0;
+        return HS_OK;
+    }
+    st = finalize(h, m, kk);
+    if (st != HS_OK) return st;
+    HS_CUDA(cudaMemcpyAsync(keys, h->out_key, kk * 8, cudaMemcpyDeviceToHost, h->stream));
+    HS_CUDA(cudaMemcpyAsync(est, h->out_est, kk * 4, cudaMemcpyDeviceToHost, h->stream));
+    HS_CUDA(cudaStreamSynchronize(h->stream));
+    *n_out = (uint32_t)kk;
+    return HS_OK;
+}
+
+hs_status learned_table(hs_learned *L, uint64_t *keys, int32_t *counts, uint64_t cap,
+                        uint64_t *n_out) {
+    if (!L || !n_out || (cap && (!keys || !counts))) return fail(HS_ERR_ARG, "bad argument");
+    cudaStream_t s = L->sk->stream;
+    hs_status st = drain(L->sk);
+    if (st != HS_OK) return st;
+    uint64_t *dk = nullptr;
+    int32_t *dc = nullptr;
+    if (cap) {
+        HS_CUDA(cudaMalloc(&dk, cap * 8));
+        HS_CUDA(cudaMalloc(&dc, cap * 4));
+    }
+    HS_CUDA(cudaMemsetAsync(&L->ctr[2], 0, 8, s));
+    HS_CUDA(launch_block_list(L->blocks, L->rlist, L->n_routed, L->R, L->Gc, L->sk->d.G, dk, dc,
+                              &L->ctr[2], cap, s));
+    unsigned long long nt = 0;
+    HS_CUDA(cudaMemcpyAsync(&nt, &L->ctr[2], 8, cudaMemcpyDeviceToHost, s));
+    HS_CUDA(cudaStreamSynchronize(s));
+    uint64_t m = std::min<uint64_t>(nt, cap);
+    cudaError_t e = cudaSuccess;
+    if (m) {
+        e = cudaMemcpy(keys, dk, m * 8, cudaMemcpyDefault);
+        if (e == cudaSuccess) e = cudaMemcpy(counts, dc, m * 4, cudaMemcpyDefault);
+    }
+    if (dk) cudaFree(dk);
+    if (dc) cudaFree(dc);
+    if (e != cudaSuccess) return fail(HS_ERR_CUDA, "learned_table: %s", cudaGetErrorString(e));
+    *n_out = nt;
+    return HS_OK;
+}
+
+hs_status learned_routed(hs_learned *L, uint64_t *coarse_keys, uint64_t cap, uint64_t *n_out) {
+    if (!L || !n_out || (cap && !coarse_keys)) return fail(HS_ERR_ARG, "bad argument");
+    uint64_t m = std::min<uint64_t>(L->n_routed, cap);
+    if (m) HS_CUDA(cudaMemcpy(coarse_keys, L->rlist, m * 8, cudaMemcpyDefault));
+    *n_out = L->n_routed;
+    return HS_OK;
+}
+
+hs_status learned_logits(hs_learned *L, uint64_t *coarse_keys, float *logits, uint64_t cap,
+                         uint64_t *n_out) {
+    if (!L || !n_out) return fail(HS_ERR_ARG, "bad argument");
+    uint64_t m = std::min<uint64_t>(L->n_list, cap);
+    if (m) {
+        HS_CUDA(cudaMemcpy(coarse_keys, L->clist, m * 8, cudaMemcpyDefault));
+        HS_CUDA(cudaMemcpy(logits, L->logits, m * 4, cudaMemcpyDefault));
+    }
+    *n_out = L->n_list;
+    return HS_OK;
+}
+
+hs_status learned_coarse_counts(hs_learned *L, int32_t *out) {
+    if (!L || !out) return fail(HS_ERR_ARG, "bad argument");
+    HS_CUDA(cudaMemcpyAsync(out, L->coarse, L->ncoarse * 4, cudaMemcpyDefault, L->sk->stream));
+    HS_CUDA(cudaStreamSynchronize(L->sk->stream));
+    return HS_OK;
+}
+
+hs_status learned_features(hs_learned *L, uint16_t *feats, uint64_t cap, uint64_t *n_out) {
+    if (!L || !n_out) return fail(HS_ERR_ARG, "bad argument");
+    uint64_t m = std::min<uint64_t>(L->n_list, cap);
+    if (m) HS_CUDA(cudaMemcpy(feats, L->feats, m * kMlpIn * 2, cudaMemcpyDefault));
+    *n_out = L->n_list;
+    return HS_OK;
+}
+
+hs_status learned_sketch(hs_learned *L, hs_sketch **out) {
+    if (!L || !out) return fail(HS_ERR_ARG, "bad argument");
+    *out = L->sk;
+    return HS_OK;
+}
+
+hs_status learned_reset(hs_learned *L) {
+    if (!L) return fail(HS_ERR_ARG, "NULL handle");
+    hs_status st = sketch_reset(L->sk);
+    if (st != HS_OK) return st;
+    const uint64_t R3 = (uint64_t)L->R * L->R * L->R;
+    HS_CUDA(cudaMemsetAsync(L->blocks, 0, L->max_blocks * R3 * 4, L->sk->stream));
     return HS_OK;
 }
 

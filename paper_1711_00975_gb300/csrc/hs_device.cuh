@@ -12,6 +12,12 @@
 namespace hs {
 
 constexpr int kMaxRows = 32;
+// learned router: MLP 27 -> 64 -> 64 -> 1, parameters w1[64][27], b1[64],
+// w2[64][64], b2[64], w3[64], b3 in that order
+constexpr int kMlpIn = 27;
+constexpr int kMlpH = 64;
+constexpr int kMlpParams = kMlpH * kMlpIn + kMlpH + kMlpH * kMlpH + kMlpH + kMlpH + 1;
+constexpr int kTableProbes = 64;   // slots tried per key in the exact tables
 constexpr uint64_t kInvalidKey = 0xFFFFFFFFFFFFFFFFull;
 constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;   // splitmix64 increment
 
@@ -157,6 +163,49 @@ __host__ __device__ __forceinline__ int32_t median5(int32_t a, int32_t b, int32_
         if (c > d) { t = c; c = d; d = t; }
     }
     return (a < c) ? (b < c ? b : c) : (a < d ? a : d);
+}
+
+// Cells of coarse cells marked in `bits` (one bit per coarse cell, coarse cell =
+// fine cell / R per axis on a Gc^3 mesh) are counted outside the sketch.
+struct RouteFilter {
+    const uint32_t *bits;   // nullptr: nothing is routed
+    uint32_t rmagic;        // ceil(2^32 / R): x / R = umulhi(x, rmagic) for x, R < 2^16
+    uint32_t Gc;
+    uint32_t R;             // coarse factor
+};
+
+__device__ __forceinline__ bool routed_cell(const RouteFilter &f, uint32_t cx, uint32_t cy,
+                                            uint32_t cz) {
+    const uint32_t qx = __umulhi(cx, f.rmagic), qy = __umulhi(cy, f.rmagic),
+                   qz = __umulhi(cz, f.rmagic);
+    const uint64_t ck = (uint64_t)qx + (uint64_t)f.Gc * (qy + (uint64_t)f.Gc * qz);
+    return (__ldg(f.bits + (ck >> 5)) >> (ck & 31)) & 1u;
+}
+
+// ---- exact open-addressing table: uint64 key (empty = all ones) + int32 count ----
+__device__ __forceinline__ uint64_t table_hash(uint64_t k) {
+    k ^= k >> 33;
+    k *= 0xFF51AFD7ED558CCDull;
+    k ^= k >> 33;
+    k *= 0xC4CEB9FE1A85EC53ull;
+    return k ^ (k >> 33);
+}
+
+// Count one particle of cell `key`; false when max_probe slots (linear probing
+// from the key's hash) were all taken by other keys.
+__device__ __forceinline__ bool table_add(unsigned long long *keys, int32_t *counts, uint64_t mask,
+                                          uint64_t key, int max_probe) {
+    uint64_t s = table_hash(key) & mask;
+    for (int p = 0; p < max_probe; ++p) {
+        const unsigned long long cur = atomicCAS(&keys[s], (unsigned long long)kInvalidKey,
+                                                 (unsigned long long)key);
+        if (cur == kInvalidKey || cur == key) {
+            atomicAdd(&counts[s], 1);
+            return true;
+        }
+        s = (s + 1) & mask;
+    }
+    return false;
 }
 
 }  // namespace hs

@@ -33,14 +33,60 @@ struct BinLayout {
     size_t smem;       // dynamic shared memory of the scatter kernel
 };
 BinLayout bin_layout(const SketchDesc &d, size_t smem_budget);
+// where routed particles go: one dense block of R^3 int32 counters per routed
+// coarse cell, blocks in coarse-key order; the block of routed cell ck is
+// prefix[ck / 32] + (number of routed cells below ck in its bitmap word)
+struct RouteTarget {
+    RouteFilter filter;
+    const uint32_t *prefix;   // exclusive prefix count of routed cells per bitmap word
+    int32_t *blocks;
+};
 cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const SketchDesc &d,
                                int32_t *C, double rate, uint64_t sample_seed, uint64_t *probe,
                                uint64_t probe_base, uint64_t probe_cap, const BinLayout &L,
                                uint16_t *bins, uint32_t *cursor, uint32_t cap, int blocks,
                                cudaStream_t s, const VolumeDesc *vols = nullptr, uint32_t nvol = 0,
-                               uint32_t probe_per_vol = 0, int threads = 1024);
+                               uint32_t probe_per_vol = 0, int threads = 1024,
+                               const RouteTarget *route = nullptr);
 cudaError_t launch_bin_accumulate(const BinLayout &L, uint16_t *bins, uint32_t *cursor,
                                   uint32_t cap, int32_t *C, cudaStream_t s);
+
+// ---- learned router (k_learned.cu) ----
+cudaError_t launch_coarse_hist(const float *xyz, uint64_t n, uint64_t g0, const SketchDesc &d,
+                               uint32_t R, uint32_t Gc, uint64_t seed, double rate,
+                               int32_t *counts, cudaStream_t s);
+cudaError_t launch_coarse_list(const int32_t *counts, uint64_t ncoarse, uint64_t *list,
+                               unsigned long long *n_list, uint64_t cap, cudaStream_t s);
+cudaError_t launch_features(const int32_t *counts, uint32_t Gc, const uint64_t *list, uint64_t m,
+                            const uint16_t *ftab, uint32_t ftab_n, uint16_t *feats,
+                            cudaStream_t s);
+cudaError_t launch_mlp_forward(const float *P, const uint16_t *feats, uint64_t m, float *logits,
+                               cudaStream_t s);
+cudaError_t launch_mlp_grad(const float *P, const uint16_t *feats, const float *y, const float *w,
+                            uint64_t m, float *grad, float *loss, cudaStream_t s);
+// loss[0] += sum w * bce, loss[1] += sum w (both zeroed first)
+cudaError_t launch_adam(float *P, float *M, float *V, const float *grad, const float *gscale,
+                        float lr, int step, cudaStream_t s);
+cudaError_t launch_logit_rank(const float *logits, uint64_t m, int32_t *rank,
+                              unsigned long long *n_pos, cudaStream_t s);
+struct SelectState;
+cudaError_t launch_route(const uint64_t *list, const int32_t *rank, uint64_t m,
+                         const SelectState *sel, int use_sel, uint32_t *bits, cudaStream_t s);
+cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *scratch,
+                                  cudaStream_t s, int *launches);
+cudaError_t launch_word_popc(const uint32_t *bits, uint64_t words, uint32_t *out, cudaStream_t s);
+cudaError_t launch_route_list(const uint64_t *list, uint64_t m, const uint32_t *bits,
+                              const uint32_t *prefix, uint64_t *rlist, cudaStream_t s);
+cudaError_t launch_block_list(const int32_t *blocks, const uint64_t *rlist, uint64_t nblocks,
+                              uint32_t R, uint32_t Gc, uint32_t G, uint64_t *out_keys,
+                              int32_t *out_counts, unsigned long long *n_out, uint64_t cap,
+                              cudaStream_t s);
+cudaError_t launch_exact_count(const float *xyz, uint64_t n, const SketchDesc &d,
+                               unsigned long long *keys, int32_t *counts, uint64_t slots,
+                               uint32_t *overflow, cudaStream_t s);
+cudaError_t launch_table_list(const unsigned long long *keys, const int32_t *counts, uint64_t slots,
+                              uint64_t *out_keys, int32_t *out_counts, unsigned long long *n_out,
+                              uint64_t cap, cudaStream_t s);
 
 // dst[i] += src[i] (int32 wrap-around), the merge of two sketches
 cudaError_t launch_add_counters(int32_t *dst, const int32_t *src, uint64_t n, cudaStream_t s);
@@ -67,7 +113,7 @@ cudaError_t launch_hot_bitmap(const int32_t *C, const SketchDesc &d, uint32_t nb
 cudaError_t launch_full_search(const int32_t *C, const SketchDesc &d, int32_t theta,
                                SearchMode mode, const uint32_t *bitmap, uint32_t nb, int prune,
                                uint64_t line_lo, uint64_t line_hi, SearchOut out, int blocks,
-                               cudaStream_t s);
+                               cudaStream_t s, RouteFilter skip = RouteFilter{nullptr, 0, 0, 0});
 // est[i] = Estimate(keys[i]); keys >= G^3 give 0 and set *bad
 cudaError_t launch_point_query(const int32_t *C, const SketchDesc &d, const uint64_t *keys,
                                uint64_t m, int32_t *est, uint32_t *bad, cudaStream_t s);
@@ -95,7 +141,7 @@ cudaError_t launch_dir_query(const int32_t *C, const SketchDesc &d, int r, uint3
                              const uint32_t *offsets, const DirRecord *rec, const uint32_t *hot,
                              uint64_t n_hot, const uint32_t *bits, int32_t theta, SearchMode mode,
                              uint64_t line_lo, uint64_t line_hi, SearchOut out, int max_blocks,
-                             cudaStream_t s);
+                             cudaStream_t s, RouteFilter skip = RouteFilter{nullptr, 0, 0, 0});
 
 // ---- ranking (k_select.cu) ----
 struct SelectState {

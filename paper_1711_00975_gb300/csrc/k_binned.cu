@@ -44,6 +44,9 @@ struct ScatterArgs {
     uint32_t log2_slot;
     uint16_t *bins;       // nbins x cap codes
     uint32_t *cursor;     // fill of each global bin (may exceed cap)
+    RouteFilter route;        // routed cells go to exact dense blocks instead
+    const uint32_t *rprefix;
+    int32_t *rblocks;
     const VolumeDesc *vols;   // batch: one entry per volume (nullptr for one sketch)
     uint32_t nvol;
     uint32_t probe_per_vol;   // batch: probe window of each volume
@@ -75,6 +78,21 @@ __device__ __noinline__ void write_probe(uint64_t *probe, uint64_t g, bool valid
     probe[g] = valid ? key_of(cx, cy, cz, G) : kInvalidKey;
 }
 
+// one exact count for a particle of a routed coarse cell: its block is the
+// cell's rank among the routed cells, its counter the fine cell's offset
+// (x fastest) inside the coarse cell
+__device__ __noinline__ void route_add(const ScatterArgs &a, uint32_t cx, uint32_t cy,
+                                       uint32_t cz) {
+    const RouteFilter &f = a.route;
+    const uint32_t qx = __umulhi(cx, f.rmagic), qy = __umulhi(cy, f.rmagic),
+                   qz = __umulhi(cz, f.rmagic);
+    const uint64_t ck = (uint64_t)qx + (uint64_t)f.Gc * (qy + (uint64_t)f.Gc * qz);
+    const uint32_t w = (uint32_t)(ck >> 5), b = (uint32_t)(ck & 31);
+    const uint32_t blk = __ldg(a.rprefix + w) + __popc(__ldg(f.bits + w) & ((1u << b) - 1u));
+    const uint32_t local = (cx - qx * f.R) + f.R * ((cy - qy * f.R) + f.R * (cz - qz * f.R));
+    atomicAdd(&a.rblocks[(uint64_t)blk * (f.R * f.R * f.R) + local], 1);
+}
+
 // Mesh reduction, sampling and probe entry of one particle; true when it is
 // kept, with its cell packed as cx | cy << 21 | cz << 42 (G <= 2^21).
 __device__ __forceinline__ bool prep_particle(float x, float y, float z, uint64_t g,
@@ -85,9 +103,15 @@ __device__ __forceinline__ bool prep_particle(float x, float y, float z, uint64_
     bool valid = axis_cell(x, d.inv_cell, d.G, cx);
     valid &= axis_cell(y, d.inv_cell, d.G, cy);
     valid &= axis_cell(z, d.inv_cell, d.G, cz);
-    if (g - a.probe_base < a.probe_end - a.probe_base)
-        write_probe(a.probe, g - a.probe_base, valid, cx, cy, cz, d.G);
+    bool routed = false;
+    if (a.route.bits && valid) routed = routed_cell(a.route, cx, cy, cz);
+    if (g - a.probe_base < a.probe_end - a.probe_base)   // the sketch's cells only
+        write_probe(a.probe, g - a.probe_base, valid && !routed, cx, cy, cz, d.G);
     cell = (uint64_t)cx | ((uint64_t)cy << 21) | ((uint64_t)cz << 42);
+    if (routed && keep) {
+        route_add(a, cx, cy, cz);
+        return false;
+    }
     return keep && valid;
 }
 
@@ -449,7 +473,7 @@ cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const 
                                uint64_t probe_base, uint64_t probe_cap, const BinLayout &L, uint16_t *bins,
                                uint32_t *cursor, uint32_t cap, int blocks, cudaStream_t s,
                                const VolumeDesc *vols, uint32_t nvol, uint32_t probe_per_vol,
-                               int threads) {
+                               int threads, const RouteTarget *route) {
     if (n == 0) return cudaSuccess;
     // bin arrays are read and written as 16-byte vectors: every bin must start
     // on a 16-byte boundary
@@ -476,6 +500,9 @@ cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const 
     while ((1u << a.log2_slot) < L.slot) ++a.log2_slot;
     a.bins = bins;
     a.cursor = cursor;
+    a.route = route ? route->filter : RouteFilter{nullptr, 0, 0, 0};
+    a.rprefix = route ? route->prefix : nullptr;
+    a.rblocks = route ? route->blocks : nullptr;
     a.vols = vols;
     a.nvol = vols ? nvol : 0;
     a.probe_per_vol = probe_per_vol;

@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(256)
                 const uint32_t *__restrict__ offsets, const DirRecord *__restrict__ rec,
                 const uint32_t *__restrict__ hot, uint64_t n_hot,
                 const uint32_t *__restrict__ bits, int32_t theta, uint32_t mode, uint64_t line_lo,
-                uint64_t line_hi, SearchOut out) {
+                uint64_t line_hi, SearchOut out, RouteFilter skip) {
     const uint32_t rows = T > 0 ? (uint32_t)T : d.rows;
     const uint32_t need = rows - (rows - 1) / 2;
     const uint64_t words_per_row = d.W >> 5 ? d.W >> 5 : 1;
@@ -170,6 +170,7 @@ __global__ void __launch_bounds__(256)
                 if (((R.L + Tx) >> s) != h) continue;
                 const uint64_t line = (uint64_t)R.cy + (uint64_t)d.G * R.cz;
                 if (line < line_lo || line >= line_hi) continue;
+                if (skip.bits && routed_cell(skip, cx, R.cy, R.cz)) continue;
                 // reported from the first hot row only; count the hot rows
                 uint64_t v[T > 0 ? T : kMaxRows];
                 bool first = true;
@@ -201,6 +202,13 @@ __global__ void __launch_bounds__(256)
 }
 
 }  // namespace
+
+// exclusive prefix sum of n uint32 (in place allowed); scratch: n / 1024 + 4096 words
+cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t *out, uint64_t n, uint32_t *scratch,
+                                  cudaStream_t s, int *launches) {
+    if (n == 0) return cudaSuccess;
+    return exclusive_scan(in, out, n, scratch, s, launches);
+}
 
 cudaError_t launch_dir_build(const SketchDesc &d, int r, uint32_t D, uint32_t *offsets,
                              uint32_t *cursor, DirRecord *rec, uint32_t *scan_scratch,
@@ -236,17 +244,17 @@ cudaError_t launch_dir_query(const int32_t *C, const SketchDesc &d, int r, uint3
                              const uint32_t *offsets, const DirRecord *rec, const uint32_t *hot,
                              uint64_t n_hot, const uint32_t *bits, int32_t theta, SearchMode mode,
                              uint64_t line_lo, uint64_t line_hi, SearchOut out, int max_blocks,
-                             cudaStream_t s) {
+                             cudaStream_t s, RouteFilter skip) {
     uint64_t total = n_hot * d.G;
     if (total == 0) return cudaSuccess;
     uint64_t blocks = (total + 255) / 256;
     if (blocks > (uint64_t)max_blocks) blocks = (uint64_t)max_blocks;
     if (d.rows == 5)
         k_dir_query<5><<<(unsigned)blocks, 256, 0, s>>>(C, d, r, D, offsets, rec, hot, n_hot, bits,
-                                                       theta, mode, line_lo, line_hi, out);
+                                                       theta, mode, line_lo, line_hi, out, skip);
     else
         k_dir_query<0><<<(unsigned)blocks, 256, 0, s>>>(C, d, r, D, offsets, rec, hot, n_hot, bits,
-                                                       theta, mode, line_lo, line_hi, out);
+                                                       theta, mode, line_lo, line_hi, out, skip);
     return cudaGetLastError();
 }
 

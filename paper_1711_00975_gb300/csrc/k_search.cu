@@ -56,7 +56,7 @@ template <int T>
 __global__ void __launch_bounds__(1024, 1)
     k_full_search(const int32_t *__restrict__ C, const SketchDesc d, int32_t theta, uint32_t mode,
                   const uint32_t *__restrict__ bitmap, uint32_t nb, int prune, uint64_t line_lo,
-                  uint64_t line_hi, SearchOut out) {
+                  uint64_t line_hi, SearchOut out, RouteFilter skip) {
     extern __shared__ uint32_t s_bits[];
     const uint32_t rows = T > 0 ? (uint32_t)T : d.rows;
     const uint32_t words_per_row = (1u << nb) >> 5 ? (1u << nb) >> 5 : 1u;
@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(1024, 1)
             }
             int32_t e = 0;
             bool pass = false;
+            if (cand && skip.bits && routed_cell(skip, cx, cy, cz)) cand = false;
             if (cand) {
                 if (T == 5) {
                     int32_t r0 = signed_count(__ldg(C + bucket_of(v[0], d.log2w)), v[0], d.log2w);
@@ -241,7 +242,7 @@ cudaError_t launch_hot_bitmap(const int32_t *C, const SketchDesc &d, uint32_t nb
 cudaError_t launch_full_search(const int32_t *C, const SketchDesc &d, int32_t theta,
                                SearchMode mode, const uint32_t *bitmap, uint32_t nb, int prune,
                                uint64_t line_lo, uint64_t line_hi, SearchOut out, int blocks,
-                               cudaStream_t s) {
+                               cudaStream_t s, RouteFilter skip) {
     if (line_hi <= line_lo) return cudaSuccess;
     uint64_t words_per_row = (1ull << nb) >> 5 ? (1ull << nb) >> 5 : 1;
     size_t smem = prune ? (size_t)d.rows * words_per_row * 4 : 0;
@@ -253,12 +254,12 @@ cudaError_t launch_full_search(const int32_t *C, const SketchDesc &d, int32_t th
         auto k = k_full_search<5>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<(unsigned)b, 1024, smem, s>>>(C, d, theta, mode, bitmap, nb, prune, line_lo, line_hi,
-                                         out);
+                                         out, skip);
     } else {
         auto k = k_full_search<0>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<(unsigned)b, 1024, smem, s>>>(C, d, theta, mode, bitmap, nb, prune, line_lo, line_hi,
-                                         out);
+                                         out, skip);
     }
     return cudaGetLastError();
 }

@@ -108,6 +108,28 @@ def lib():
                 "batch_stats": [vp, ctypes.POINTER(hs_stats), ci],
                 "batch_autotune": [vp, vp, vp, f64, ctypes.POINTER(hs_tune)],
                 "batch_destroy": [vp],
+                "mlp_create": [u64, vp, ctypes.POINTER(vp)],
+                "mlp_set_params": [vp, vp],
+                "mlp_get_params": [vp, vp],
+                "mlp_forward": [vp, vp, u64, vp],
+                "mlp_gradient": [vp, vp, vp, vp, u64, vp, vp],
+                "mlp_train_step": [vp, vp, vp, vp, u64, ctypes.c_float, vp],
+                "mlp_destroy": [vp],
+                "exact_counts": [vp, u64, f64, f64, u32, vp, vp, vp, u64, ctypes.POINTER(u64)],
+                "learned_create": [ctypes.POINTER(hs_params), u32, u32, u64, f64, vp,
+                                   ctypes.POINTER(vp)],
+                "learned_capacity": [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)],
+                "learned_routed": [vp, vp, u64, ctypes.POINTER(u64)],
+                "learned_prepare": [vp, vp, u64, vp, ctypes.POINTER(u64)],
+                "learned_update": [vp, vp, u64, f64],
+                "learned_topk": [vp, u32, vp, vp, ctypes.POINTER(u32)],
+                "learned_table": [vp, vp, vp, u64, ctypes.POINTER(u64)],
+                "learned_logits": [vp, vp, vp, u64, ctypes.POINTER(u64)],
+                "learned_features": [vp, vp, u64, ctypes.POINTER(u64)],
+                "learned_coarse_counts": [vp, vp],
+                "learned_sketch": [vp, ctypes.POINTER(vp)],
+                "learned_reset": [vp],
+                "learned_destroy": [vp],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -413,3 +435,180 @@ class Batch:
 
     def autotune(self, xyz, offsets, rate: float = 1.0) -> dict:
         return batch_autotune(self.h, xyz, offsets, rate)
+
+
+# ---- learned router ----
+
+HS_MLP_PARAMS = 6017
+MLP_IN, MLP_H = 27, 64
+
+
+class MLP:
+    """The router network (27 -> 64 -> 64 -> 1); all math in library kernels."""
+
+    def __init__(self, seed: int = 0, stream=None):
+        h = ctypes.c_void_p()
+        _check(lib().mlp_create(seed, _stream_ptr(stream), ctypes.byref(h)), "mlp_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(HS_MLP_PARAMS, np.float32)
+        _check(lib().mlp_get_params(self.h, out.ctypes.data), "mlp_get_params")
+        return out
+
+    def set_params(self, p) -> None:
+        p = np.ascontiguousarray(p, np.float32)
+        assert p.size == HS_MLP_PARAMS
+        _check(lib().mlp_set_params(self.h, p.ctypes.data), "mlp_set_params")
+
+    def forward(self, feats) -> np.ndarray:
+        feats = feats if not isinstance(feats, np.ndarray) else np.ascontiguousarray(feats, np.uint16)
+        n = (feats.numel() if hasattr(feats, "numel") else feats.size) // MLP_IN
+        out = np.empty(n, np.float32)
+        _check(lib().mlp_forward(self.h, _ptr(feats), n, out.ctypes.data), "mlp_forward")
+        return out
+
+    def gradient(self, feats, y, w):
+        n = (feats.numel() if hasattr(feats, "numel") else feats.size) // MLP_IN
+        grad = np.empty(HS_MLP_PARAMS, np.float32)
+        loss = np.empty(1, np.float32)
+        _check(lib().mlp_gradient(self.h, _ptr(feats), _ptr(y), _ptr(w), n, grad.ctypes.data,
+                                  loss.ctypes.data), "mlp_gradient")
+        return grad, float(loss[0])
+
+    def train_step(self, feats, y, w, lr: float, want_loss: bool = True):
+        n = (feats.numel() if hasattr(feats, "numel") else feats.size) // MLP_IN
+        loss = ctypes.c_float()
+        _check(lib().mlp_train_step(self.h, _ptr(feats), _ptr(y), _ptr(w), n, lr,
+                                    ctypes.byref(loss) if want_loss else None), "mlp_train_step")
+        return loss.value if want_loss else None
+
+
+def exact_counts(xyz, n: int, box: float, cell: float, log2_slots: int, stream=None):
+    """(keys, counts) of every occupied cell, computed on the GPU (device xyz)."""
+    nn = ctypes.c_uint64()
+    _check(lib().exact_counts(_ptr(xyz), n, box, cell, log2_slots, _stream_ptr(stream), None, None,
+                              0, ctypes.byref(nn)), "exact_counts")
+    cap = nn.value
+    keys = np.empty(max(cap, 1), np.uint64)
+    cnt = np.empty(max(cap, 1), np.int32)
+    _check(lib().exact_counts(_ptr(xyz), n, box, cell, log2_slots, _stream_ptr(stream),
+                              keys.ctypes.data, cnt.ctypes.data, cap, ctypes.byref(nn)),
+           "exact_counts")
+    return keys[:nn.value], cnt[:nn.value]
+
+
+class Learned:
+    """Learned sketch: routed coarse cells counted exactly, the rest sketched."""
+
+    def __init__(self, rows: int, log2_width: int, box: float, cell: float, hash_seed: int = 0,
+                 sample_seed: int = 0, coarse_factor: int = 10, table_log2: int = 20,
+                 feature_seed: int = 64, feature_rate: float = 1.0 / 64, stream=None,
+                 flags: int = 0):
+        self.params = make_params(rows, log2_width, box, cell, hash_seed, sample_seed, flags)
+        h = ctypes.c_void_p()
+        _check(lib().learned_create(ctypes.byref(self.params), coarse_factor, table_log2,
+                                    feature_seed, feature_rate, _stream_ptr(stream),
+                                    ctypes.byref(h)), "learned_create")
+        self.h = h
+        sk = ctypes.c_void_p()
+        _check(lib().learned_sketch(self.h, ctypes.byref(sk)), "learned_sketch")
+        self.sketch_h = sk
+        info = sketch_info(sk)
+        self.rows, self.width, self.G = info.rows, info.width, info.grid
+        self.R = coarse_factor
+        self.Gc = self.G // coarse_factor
+        mr, tb = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib().learned_capacity(self.h, ctypes.byref(mr), ctypes.byref(tb)),
+               "learned_capacity")
+        self.max_routed, self.table_bytes = mr.value, tb.value
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().learned_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def prepare(self, xyz, mlp: MLP, n: int | None = None) -> int:
+        if n is None:
+            n = (xyz.numel() if hasattr(xyz, "numel") else xyz.size) // 3
+        nr = ctypes.c_uint64()
+        _check(lib().learned_prepare(self.h, _ptr(xyz), n, mlp.h, ctypes.byref(nr)), "learned_prepare")
+        return nr.value
+
+    def update(self, xyz, n: int | None = None, rate: float = 1.0):
+        if n is None:
+            n = (xyz.numel() if hasattr(xyz, "numel") else xyz.size) // 3
+        _check(lib().learned_update(self.h, _ptr(xyz), n, rate), "learned_update")
+
+    def topk(self, k: int):
+        keys = np.empty(k, np.uint64)
+        est = np.empty(k, np.int32)
+        n = ctypes.c_uint32()
+        _check(lib().learned_topk(self.h, k, keys.ctypes.data, est.ctypes.data, ctypes.byref(n)),
+               "learned_topk")
+        return keys[:n.value], est[:n.value]
+
+    def table(self):
+        nn = ctypes.c_uint64()
+        _check(lib().learned_table(self.h, None, None, 0, ctypes.byref(nn)), "learned_table")
+        keys = np.empty(max(nn.value, 1), np.uint64)
+        cnt = np.empty(max(nn.value, 1), np.int32)
+        _check(lib().learned_table(self.h, keys.ctypes.data, cnt.ctypes.data, nn.value,
+                                   ctypes.byref(nn)), "learned_table")
+        o = np.argsort(keys[:nn.value])
+        return keys[:nn.value][o], cnt[:nn.value][o]
+
+    def routed(self) -> np.ndarray:
+        nn = ctypes.c_uint64()
+        _check(lib().learned_routed(self.h, None, 0, ctypes.byref(nn)), "learned_routed")
+        out = np.empty(max(nn.value, 1), np.uint64)
+        _check(lib().learned_routed(self.h, out.ctypes.data, nn.value, ctypes.byref(nn)),
+               "learned_routed")
+        return out[:nn.value]
+
+    def logits(self):
+        nn = ctypes.c_uint64()
+        _check(lib().learned_logits(self.h, None, None, 0, ctypes.byref(nn)), "learned_logits")
+        keys = np.empty(max(nn.value, 1), np.uint64)
+        lg = np.empty(max(nn.value, 1), np.float32)
+        _check(lib().learned_logits(self.h, keys.ctypes.data, lg.ctypes.data, nn.value,
+                                    ctypes.byref(nn)), "learned_logits")
+        return keys[:nn.value], lg[:nn.value]
+
+    def features(self):
+        nn = ctypes.c_uint64()
+        _check(lib().learned_features(self.h, None, 0, ctypes.byref(nn)), "learned_features")
+        f = np.empty((max(nn.value, 1), MLP_IN), np.uint16)
+        _check(lib().learned_features(self.h, f.ctypes.data, nn.value, ctypes.byref(nn)),
+               "learned_features")
+        return f[:nn.value]
+
+    def coarse_counts(self) -> np.ndarray:
+        out = np.empty(self.Gc ** 3, np.int32)
+        _check(lib().learned_coarse_counts(self.h, out.ctypes.data), "learned_coarse_counts")
+        return out
+
+    def counters(self) -> np.ndarray:
+        out = np.empty((self.rows, self.width), np.int32)
+        sketch_counters(self.sketch_h, out)
+        return out
+
+    def reset(self):
+        _check(lib().learned_reset(self.h), "learned_reset")
