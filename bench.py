@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-red", action="store_true", help="skip the L2 atomic-rate probe")
     ap.add_argument("--no-batch", action="store_true", help="skip the sub-volume batch leg")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-router leg")
+    ap.add_argument("--train-boxes", type=int, default=200,
+                    help="100 Mpc/h training boxes of the learned router (seeds 1000..)")
     ap.add_argument("--second-rate", type=float, default=0.1,
                     help="also time this sample rate (0 to skip)")
     return ap.parse_args()
@@ -244,6 +247,121 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+LEARNED = dict(coarse_factor=10, table_log2=20, sketch_log2_width=23, feature_seed=64,
+               feature_rate=1.0 / 64, k_label=80, exact_log2_slots=31)
+
+
+def run_learned(dev, n: int, main_keys: np.ndarray, train_boxes: int, stream):
+    """The learned router on the 10^9-particle box: train on 100 Mpc/h boxes,
+    then top-k recall against exact counts for the plain sketch at 5 x 2^24
+    (320 MiB, the main leg's last top-k) and 5 x 2^23 (160 MiB), and for the
+    learned sketch (5 x 2^23 + exact blocks of a 2^20-slot table's bytes)."""
+    import torch
+
+    import synth
+    from paper_1711_00975_gb300 import halosketch as hs
+    from paper_1711_00975_gb300 import router
+
+    W = WORKLOAD
+    C = LEARNED
+    k = W["k"]
+    out = {"workload": W["name"], "k": k, "train_boxes": train_boxes}
+    # ---- training set: features from the library's sample pass, labels from exact counts
+    t0 = time.time()
+    mlp = hs.MLP(seed=1, stream=stream)
+    tspec = synth.training_box(1000)
+    bufs = [torch.empty((tspec.n, 3), dtype=torch.float32).pin_memory() for _ in range(2)]
+    gen_s = [0.0]
+
+    def gen(i, buf):
+        t = time.time()
+        synth.HaloBox(synth.training_box(1000 + i)).generate_into_ptr(buf.data_ptr(), 0, tspec.n)
+        gen_s[0] += time.time() - t
+
+    Lt = hs.Learned(1, 16, tspec.box, W["cell"], coarse_factor=C["coarse_factor"], table_log2=12,
+                    feature_seed=C["feature_seed"], feature_rate=C["feature_rate"], stream=stream)
+    Et = hs.Exact(tspec.box, W["cell"], 24, stream)
+    dbox = torch.empty((tspec.n, 3), dtype=torch.float32, device=dev.device)
+    feats, ys = [], []
+    th = threading.Thread(target=gen, args=(0, bufs[0]))
+    th.start()
+    for i in range(train_boxes):
+        th.join()
+        dbox.copy_(bufs[i % 2])
+        torch.cuda.synchronize()
+        if i + 1 < train_boxes:
+            th = threading.Thread(target=gen, args=(i + 1, bufs[(i + 1) % 2]))
+            th.start()
+        f, y, _ = router.box_examples(dbox, tspec.n, tspec.box, W["cell"], mlp,
+                                      C["coarse_factor"], C["feature_seed"], C["feature_rate"],
+                                      C["k_label"], learned=Lt, exact=Et)
+        feats.append(f)
+        ys.append(y)
+    Lt.close()
+    Et.close()
+    del dbox
+    F = np.concatenate(feats)
+    Y = np.concatenate(ys)
+    t1 = time.time()
+    losses = router.train(mlp, F, Y, epochs=4, batch=65536, lr=1e-3, seed=0)
+    torch.cuda.synchronize()
+    out["training"] = {"examples": int(Y.size), "positives": int(Y.sum()),
+                       "examples_s": t1 - t0, "generation_s": gen_s[0],
+                       "train_s": time.time() - t1, "epoch_losses": losses,
+                       "label": f"coarse cell holds a fine cell >= the {C['k_label']}-th largest "
+                                f"exact count of its box"}
+    # ---- evaluation on the main box
+    E = hs.Exact(W["box"], W["cell"], C["exact_log2_slots"], stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    E.add(dev, n)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    out["exact_add_ms"] = ev[0].elapsed_time(ev[1])
+    out["distinct_cells"] = E.size()
+
+    def timed_call(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return r, a.elapsed_time(b)
+
+    plain_320 = E.recall(main_keys, k)
+    sk = hs.Sketch(W["rows"], C["sketch_log2_width"], W["box"], W["cell"], W["hash_seed"],
+                   W["sample_seed"], stream=stream)
+    _, up_ms = timed_call(lambda: (sk.update(dev, n), sk.flush()))
+    (pk, _), tk_ms = timed_call(lambda: sk.topk(k))
+    plain_160 = E.recall(pk, k)
+    sk.close()
+    L = hs.Learned(W["rows"], C["sketch_log2_width"], W["box"], W["cell"], W["hash_seed"],
+                   W["sample_seed"], coarse_factor=C["coarse_factor"], table_log2=C["table_log2"],
+                   feature_seed=C["feature_seed"], feature_rate=C["feature_rate"], stream=stream)
+    nr, prep_ms = timed_call(lambda: L.prepare(dev, mlp, n))
+    _, lup_ms = timed_call(lambda: (L.update(dev, n), hs.sketch_flush(L.sketch_h)))
+    (lk, _), ltk_ms = timed_call(lambda: L.topk(k))
+    learned = E.recall(lk, k)
+    sketch_bytes = W["rows"] * 4 << C["sketch_log2_width"]
+    out.update({
+        "recall_plain_320MiB": plain_320, "recall_plain_160MiB": plain_160,
+        "recall_learned": learned,
+        "memory_bytes": {"plain_320MiB": W["rows"] * 4 << W["log2_width"],
+                         "plain_160MiB": sketch_bytes,
+                         "learned": sketch_bytes + L.table_bytes,
+                         "learned_table": L.table_bytes,
+                         "learned_routing_aux": (L.Gc ** 3 + 31) // 32 * 8},
+        "routed_coarse_cells": int(nr), "max_routed": int(L.max_routed),
+        "plain_160MiB_ms": {"update": up_ms, "topk": tk_ms},
+        "learned_ms": {"prepare": prep_ms, "update": lup_ms, "topk": ltk_ms},
+        "learned_particles_per_s": n / ((prep_ms + lup_ms + ltk_ms) * 1e-3),
+        "exact_table": f"2^{C['exact_log2_slots']} slots"})
+    L.close()
+    E.close()
+    mlp.close()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -384,6 +502,10 @@ def run_ours(args):
                "h2d_bytes_per_step": 12 * n, "d2h_bytes_per_step": 12 * k,
                "ms_per_step": max(ems, wall * 1e3)}
 
+    learned = None
+    if not args.no_learned and rank == 0:
+        learned = run_learned(dev, n, keys.copy(), args.train_boxes, stream)
+
     batched = None
     if not args.no_batch:
         del dev
@@ -416,7 +538,7 @@ def run_ours(args):
                           "candidates": st["last_candidates"], "threshold": st["last_threshold"],
                           "passes": st["last_passes"]},
             "roofline": roof, "search": search_roof, "red_rate": red, "second_rate": second, "e2e": e2e,
-            "batched": batched, "cpu_baseline": cpu, "clocks": clocks,
+            "batched": batched, "learned": learned, "cpu_baseline": cpu, "clocks": clocks,
             "gpu_launches": int(st["kernel_launches"])}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -308,12 +308,30 @@ hs_status mlp_train_step(hs_mlp *m, const uint16_t *features, const float *y, co
                          uint64_t n, float lr, float *loss);
 hs_status mlp_destroy(hs_mlp *m);
 
-/* Exact per-cell counts of n particles (device xyz) on the box/cell mesh in an
- * open-addressing table of 2^log2_slots entries (Sec. 4.2, the exact
- * algorithm).  Writes up to cap (key, count) pairs in table order to keys /
- * counts (host or device; NULL keys: count only) and the number of distinct
- * cells to *n_out.  HS_ERR_TABLE_FULL when a key finds no free slot within 64
- * probes.  Synchronous on cuda_stream. */
+/* ---- exact counts (Sec. 4.2, the exact algorithm) ----
+ *
+ * One counter per occupied cell of the box/cell mesh, in an open-addressing
+ * table of 2^log2_slots (uint64 key, int32 count) entries in device memory
+ * (12 bytes a slot; linear probing from a 64-bit mix of the key, at most 64
+ * slots per key).  The reads below fail with HS_ERR_TABLE_FULL when some key
+ * found no free slot (size the table about 2x the distinct cells or more).
+ * Used as the judge of top-k recall and for the router's training labels.
+ * All calls are ordered on cuda_stream; the reads are synchronous. */
+typedef struct hs_exact hs_exact;
+hs_status exact_create(double box, double cell, uint32_t log2_slots, void *cuda_stream,
+                       hs_exact **out);
+/* count n particles (device xyz; cells as in sketch_update, invalid ones skipped) */
+hs_status exact_add(hs_exact *E, const float *xyz, uint64_t n);
+/* up to cap (key, count) pairs in table order (host or device); *n_out = distinct
+ * cells; cap 0: count only */
+hs_status exact_list(hs_exact *E, uint64_t *keys, int32_t *counts, uint64_t cap, uint64_t *n_out);
+/* the min(k, distinct) heaviest cells ranked by (count desc, key asc) */
+hs_status exact_topk(hs_exact *E, uint32_t k, uint64_t *keys, int32_t *counts, uint32_t *n_out);
+/* counts[i] = exact count of keys[i] (0 if never seen); host or device arrays */
+hs_status exact_query(hs_exact *E, const uint64_t *keys, uint64_t m, int32_t *counts);
+hs_status exact_reset(hs_exact *E);
+hs_status exact_destroy(hs_exact *E);
+/* one-shot: exact_create + exact_add + exact_list + exact_destroy */
 hs_status exact_counts(const float *xyz, uint64_t n, double box, double cell, uint32_t log2_slots,
                        void *cuda_stream, uint64_t *keys, int32_t *counts, uint64_t cap,
                        uint64_t *n_out);

@@ -1504,6 +1504,23 @@ struct hs_mlp {
     int device = 0;
 };
 
+struct hs_exact {
+    SketchDesc d{};
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 0;
+    uint64_t slots = 0;
+    uint32_t key_bits = 1;
+    unsigned long long *keys = nullptr;   // all ones = empty
+    int32_t *counts = nullptr;
+    uint32_t *overflow = nullptr;
+    unsigned long long *ctr = nullptr;    // [0] listed entries, [1] taken entries
+    SelectState *sel = nullptr;
+    unsigned long long *hist = nullptr;
+    uint64_t *tmp_key = nullptr, *out_key = nullptr;
+    int32_t *tmp_est = nullptr, *out_est = nullptr;
+    uint64_t out_cap = 0;
+};
+
 struct hs_learned {
     hs_sketch *sk = nullptr;       // the sketch of the cells that are not routed
     uint32_t R = 10, Gc = 0;
@@ -1699,65 +1716,179 @@ hs_status mlp_train_step(hs_mlp *m, const uint16_t *feats, const float *y, const
     return HS_OK;
 }
 
-hs_status exact_counts(const float *xyz, uint64_t n, double box, double cell, uint32_t log2_slots,
-                       void *cuda_stream, uint64_t *keys, int32_t *counts, uint64_t cap,
-                       uint64_t *n_out) {
-    if (!n_out || (n && !xyz) || log2_slots < 4 || log2_slots > 34)
-        return fail(HS_ERR_ARG, "bad argument");
+hs_status exact_destroy(hs_exact *E) {
+    if (!E) return HS_OK;
+    void *ps[] = {E->keys, E->counts, E->overflow, E->ctr, E->sel, E->hist,
+                  E->tmp_key, E->tmp_est, E->out_key, E->out_est};
+    for (void *q : ps)
+        if (q) cudaFree(q);
+    delete E;
+    return HS_OK;
+}
+
+hs_status exact_create(double box, double cell, uint32_t log2_slots, void *cuda_stream,
+                       hs_exact **out) {
+    if (!out || log2_slots < 4 || log2_slots > 34) return fail(HS_ERR_ARG, "bad argument");
     hs_params p{1, 1, box, cell, 0, 0, 0, 0};
     hs_status st = check_params(&p);
     if (st != HS_OK) return st;
-    if (n && !is_device_ptr(xyz)) return fail(HS_ERR_ARG, "xyz must be device memory");
-    cudaStream_t s = (cudaStream_t)cuda_stream;
-    SketchDesc d{};
-    d.G = (uint32_t)std::llround(box / cell);
-    d.inv_cell = (float)(1.0 / cell);
-    const uint64_t slots = 1ull << log2_slots;
-    unsigned long long *tk = nullptr, *cnt = nullptr;
-    int32_t *tc = nullptr;
-    uint32_t *ovf = nullptr;
-    cudaError_t e = cudaMalloc(&tk, slots * 8);
-    if (e == cudaSuccess) e = cudaMalloc(&tc, slots * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&ovf, 4);
-    if (e == cudaSuccess) e = cudaMalloc(&cnt, 8);
-    if (e == cudaSuccess) e = cudaMemsetAsync(tk, 0xFF, slots * 8, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(tc, 0, slots * 4, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ovf, 0, 4, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, 8, s);
-    if (e == cudaSuccess) e = launch_exact_count(xyz, n, d, tk, tc, slots, ovf, s);
-    uint64_t *dk = keys;
-    int32_t *dc = counts;
-    const bool dev_out = keys && is_device_ptr(keys);
-    if (e == cudaSuccess && keys && !dev_out) {
-        e = cudaMalloc(&dk, std::max<uint64_t>(cap, 1) * 8);
-        if (e == cudaSuccess) e = cudaMalloc(&dc, std::max<uint64_t>(cap, 1) * 4);
+    hs_exact *E = new (std::nothrow) hs_exact();
+    if (!E) return fail(HS_ERR_OOM, "host allocation failed");
+    E->stream = (cudaStream_t)cuda_stream;
+    E->d.G = (uint32_t)std::llround(box / cell);
+    E->d.inv_cell = (float)(1.0 / cell);
+    E->slots = 1ull << log2_slots;
+    const uint64_t cells = (uint64_t)E->d.G * E->d.G * E->d.G;
+    while (E->key_bits < 64 && (1ull << E->key_bits) < cells) ++E->key_bits;
+    cudaError_t e = cudaGetDevice(&E->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&E->num_sms, cudaDevAttrMultiProcessorCount, E->device);
+    if (e == cudaSuccess) e = cudaMalloc(&E->keys, E->slots * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&E->counts, E->slots * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&E->overflow, 4);
+    if (e == cudaSuccess) e = cudaMalloc(&E->ctr, 2 * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&E->sel, sizeof(SelectState));
+    if (e == cudaSuccess) e = cudaMalloc(&E->hist, 256 * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        exact_destroy(E);
+        return fail(HS_ERR_OOM, "exact_create: %s", cudaGetErrorString(e));
     }
-    if (e == cudaSuccess && keys) e = launch_table_list(tk, tc, slots, dk, dc, cnt, cap, s);
-    unsigned long long nn = 0;
+    st = exact_reset(E);
+    if (st != HS_OK) {
+        exact_destroy(E);
+        return st;
+    }
+    *out = E;
+    return HS_OK;
+}
+
+hs_status exact_reset(hs_exact *E) {
+    if (!E) return fail(HS_ERR_ARG, "NULL handle");
+    HS_CUDA(cudaMemsetAsync(E->keys, 0xFF, E->slots * 8, E->stream));
+    HS_CUDA(cudaMemsetAsync(E->counts, 0, E->slots * 4, E->stream));
+    HS_CUDA(cudaMemsetAsync(E->overflow, 0, 4, E->stream));
+    HS_CUDA(cudaStreamSynchronize(E->stream));
+    return HS_OK;
+}
+
+hs_status exact_add(hs_exact *E, const float *xyz, uint64_t n) {
+    if (!E || (n && !xyz)) return fail(HS_ERR_ARG, "bad argument");
+    if (n == 0) return HS_OK;
+    if (!is_device_ptr(xyz)) return fail(HS_ERR_ARG, "xyz must be device memory");
+    HS_CUDA(launch_exact_count(xyz, n, E->d, E->keys, E->counts, E->slots, E->overflow, E->stream));
+    return HS_OK;
+}
+
+static hs_status exact_check(hs_exact *E) {
     uint32_t of = 0;
-    if (e == cudaSuccess && !keys) {                 // only the number of distinct cells
-        e = launch_table_list(tk, tc, slots, nullptr, nullptr, cnt, 0, s);
+    HS_CUDA(cudaMemcpyAsync(&of, E->overflow, 4, cudaMemcpyDeviceToHost, E->stream));
+    HS_CUDA(cudaStreamSynchronize(E->stream));
+    if (of) return fail(HS_ERR_TABLE_FULL, "exact table: a key found no free slot in %d probes",
+                        kTableProbes);
+    return HS_OK;
+}
+
+hs_status exact_list(hs_exact *E, uint64_t *keys, int32_t *counts, uint64_t cap, uint64_t *n_out) {
+    if (!E || !n_out || (cap && (!keys || !counts))) return fail(HS_ERR_ARG, "bad argument");
+    hs_status st = exact_check(E);
+    if (st != HS_OK) return st;
+    cudaStream_t s = E->stream;
+    const bool dev = cap && is_device_ptr(keys) && is_device_ptr(counts);
+    uint64_t *dk = dev ? keys : nullptr;
+    int32_t *dc = dev ? counts : nullptr;
+    cudaError_t e = cudaSuccess;
+    if (cap && !dev) {
+        e = cudaMalloc(&dk, cap * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&dc, cap * 4);
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&nn, cnt, 8, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&of, ovf, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(E->ctr, 0, 8, s);
+    if (e == cudaSuccess) e = launch_table_list(E->keys, E->counts, E->slots, dk, dc, E->ctr, cap, s);
+    unsigned long long nn = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nn, E->ctr, 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess && keys && !dev_out) {
-        uint64_t m = std::min<uint64_t>(nn, cap);
+    const uint64_t m = std::min<uint64_t>(nn, cap);
+    if (e == cudaSuccess && m && !dev) {
         e = cudaMemcpy(keys, dk, m * 8, cudaMemcpyDeviceToHost);
         if (e == cudaSuccess) e = cudaMemcpy(counts, dc, m * 4, cudaMemcpyDeviceToHost);
     }
-    if (keys && !dev_out) {
+    if (!dev) {
         if (dk) cudaFree(dk);
         if (dc) cudaFree(dc);
     }
-    cudaFree(tk);
-    cudaFree(tc);
-    cudaFree(ovf);
-    cudaFree(cnt);
-    if (e != cudaSuccess) return fail(HS_ERR_CUDA, "exact_counts: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(HS_ERR_CUDA, "exact_list: %s", cudaGetErrorString(e));
     *n_out = nn;
-    if (of) return fail(HS_ERR_TABLE_FULL, "exact_counts: 2^%u slots are too few", log2_slots);
     return HS_OK;
+}
+
+hs_status exact_topk(hs_exact *E, uint32_t k, uint64_t *keys, int32_t *counts, uint32_t *n_out) {
+    if (!E || !n_out || (k && (!keys || !counts))) return fail(HS_ERR_ARG, "bad argument");
+    uint64_t D = 0;
+    hs_status st = exact_list(E, nullptr, nullptr, 0, &D);
+    if (st != HS_OK) return st;
+    const uint64_t kk = std::min<uint64_t>(k, D);
+    *n_out = 0;
+    if (kk == 0) return HS_OK;
+    if (E->out_cap < kk) {
+        void *ps[] = {E->tmp_key, E->tmp_est, E->out_key, E->out_est};
+        for (void *q : ps)
+            if (q) cudaFree(q);
+        E->tmp_key = E->out_key = nullptr;
+        E->tmp_est = E->out_est = nullptr;
+        E->out_cap = 0;
+        HS_CUDA(cudaMalloc(&E->tmp_key, kk * 8));
+        HS_CUDA(cudaMalloc(&E->tmp_est, kk * 4));
+        HS_CUDA(cudaMalloc(&E->out_key, kk * 8));
+        HS_CUDA(cudaMalloc(&E->out_est, kk * 4));
+        E->out_cap = kk;
+    }
+    // Rank every slot: empty slots carry count 0 and so rank below the kk-th
+    // occupied one (its count is >= 1 because kk <= D).
+    int launches = 0;
+    const uint64_t *tk = reinterpret_cast<const uint64_t *>(E->keys);
+    HS_CUDA(launch_select_kth(tk, E->counts, E->slots, kk, E->key_bits, E->sel, E->hist,
+                              E->num_sms * 4, E->stream, &launches));
+    HS_CUDA(launch_take_sorted(tk, E->counts, E->slots, E->sel, 0, E->tmp_key, E->tmp_est,
+                               &E->ctr[1], kk, E->out_key, E->out_est, E->num_sms * 4, E->stream,
+                               &launches));
+    HS_CUDA(cudaMemcpyAsync(keys, E->out_key, kk * 8, cudaMemcpyDefault, E->stream));
+    HS_CUDA(cudaMemcpyAsync(counts, E->out_est, kk * 4, cudaMemcpyDefault, E->stream));
+    HS_CUDA(cudaStreamSynchronize(E->stream));
+    *n_out = (uint32_t)kk;
+    return HS_OK;
+}
+
+hs_status exact_query(hs_exact *E, const uint64_t *keys, uint64_t m, int32_t *counts) {
+    if (!E || (m && (!keys || !counts))) return fail(HS_ERR_ARG, "bad argument");
+    if (m == 0) return HS_OK;
+    hs_status st = exact_check(E);
+    if (st != HS_OK) return st;
+    const uint64_t *dk;
+    uint64_t *tk = nullptr;
+    st = device_input(keys, m, E->stream, &dk, &tk);
+    if (st != HS_OK) return st;
+    const bool dev_out = is_device_ptr(counts);
+    int32_t *dc = counts;
+    cudaError_t e = cudaSuccess;
+    if (!dev_out) e = cudaMalloc(&dc, m * 4);
+    if (e == cudaSuccess) e = launch_exact_query(E->keys, E->counts, E->slots, dk, m, dc, E->stream);
+    if (e == cudaSuccess && !dev_out)
+        e = cudaMemcpyAsync(counts, dc, m * 4, cudaMemcpyDeviceToHost, E->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(E->stream);
+    if (tk) cudaFree(tk);
+    if (!dev_out && dc) cudaFree(dc);
+    if (e != cudaSuccess) return fail(HS_ERR_CUDA, "exact_query: %s", cudaGetErrorString(e));
+    return HS_OK;
+}
+
+hs_status exact_counts(const float *xyz, uint64_t n, double box, double cell, uint32_t log2_slots,
+                       void *cuda_stream, uint64_t *keys, int32_t *counts, uint64_t cap,
+                       uint64_t *n_out) {
+    if (!n_out || (n && !xyz)) return fail(HS_ERR_ARG, "bad argument");
+    hs_exact *E = nullptr;
+    hs_status st = exact_create(box, cell, log2_slots, cuda_stream, &E);
+    if (st == HS_OK) st = exact_add(E, xyz, n);
+    if (st == HS_OK) st = exact_list(E, keys, counts, keys ? cap : 0, n_out);
+    exact_destroy(E);
+    return st;
 }
 
 hs_status learned_destroy(hs_learned *L) {

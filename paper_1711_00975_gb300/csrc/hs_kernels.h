@@ -87,6 +87,9 @@ cudaError_t launch_exact_count(const float *xyz, uint64_t n, const SketchDesc &d
 cudaError_t launch_table_list(const unsigned long long *keys, const int32_t *counts, uint64_t slots,
                               uint64_t *out_keys, int32_t *out_counts, unsigned long long *n_out,
                               uint64_t cap, cudaStream_t s);
+cudaError_t launch_exact_query(const unsigned long long *tkeys, const int32_t *tcounts,
+                               uint64_t slots, const uint64_t *keys, uint64_t m, int32_t *counts,
+                               cudaStream_t s);
 
 // dst[i] += src[i] (int32 wrap-around), the merge of two sketches
 cudaError_t launch_add_counters(int32_t *dst, const int32_t *src, uint64_t n, cudaStream_t s);

@@ -352,50 +352,6 @@ __global__ void k_block_list(const int32_t *__restrict__ blocks, const uint64_t 
 
 }  // namespace
 
-namespace {
-
-// exact counts of all particles' cells (the judge of recall, training labels)
-__global__ void k_exact_count(const float *__restrict__ xyz, uint64_t n, const SketchDesc d,
-                              unsigned long long *__restrict__ keys, int32_t *__restrict__ counts,
-                              uint64_t mask, uint32_t *__restrict__ overflow) {
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        uint32_t cx, cy, cz;
-        bool ok = axis_cell(xyz[3 * i], d.inv_cell, d.G, cx);
-        ok &= axis_cell(xyz[3 * i + 1], d.inv_cell, d.G, cy);
-        ok &= axis_cell(xyz[3 * i + 2], d.inv_cell, d.G, cz);
-        if (!ok) continue;
-        if (!table_add(keys, counts, mask, key_of(cx, cy, cz, d.G), kTableProbes))
-            atomicOr(overflow, 1u);
-    }
-}
-
-// occupied slots -> (key, count) lists
-__global__ void k_table_list(const unsigned long long *__restrict__ keys,
-                             const int32_t *__restrict__ counts, uint64_t slots,
-                             uint64_t *__restrict__ out_keys, int32_t *__restrict__ out_counts,
-                             unsigned long long *__restrict__ n_out, uint64_t cap) {
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const int lane = threadIdx.x & 31;
-    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < slots; base += stride) {
-        const uint64_t i = base + threadIdx.x;
-        const bool on = i < slots && keys[i] != kInvalidKey;
-        const unsigned m = __ballot_sync(0xFFFFFFFFu, on);
-        if (!m) continue;
-        unsigned long long b0 = 0;
-        if (lane == __ffs(m) - 1) b0 = atomicAdd(n_out, (unsigned long long)__popc(m));
-        b0 = __shfl_sync(0xFFFFFFFFu, b0, __ffs(m) - 1);
-        if (on) {
-            unsigned long long j = b0 + __popc(m & ((1u << lane) - 1u));
-            if (j < cap) {
-                out_keys[j] = keys[i];
-                out_counts[j] = counts[i];
-            }
-        }
-    }
-}
-
-}  // namespace
 
 cudaError_t launch_coarse_hist(const float *xyz, uint64_t n, uint64_t g0, const SketchDesc &d,
                                uint32_t R, uint32_t Gc, uint64_t seed, double rate,
@@ -493,24 +449,6 @@ cudaError_t launch_block_list(const int32_t *blocks_, const uint64_t *rlist, uin
     uint64_t blocks = std::min<uint64_t>((total + 255) / 256, 8192);
     k_block_list<<<(unsigned)blocks, 256, 0, s>>>(blocks_, rlist, nblocks, R, Gc, G, out_keys,
                                                   out_counts, n_out, cap);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_exact_count(const float *xyz, uint64_t n, const SketchDesc &d,
-                               unsigned long long *keys, int32_t *counts, uint64_t slots,
-                               uint32_t *overflow, cudaStream_t s) {
-    if (n == 0) return cudaSuccess;
-    uint64_t blocks = std::min<uint64_t>((n + 255) / 256, 8192);
-    k_exact_count<<<(unsigned)blocks, 256, 0, s>>>(xyz, n, d, keys, counts, slots - 1, overflow);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_table_list(const unsigned long long *keys, const int32_t *counts, uint64_t slots,
-                              uint64_t *out_keys, int32_t *out_counts, unsigned long long *n_out,
-                              uint64_t cap, cudaStream_t s) {
-    uint64_t blocks = std::min<uint64_t>((slots + 255) / 256, 8192);
-    k_table_list<<<(unsigned)blocks, 256, 0, s>>>(keys, counts, slots, out_keys, out_counts, n_out,
-                                                  cap);
     return cudaGetLastError();
 }
 

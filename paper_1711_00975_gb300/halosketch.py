@@ -118,6 +118,13 @@ def lib():
                 "exact_counts": [vp, u64, f64, f64, u32, vp, vp, vp, u64, ctypes.POINTER(u64)],
                 "learned_create": [ctypes.POINTER(hs_params), u32, u32, u64, f64, vp,
                                    ctypes.POINTER(vp)],
+                "exact_create": [f64, f64, u32, vp, ctypes.POINTER(vp)],
+                "exact_add": [vp, vp, u64],
+                "exact_list": [vp, vp, vp, u64, ctypes.POINTER(u64)],
+                "exact_topk": [vp, u32, vp, vp, ctypes.POINTER(u32)],
+                "exact_query": [vp, vp, u64, vp],
+                "exact_reset": [vp],
+                "exact_destroy": [vp],
                 "learned_capacity": [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)],
                 "learned_routed": [vp, vp, u64, ctypes.POINTER(u64)],
                 "learned_prepare": [vp, vp, u64, vp, ctypes.POINTER(u64)],
@@ -507,6 +514,75 @@ def exact_counts(xyz, n: int, box: float, cell: float, log2_slots: int, stream=N
                               keys.ctypes.data, cnt.ctypes.data, cap, ctypes.byref(nn)),
            "exact_counts")
     return keys[:nn.value], cnt[:nn.value]
+
+
+class Exact:
+    """Exact per-cell counts in a device hash table (the exact algorithm)."""
+
+    def __init__(self, box: float, cell: float, log2_slots: int, stream=None):
+        h = ctypes.c_void_p()
+        _check(lib().exact_create(box, cell, log2_slots, _stream_ptr(stream), ctypes.byref(h)),
+               "exact_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().exact_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add(self, xyz, n: int | None = None):
+        if n is None:
+            n = (xyz.numel() if hasattr(xyz, "numel") else xyz.size) // 3
+        _check(lib().exact_add(self.h, _ptr(xyz), n), "exact_add")
+
+    def size(self) -> int:
+        nn = ctypes.c_uint64()
+        _check(lib().exact_list(self.h, None, None, 0, ctypes.byref(nn)), "exact_list")
+        return nn.value
+
+    def list(self):
+        n = self.size()
+        keys = np.empty(max(n, 1), np.uint64)
+        cnt = np.empty(max(n, 1), np.int32)
+        nn = ctypes.c_uint64()
+        _check(lib().exact_list(self.h, keys.ctypes.data, cnt.ctypes.data, n, ctypes.byref(nn)),
+               "exact_list")
+        return keys[:nn.value], cnt[:nn.value]
+
+    def topk(self, k: int):
+        keys = np.empty(max(k, 1), np.uint64)
+        cnt = np.empty(max(k, 1), np.int32)
+        n = ctypes.c_uint32()
+        _check(lib().exact_topk(self.h, k, keys.ctypes.data, cnt.ctypes.data, ctypes.byref(n)),
+               "exact_topk")
+        return keys[:n.value], cnt[:n.value]
+
+    def query(self, keys) -> np.ndarray:
+        keys = np.ascontiguousarray(keys, np.uint64)
+        out = np.empty(max(keys.size, 1), np.int32)
+        _check(lib().exact_query(self.h, keys.ctypes.data, keys.size, out.ctypes.data),
+               "exact_query")
+        return out[:keys.size]
+
+    def reset(self):
+        _check(lib().exact_reset(self.h), "exact_reset")
+
+    def recall(self, method_keys, k: int) -> float:
+        """count{c in method_keys[:k] : f_c >= f_(k)} / k, f_(k) the k-th largest count."""
+        top = self.topk(k)[1]
+        if k <= 0:
+            return 1.0
+        fk = int(top[k - 1]) if top.size >= k else 0
+        if fk <= 0:
+            return 0.0
+        f = self.query(np.asarray(method_keys, np.uint64)[:k])
+        return float(np.count_nonzero(f >= fk)) / k
 
 
 class Learned:

@@ -19,21 +19,40 @@ from . import halosketch as hs
 
 def box_examples(xyz, n: int, box: float, cell: float, mlp: hs.MLP, coarse_factor: int = 10,
                  feature_seed: int = 64, feature_rate: float = 1.0 / 64, k_label: int = 80,
-                 log2_slots: int = 24, stream=None):
-    """(features uint16 [m, 27], labels float32 [m], coarse keys [m]) of one box (device xyz)."""
-    L = hs.Learned(1, 16, box, cell, coarse_factor=coarse_factor, table_log2=12,
-                   feature_seed=feature_seed, feature_rate=feature_rate, stream=stream)
+                 log2_slots: int = 24, stream=None, learned: hs.Learned | None = None,
+                 exact: hs.Exact | None = None):
+    """(features uint16 [m, 27], labels float32 [m], coarse keys [m]) of one box (device xyz).
+
+    `learned` / `exact` may be passed in to reuse their device memory across
+    boxes of the same geometry (they are reset here)."""
+    own_l = learned is None
+    own_e = exact is None
+    L = learned if learned is not None else hs.Learned(
+        1, 16, box, cell, coarse_factor=coarse_factor, table_log2=12, feature_seed=feature_seed,
+        feature_rate=feature_rate, stream=stream)
+    E = exact if exact is not None else hs.Exact(box, cell, log2_slots, stream)
     try:
         L.prepare(xyz, mlp, n)
         ckeys, _ = L.logits()
         feats = L.features()
+        if not own_e:
+            E.reset()
+        E.add(xyz, n)
+        # every cell with a count >= the k_label-th largest (ties included)
+        want = k_label
+        while True:
+            keys, counts = E.topk(want)
+            if counts.size < want or counts[-1] < counts[min(k_label, counts.size) - 1]:
+                break
+            want *= 2
     finally:
-        L.close()
-    keys, counts = hs.exact_counts(xyz, n, box, cell, log2_slots, stream)
+        if own_l:
+            L.close()
+        if own_e:
+            E.close()
     if counts.size == 0:
         return feats, np.zeros(len(ckeys), np.float32), ckeys
-    kk = min(k_label, counts.size)
-    fk = np.partition(counts, counts.size - kk)[counts.size - kk]
+    fk = counts[min(k_label, counts.size) - 1]
     heavy = keys[counts >= fk].astype(np.int64)
     G = int(round(box / cell))
     R = coarse_factor

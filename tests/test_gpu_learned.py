@@ -122,6 +122,33 @@ def test_exact_counts_vs_oracle(hs):
         hs.exact_counts(_dev(x), len(x), 100.0, 0.1, 8)   # 256 slots: the table is full
 
 
+@pytest.mark.parametrize("log2_slots", [16, 22])
+def test_exact_object_topk_query_recall(hs, log2_slots):
+    spec = synth.BoxSpec(n=40000 if log2_slots == 16 else 1 << 20, box=100.0, n_halo=300, seed=4)
+    x = synth.HaloBox(spec).generate()
+    E = hs.Exact(100.0, 0.1, log2_slots)
+    xd = _dev(x)
+    E.add(xd[: len(x) // 3])                                # two ragged calls
+    E.add(xd[len(x) // 3:])
+    p = oracle.Params(1, 8, 100.0, 0.1, 0)
+    ek, ec = oracle.exact_counts(x, p)
+    assert E.size() == ek.size
+    for k in (1, 10, 1000, ek.size + 5):
+        tk, tc = E.topk(k)
+        wk, wc = oracle.exact_topk(ek, ec.astype(np.int32), k)
+        assert np.array_equal(tk, wk) and np.array_equal(tc, wc), k
+    rng = np.random.default_rng(1)
+    q = np.concatenate([ek[rng.choice(ek.size, 500)], rng.integers(0, 10 ** 9, 500).astype(np.uint64)])
+    lut = dict(zip(ek.tolist(), ec.tolist()))
+    assert np.array_equal(E.query(q), np.array([lut.get(int(v), 0) for v in q], np.int32))
+    sk = hs.Sketch(3, 12, 100.0, 0.1, 5)
+    sk.update(xd)
+    mk = sk.topk(300)[0]
+    assert E.recall(mk, 300) == oracle.recall_at_k(mk, ek, ec, 300)
+    E.reset()
+    assert E.size() == 0
+
+
 # ---------------------------------------------------------------- learned sketch
 
 def centre_router(thr_count):
