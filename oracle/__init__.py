@@ -72,6 +72,10 @@ def _load():
                 "or_learned_update": ([vp, u32, u32, vp, vp, u64, u64, f32, u32, u64, f64, vp, u32,
                                        vp, vp, u64], u64),
                 "or_topk_unrouted": ([vp, u32, u32, vp, u32, vp, u32, u32, vp, vp], u64),
+                "or_sketch_update_super": ([vp, u32, u32, vp, vp, u64, u64, f32, u32, u32, u64,
+                                            f64], None),
+                "or_topk_hier": ([vp, u32, u32, vp, vp, u32, u32, vp, u32, u32, u32, u32, vp, vp,
+                                  ci], u64),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(lib, name)
@@ -221,6 +225,35 @@ def topk_full(C: np.ndarray, p: Params, k: int, nthreads: int = 1, key_lo: int =
     est = np.empty(max(k, 1), np.int32)
     n = _load().or_topk_range(_ptr(C), p.rows, p.log2_width, _ptr(p.seeds), p.G, key_lo, key_hi, k,
                               _ptr(keys), _ptr(est), nthreads)
+    return keys[:n].copy(), est[:n].copy()
+
+
+# ---- hierarchy (Algorithm 3, CSHi) ----
+
+def super_params(p: Params, F: int, log2_width: int, rows: int | None = None) -> Params:
+    """The super-item sketch M1: cells of F x F x F, hash seed hash_seed + 1."""
+    q = Params(rows or p.rows, log2_width, p.box, p.cell * F, p.hash_seed + 1, p.sample_seed)
+    assert q.G * F == p.G
+    return q
+
+
+def sketch_update_super(C1: np.ndarray, p: Params, q: Params, F: int, xyz: np.ndarray,
+                        g0: int = 0, rate: float = 1.0) -> np.ndarray:
+    """Add the super-item (cell / F per axis; cells on p's fine mesh) of every kept particle."""
+    assert C1.dtype == np.int32 and C1.shape == (q.rows, q.width)
+    xyz = np.ascontiguousarray(xyz, np.float32)
+    _load().or_sketch_update_super(_ptr(C1), q.rows, q.log2_width, _ptr(q.seeds), _ptr(xyz),
+                                   xyz.size // 3, g0, p.inv_cell, p.G, F, p.sample_seed, rate)
+    return C1
+
+
+def topk_hier(C2: np.ndarray, p: Params, C1: np.ndarray, q: Params, F: int, k: int,
+              c_mult: int, nthreads: int = 1):
+    keys = np.empty(max(k, 1), np.uint64)
+    est = np.empty(max(k, 1), np.int32)
+    n = _load().or_topk_hier(_ptr(C2), p.rows, p.log2_width, _ptr(p.seeds), _ptr(C1), q.rows,
+                             q.log2_width, _ptr(q.seeds), p.G, F, k, c_mult, _ptr(keys), _ptr(est),
+                             nthreads)
     return keys[:n].copy(), est[:n].copy()
 
 

@@ -584,3 +584,66 @@ uint64_t or_topk_unrouted(const int32_t *C, uint32_t t, uint32_t log2w, const ui
     free(h);
     return cnt;
 }
+
+/* ======================================================================
+ * Count Sketch Hierarchical (Algorithm 3, CSHi; the "GPU hierarchy" variant
+ * of Sec. 3): a second sketch M1 counts super-items, a cell's super-item
+ * being the F x F x F block holding it (super coords = cell coords / F on a
+ * grid of G / F).  The query finds the c*k best super-items by M1's
+ * estimates, then ranks every cell inside them by M2's estimates.
+ * ====================================================================== */
+
+/* Add(M1, super-item of s_i) for every kept particle (Algorithm 3, processing the stream) */
+void or_sketch_update_super(int32_t *C, uint32_t t, uint32_t log2w, const uint64_t *seeds,
+                            const float *xyz, uint64_t n, uint64_t g0, float inv, uint32_t G,
+                            uint32_t F, uint64_t sample_seed, double rate) {
+    for (uint64_t i = 0; i < n; ++i) {
+        if (!or_keep(g0 + i, sample_seed, rate)) continue;
+        uint32_t c[3];
+        if (!or_cell(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], inv, G, c)) continue;
+        uint32_t q[3] = {c[0] / F, c[1] / F, c[2] / F};
+        or_add(C, t, log2w, seeds, q);
+    }
+}
+
+/*
+ * Querying (Algorithm 3 with the top-(c*k) rule of the GPU hierarchy): the
+ * m_super = min(c*k, (G/F)^3) best super-items of M1 (CSFS over the super
+ * dictionary), then the k best cells of those super-items by M2, ranked by
+ * (estimate desc, key asc).  Returns the number written.
+ */
+uint64_t or_topk_hier(const int32_t *C2, uint32_t t2, uint32_t log2w2, const uint64_t *seeds2,
+                      const int32_t *C1, uint32_t t1, uint32_t log2w1, const uint64_t *seeds1,
+                      uint32_t G, uint32_t F, uint32_t k, uint32_t c_mult,
+                      uint64_t *keys_out, int32_t *est_out, int nthreads) {
+    uint32_t Gs = G / F;
+    uint64_t ns = (uint64_t)Gs * Gs * Gs;
+    uint64_t m = (uint64_t)c_mult * k;
+    if (m > ns) m = ns;
+    if (k == 0 || m == 0) return 0;
+    uint64_t *skeys = (uint64_t *)malloc(sizeof(uint64_t) * m);
+    int32_t *sest = (int32_t *)malloc(sizeof(int32_t) * m);
+    or_entry *h = (or_entry *)malloc(sizeof(or_entry) * k);
+    if (!skeys || !sest || !h) { free(skeys); free(sest); free(h); return 0; }
+    uint64_t got = or_topk_range(C1, t1, log2w1, seeds1, Gs, 0, ns, (uint32_t)m, skeys, sest, nthreads);
+    uint64_t cnt = 0;
+    for (uint64_t s = 0; s < got; ++s) {
+        uint32_t q[3];
+        or_key_decode(skeys[s], Gs, q);
+        for (uint32_t lz = 0; lz < F; ++lz)
+            for (uint32_t ly = 0; ly < F; ++ly)
+                for (uint32_t lx = 0; lx < F; ++lx) {
+                    uint32_t c[3] = {q[0] * F + lx, q[1] * F + ly, q[2] * F + lz};
+                    or_entry e;
+                    e.est = or_estimate_cell(C2, t2, log2w2, seeds2, c);
+                    e.key = or_key_of(c, G);
+                    or_offer(h, &cnt, k, e);
+                }
+    }
+    qsort(h, cnt, sizeof(or_entry), or_cmp_rank);
+    for (uint64_t i = 0; i < cnt; ++i) { keys_out[i] = h[i].key; est_out[i] = h[i].est; }
+    free(skeys);
+    free(sest);
+    free(h);
+    return cnt;
+}
