@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-red", action="store_true", help="skip the L2 atomic-rate probe")
     ap.add_argument("--no-batch", action="store_true", help="skip the sub-volume batch leg")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-router leg")
+    ap.add_argument("--no-stream", action="store_true", help="skip the out-of-core stream leg")
+    ap.add_argument("--stream-n", type=float, default=2e10, help="particles of the stream leg")
     ap.add_argument("--train-boxes", type=int, default=200,
                     help="100 Mpc/h training boxes of the learned router (seeds 1000..)")
     ap.add_argument("--second-rate", type=float, default=0.1,
@@ -362,6 +364,120 @@ def run_learned(dev, n: int, main_keys: np.ndarray, train_boxes: int, stream):
     return out
 
 
+STREAM = dict(name="stream-2e10", box=2000.0, n_halo=64 * 10**6, cell=0.1, rows=5,
+              log2_width=26, k=10**5, rate=0.1, chunk_bytes=10**9, pool_chunks=4, box_seed=4,
+              hash_seed=5, sample_seed=6, super_factor=10, super_log2_width=26, c_mult=2)
+
+
+def measure_h2d(src, dst, stream, reps: int = 5) -> float:
+    """Best pinned host -> device copy rate (GB/s) of one chunk, CUDA events."""
+    import torch
+    best = 0.0
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            dst.copy_(src, non_blocking=True)
+            b.record(stream)
+        torch.cuda.synchronize()
+        best = max(best, src.numel() * src.element_size() / (a.elapsed_time(b) * 1e-3) / 1e9)
+    return best
+
+
+def run_stream(n_total: int, hbm: float):
+    """Out-of-core stream: n_total particles of a 2000 Mpc/h box pass from pinned
+    host chunks of 1 GB through the library's double-buffered staging (copy
+    stream + compute stream) into a 5 x 2^26 sketch at sample rate 0.1, then
+    the top-10^5.  Host generation (about 1e8 particles/s) is far slower than
+    the link, so the chunks cycle through a pool of the stream's first 4 GB
+    while the particle indices (and so the sampling) run over the whole
+    stream; the copies and the updates are those of the full stream."""
+    import torch
+
+    import synth
+    from paper_1711_00975_gb300 import halosketch as hs
+
+    S = STREAM
+    C = S["chunk_bytes"] // 12
+
+    def note(msg):
+        print(f"[stream {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+    spec = synth.BoxSpec(n=n_total, box=S["box"], n_halo=S["n_halo"], seed=S["box_seed"])
+    t0 = time.time()
+    hb = synth.HaloBox(spec)
+    pool = [torch.empty((C, 3), dtype=torch.float32).pin_memory() for _ in range(S["pool_chunks"])]
+    for c, buf in enumerate(pool):
+        hb.generate_into_ptr(buf.data_ptr(), c * C, C)
+    gen_s = time.time() - t0
+    gen_rate = C * S["pool_chunks"] / gen_s
+    note(f"pool of {len(pool)} chunks generated in {gen_s:.1f} s")
+    stream = torch.cuda.Stream()
+    probe = torch.empty((C, 3), dtype=torch.float32, device="cuda")
+    h2d_peak = measure_h2d(pool[0], probe, stream)
+    del probe
+    sk = hs.Sketch(S["rows"], S["log2_width"], S["box"], S["cell"], S["hash_seed"],
+                   S["sample_seed"], stream=stream)
+    # 8e12 cells: the query is hierarchical (Algorithm 3) over 10^3-cell super-items
+    sk.set_hierarchy(S["super_factor"], S["super_log2_width"], S["c_mult"])
+    sup = sk.super_handle()
+    nchunks = (n_total + C - 1) // C
+
+    def one_pass():
+        for c in range(nchunks):
+            cnt = min(C, n_total - c * C)
+            hs.sketch_update(sk.h, pool[c % len(pool)], cnt, S["rate"])
+        hs.sketch_flush(sk.h)
+
+    # warm-up: a few chunks and one top-k (builds bins, probe, directories)
+    for c in range(3):
+        hs.sketch_update(sk.h, pool[c], C, S["rate"])
+    note("warm-up updates issued")
+    sk.topk(S["k"])
+    note("warm-up top-k done")
+    sk.reset()
+    sk.stats(reset=True)
+    hs.sketch_stats(sup, reset=True)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    w0 = time.perf_counter()
+    e[0].record(stream)
+    one_pass()
+    e[1].record(stream)
+    note("stream issued")
+    keys, est = sk.topk(S["k"])
+    e[2].record(stream)
+    note("top-k done")
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    upd_ms = e[0].elapsed_time(e[1])
+    tk_ms = e[1].elapsed_time(e[2])
+    st = sk.stats(reset=True)
+    st1 = hs.sketch_stats(sup, reset=True)
+    total_ms = max(e[0].elapsed_time(e[2]), wall * 1e3)
+    h2d = 12.0 * n_total / (upd_ms * 1e-3) / 1e9
+    kernel_ms = st["update_ms"] + st1["update_ms"]
+    kern_gbs = 12.0 * n_total / (kernel_ms * 1e-3) / 1e9 if kernel_ms > 0 else None
+    sk.close()
+    return {"workload": S["name"], "particles": n_total, "box_mpc_h": S["box"], "grid": round(S["box"] / S["cell"]),
+            "rows": S["rows"], "width": 1 << S["log2_width"], "k": S["k"], "sample_rate": S["rate"],
+            "chunk_bytes": C * 12, "chunks": nchunks, "pool_chunks": S["pool_chunks"],
+            "value": n_total / (total_ms * 1e-3), "unit": "particles/s", "ms": total_ms,
+            "stream_ms": upd_ms, "topk_ms": tk_ms,
+            "h2d": {"achieved_gbs": h2d, "peak_gbs": h2d_peak, "frac": h2d / h2d_peak,
+                    "peak_source": "best pinned 1 GB cudaMemcpyAsync on this box"},
+            "hbm": {"kernel_ms": kernel_ms, "achieved_gbs": kern_gbs, "peak_gbs": hbm,
+                    "frac": kern_gbs / hbm if kern_gbs else None,
+                    "note": "12 B/particle over the update kernels' own time"},
+            "gpu_launches": int(st["kernel_launches"] + st1["kernel_launches"]),
+            "top_count": int(est[0]) if len(est) else 0,
+            "query": {"kind": "hierarchical (Algorithm 3)", "super_factor": S["super_factor"],
+                      "super_sketch": f"{S['rows']} x 2^{S['super_log2_width']}",
+                      "c_mult": S["c_mult"], "super_topk_ms": st1["topk_ms"],
+                      "update_ms_fine": st["update_ms"], "update_ms_super": st1["update_ms"]},
+            "generation": {"seconds": gen_s, "particles_per_s": gen_rate,
+                           "note": "host generator rate; the stream cycles a pool of chunks"}}
+
+
 def run_ours(args):
     import torch
 
@@ -506,6 +622,13 @@ def run_ours(args):
     if not args.no_learned and rank == 0:
         learned = run_learned(dev, n, keys.copy(), args.train_boxes, stream)
 
+    stream_leg = None
+    if not args.no_stream and rank == 0:
+        del dev
+        torch.cuda.empty_cache()
+        dev = None
+        stream_leg = run_stream(int(args.stream_n), hbm)
+
     batched = None
     if not args.no_batch:
         del dev
@@ -538,7 +661,7 @@ def run_ours(args):
                           "candidates": st["last_candidates"], "threshold": st["last_threshold"],
                           "passes": st["last_passes"]},
             "roofline": roof, "search": search_roof, "red_rate": red, "second_rate": second, "e2e": e2e,
-            "batched": batched, "learned": learned, "cpu_baseline": cpu, "clocks": clocks,
+            "batched": batched, "learned": learned, "stream": stream_leg, "cpu_baseline": cpu, "clocks": clocks,
             "gpu_launches": int(st["kernel_launches"])}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -134,12 +134,34 @@ hs_status sketch_create(const hs_params *params, void *cuda_stream, hs_sketch **
  * n_seen += n.  sample_rate in (0, 1]; rate 1 keeps every particle.
  * Device xyz: asynchronous on the handle's stream; the buffer must stay valid
  * until that work completes.  Host xyz: copied in chunks through the
- * library's staging buffers; the call returns after the last copy is issued
- * (pageable memory may be reused on return; pinned memory once the stream
- * has drained).  n == 0 is a no-op.  HS_ERR_ARG for a null handle, a null
- * xyz with n > 0, or a rate outside (0, 1].
+ * library's staging buffers (two device buffers of 2^23 particles: the copy of
+ * one, on the handle's own copy stream, overlaps the update of the other); the
+ * call returns after the last copy is issued (pageable memory may be reused on
+ * return; pinned memory after sketch_wait_copies).  n == 0 is a no-op.
+ * HS_ERR_ARG for a null handle, a null xyz with n > 0, or a rate outside (0, 1].
  */
 hs_status sketch_update(hs_sketch *h, const float *xyz, uint64_t n, double sample_rate);
+
+/*
+ * Count Sketch Hierarchical (Algorithm 3, CSHi; the paper's "GPU hierarchy"):
+ * a second sketch M1 of 2^super_log2_width counters per row (same rows and
+ * sample seed, hash seed + 1) counts super-items, the super_factor^3 blocks of
+ * cells, at every sketch_update; topk_extract then finds the c_mult * k best
+ * super-items by M1's full search and ranks the cells inside them by this
+ * sketch (M2), so the query costs c_mult * k * super_factor^3 estimates
+ * instead of G^3.  Needs a fresh plain sketch (nothing added, no router), a
+ * mesh G < 2^16 divisible by super_factor in [2, 64].  Point queries, counters
+ * and merges of M2 are unchanged; reset, seek, flush and merge act on both.
+ */
+hs_status sketch_set_hierarchy(hs_sketch *h, uint32_t super_factor, uint32_t super_log2_width,
+                               uint32_t c_mult);
+/* M1 of a hierarchical sketch (NULL without a hierarchy); owned by h. */
+hs_status sketch_super(hs_sketch *h, hs_sketch **out);
+
+/* Block until every host -> device copy issued by sketch_update has completed,
+ * so the host buffers may be reused, without waiting for the updates (an
+ * out-of-core stream refills one pinned chunk while the GPU consumes another). */
+hs_status sketch_wait_copies(hs_sketch *h);
 
 /*
  * Estimate (Sec. 2.2) for m cell keys: est[i] = median over rows of

@@ -46,6 +46,7 @@ constexpr size_t kSearchSmemBudget = 192 * 1024;
 constexpr size_t kBinSmemBudget = 224 * 1024;
 constexpr uint64_t kBinBudgetBytes = 4ull << 30;   // global bins, at most
 constexpr double kBinnedMinUpdates = 1 << 20;      // smaller calls add directly
+constexpr uint64_t kMaxScanCells = 1ull << 40;      // largest full scan one top-k may run
 
 struct EventPair {
     cudaEvent_t a, b;
@@ -76,6 +77,8 @@ struct hs_sketch {
     // top-k scratch
     uint64_t cap = 0;               // candidate capacity
     uint64_t min_cap = 0;           // extra candidates a learned top-k appends
+    hs_sketch *super = nullptr;     // hierarchy: sketch of F^3 super-items (Algorithm 3)
+    uint32_t super_mult = 0;        // hierarchy: c of the top-(c*k) super-items
     uint64_t *cand_key = nullptr;
     int32_t *cand_est = nullptr;
     unsigned long long *counters = nullptr;   // [0] candidates, [1] tmp, [2] distinct
@@ -537,14 +540,26 @@ hs_status search_pass(hs_sketch *h, int32_t theta, SearchMode mode, uint64_t lin
                                       h->num_sms * 8, h->stream));
             h->stats.kernel_launches += 1;
         }
+        // a scan touches every cell of the lines: refuse meshes whose scan would
+        // run for minutes, and keep each launch to about 2^34 cells
+        const uint64_t G = h->d.G;
+        if ((line_hi - line_lo) * G > kMaxScanCells)
+            return fail(HS_ERR_STATE,
+                        "full scan of %llu cells refused (directory search unavailable at this "
+                        "threshold); use the hierarchical query (sketch_set_hierarchy)",
+                        (unsigned long long)((line_hi - line_lo) * G));
+        const uint64_t seg = std::max<uint64_t>(1, (1ull << 34) / G);
         EventPair ev = take_events(h);
         cudaEventRecord(ev.a, h->stream);
-        HS_CUDA(launch_full_search(h->C, h->d, theta, mode, h->bitmap, h->nb, prune, line_lo,
-                                   line_hi, out, h->num_sms, h->stream, h->route.filter));
+        for (uint64_t l0 = line_lo; l0 < line_hi; l0 += seg) {
+            HS_CUDA(launch_full_search(h->C, h->d, theta, mode, h->bitmap, h->nb, prune, l0,
+                                       std::min(line_hi, l0 + seg), out, h->num_sms, h->stream,
+                                       h->route.filter));
+            h->stats.kernel_launches += 1;
+        }
         cudaEventRecord(ev.b, h->stream);
         h->pending_search.push_back(ev);
         h->stats.search_launches += 1;
-        h->stats.kernel_launches += 1;
     }
     h->stats.last_passes += 1;
     h->stats.last_threshold = theta;
@@ -605,6 +620,8 @@ hs_status sketch_create(const hs_params *params, void *cuda_stream, hs_sketch **
     d.log2w = params->log2_width;
     d.G = (uint32_t)std::llround(params->box / params->cell);
     d.inv_cell = (float)(1.0 / params->cell);
+    d.Gq = d.G;
+    d.F = 1;
     d.W = 1ull << params->log2_width;
     for (uint32_t r = 0; r < d.rows; ++r) {   // splitmix64 outputs 4r .. 4r+3
         d.seed[r].a0 = splitmix64_at(params->hash_seed, 4 * r + 0);
@@ -636,6 +653,7 @@ hs_status sketch_create(const hs_params *params, void *cuda_stream, hs_sketch **
 hs_status sketch_destroy(hs_sketch *h) {
     if (!h) return HS_OK;
     cudaStreamSynchronize(h->stream);
+    if (h->super) sketch_destroy(h->super);
     free_topk_scratch(h);
     free_dir(h);
     if (h->bins) cudaFree(h->bins);
@@ -670,6 +688,8 @@ hs_status sketch_update(hs_sketch *h, const float *xyz, uint64_t n, double sampl
     if (n > (~0ull - h->n_seen)) return fail(HS_ERR_ARG, "particle index overflow");
     if (is_device_ptr(xyz)) {
         hs_status st = launch_update_timed(h, xyz, n, h->n_seen, sample_rate);
+        if (st == HS_OK && h->super)
+            st = launch_update_timed(h->super, xyz, n, h->n_seen, sample_rate);
         if (st != HS_OK) return st;
     } else {
         hs_status st = ensure_staging(h);
@@ -684,11 +704,20 @@ hs_status sketch_update(hs_sketch *h, const float *xyz, uint64_t n, double sampl
             HS_CUDA(cudaEventRecord(h->ev_copied[b], h->copy_stream));
             HS_CUDA(cudaStreamWaitEvent(h->stream, h->ev_copied[b], 0));
             st = launch_update_timed(h, h->stage[b], cnt, h->n_seen + off, sample_rate);
+            if (st == HS_OK && h->super)
+                st = launch_update_timed(h->super, h->stage[b], cnt, h->n_seen + off, sample_rate);
             if (st != HS_OK) return st;
             HS_CUDA(cudaEventRecord(h->ev_free[b], h->stream));
         }
     }
     h->n_seen += n;
+    if (h->super) h->super->n_seen += n;
+    return HS_OK;
+}
+
+hs_status sketch_wait_copies(hs_sketch *h) {
+    if (!h) return fail(HS_ERR_ARG, "handle is NULL");
+    if (h->copy_stream) HS_CUDA(cudaStreamSynchronize(h->copy_stream));
     return HS_OK;
 }
 
@@ -719,10 +748,133 @@ hs_status sketch_query(hs_sketch *h, const uint64_t *keys, uint64_t m, int32_t *
     return HS_OK;
 }
 
+// One pass of the hierarchy's second layer over the key window [key_lo, key_hi).
+static hs_status expand_pass(hs_sketch *h, const uint64_t *skeys, uint64_t ns, int32_t theta,
+                             SearchMode mode, uint64_t key_lo, uint64_t key_hi,
+                             unsigned long long count_base, unsigned long long *count_out) {
+    HS_CUDA(cudaMemcpyAsync(&h->counters[0], &count_base, sizeof(count_base),
+                            cudaMemcpyHostToDevice, h->stream));
+    SearchOut out{h->cand_key, h->cand_est, &h->counters[0], h->cap};
+    if (!(mode == kGT && theta == INT32_MAX) && key_hi > key_lo) {
+        EventPair ev = take_events(h);
+        cudaEventRecord(ev.a, h->stream);
+        int launches = 0;
+        HS_CUDA(launch_expand(h->C, h->d, skeys, ns, h->super->d.F, h->super->d.G, theta, mode,
+                              key_lo, key_hi, out, h->num_sms * 8, h->stream, &launches));
+        cudaEventRecord(ev.b, h->stream);
+        h->pending_search.push_back(ev);
+        h->stats.search_launches += 1;
+        h->stats.kernel_launches += launches;
+    }
+    h->stats.last_passes += 1;
+    h->stats.last_threshold = theta;
+    unsigned long long c = 0;
+    HS_CUDA(cudaMemcpyAsync(&c, &h->counters[0], sizeof(c), cudaMemcpyDeviceToHost, h->stream));
+    HS_CUDA(cudaStreamSynchronize(h->stream));
+    *count_out = c;
+    return HS_OK;
+}
+
+// Hierarchical query (Algorithm 3, CSHi, with the top-(c*k) rule of the GPU
+// hierarchy): the c*k best super-items by the super sketch's own full search,
+// then the kk best cells inside them, found with a raised threshold like the
+// flat search.
+static hs_status topk_hier(hs_sketch *h, uint64_t kk, uint64_t *keys, int32_t *est,
+                           uint32_t *n_out) {
+    hs_sketch *S = h->super;
+    const uint64_t ms = std::min<uint64_t>((uint64_t)h->super_mult * kk, S->n_cells);
+    if (ms > 0xFFFFFFFFull) return fail(HS_ERR_ARG, "c * k too large");
+    std::vector<uint64_t> hk(ms);
+    std::vector<int32_t> he(ms);
+    uint32_t ns = 0;
+    hs_status st = topk_extract(S, (uint32_t)ms, hk.data(), he.data(), &ns);
+    if (st != HS_OK) return st;
+    const uint64_t *skeys = S->out_key;   // the super ranking stays on the device
+    st = drain(h);
+    if (st != HS_OK) return st;
+    st = ensure_topk_scratch(h, kk);
+    if (st != HS_OK) return st;
+    h->stats.last_passes = 0;
+    EventPair whole = take_events(h);
+    cudaEventRecord(whole.a, h->stream);
+    const uint64_t n_cells = h->n_cells;
+    int32_t theta = INT32_MIN;
+    uint64_t final_m = 0;
+    for (int round = 0;; ++round) {
+        if (round > 64) return fail(HS_ERR_STATE, "top-k threshold did not converge");
+        unsigned long long c = 0;
+        st = expand_pass(h, skeys, ns, theta, kGE, 0, n_cells, 0, &c);
+        if (st != HS_OK) return st;
+        h->stats.last_candidates = c;
+        if (c <= h->cap) {
+            if (c >= kk) {
+                final_m = c;
+                break;
+            }
+            if (theta == INT32_MIN) return fail(HS_ERR_STATE, "fewer cells than k");
+            theta = INT32_MIN;
+            continue;
+        }
+        int32_t t2 = 0;
+        st = kth_estimate(h, h->cand_key, h->cand_est, h->cap, kk, &t2);
+        if (st != HS_OK) return st;
+        if (t2 > theta) {
+            theta = t2;
+            continue;
+        }
+        unsigned long long c_gt = 0;
+        st = expand_pass(h, skeys, ns, theta, kGT, 0, n_cells, 0, &c_gt);
+        if (st != HS_OK) return st;
+        if (c_gt > h->cap) {
+            st = kth_estimate(h, h->cand_key, h->cand_est, h->cap, kk, &t2);
+            if (st != HS_OK) return st;
+            theta = t2;
+            continue;
+        }
+        if (c_gt >= kk) {
+            final_m = c_gt;
+            break;
+        }
+        // the ties at theta in key order: windows of the key space, halved
+        // when one holds more ties than the candidate buffer has room for
+        uint64_t need = kk - c_gt, have = 0, lo = 0, span = n_cells;
+        while (have < need && lo < n_cells) {
+            const uint64_t hi = span >= n_cells - lo ? n_cells : lo + span;
+            unsigned long long c2 = 0;
+            st = expand_pass(h, skeys, ns, theta, kEQ, lo, hi, c_gt + have, &c2);
+            if (st != HS_OK) return st;
+            if (c2 > h->cap) {
+                span = std::max<uint64_t>(1, span / 2);
+                continue;
+            }
+            have = c2 - c_gt;
+            lo = hi;
+        }
+        final_m = c_gt + have;
+        h->stats.last_candidates = final_m;
+        break;
+    }
+    st = finalize(h, final_m, kk);
+    if (st != HS_OK) return st;
+    const uint64_t n = std::min<uint64_t>(final_m, kk);
+    HS_CUDA(cudaMemcpyAsync(keys, h->out_key, n * 8, cudaMemcpyDeviceToHost, h->stream));
+    HS_CUDA(cudaMemcpyAsync(est, h->out_est, n * 4, cudaMemcpyDeviceToHost, h->stream));
+    cudaEventRecord(whole.b, h->stream);
+    HS_CUDA(cudaStreamSynchronize(h->stream));
+    float ms_t = 0;
+    if (cudaEventElapsedTime(&ms_t, whole.a, whole.b) == cudaSuccess) h->stats.topk_ms += ms_t;
+    h->pool.push_back(whole);
+    h->stats.topk_calls += 1;
+    drain_timings(h);
+    *n_out = (uint32_t)n;
+    return HS_OK;
+}
+
 hs_status topk_extract(hs_sketch *h, uint32_t k, uint64_t *keys, int32_t *est, uint32_t *n_out) {
     if (!h) return fail(HS_ERR_ARG, "handle is NULL");
     if (k == 0 || !keys || !est || !n_out) return fail(HS_ERR_ARG, "k == 0 or NULL output");
     const uint64_t kk = std::min<uint64_t>(k, h->n_cells);
+    if (h->super) return topk_hier(h, kk, keys, est, n_out);
     hs_status st = drain(h);
     if (st != HS_OK) return st;
     st = ensure_topk_scratch(h, kk);
@@ -831,6 +983,7 @@ hs_status sketch_reset(hs_sketch *h) {
     HS_CUDA(cudaMemsetAsync(h->probe, 0xFF, kProbeCap * 8, h->stream));
     h->n_seen = 0;
     h->probe_base = 0;
+    if (h->super) return sketch_reset(h->super);
     return HS_OK;
 }
 
@@ -861,6 +1014,12 @@ hs_status sketch_merge(hs_sketch *dst, hs_sketch *src) {
         dst->d.G != src->d.G || dst->d.inv_cell != src->d.inv_cell)
         return fail(HS_ERR_ARG, "sketches were built with different parameters");
     if (dst == src) return fail(HS_ERR_ARG, "cannot merge a sketch into itself");
+    if (!dst->super != !src->super)
+        return fail(HS_ERR_ARG, "one sketch has a hierarchy and the other has not");
+    if (dst->super) {
+        hs_status s2 = sketch_merge(dst->super, src->super);
+        if (s2 != HS_OK) return s2;
+    }
     hs_status st = drain(src);
     if (st == HS_OK) st = drain(dst);
     if (st != HS_OK) return st;
@@ -892,12 +1051,52 @@ hs_status sketch_seek(hs_sketch *h, uint64_t n_seen) {
     HS_CUDA(cudaMemsetAsync(h->probe, 0xFF, kProbeCap * 8, h->stream));
     h->n_seen = n_seen;
     h->probe_base = n_seen;
+    if (h->super) return sketch_seek(h->super, n_seen);
     return HS_OK;
 }
 
 hs_status sketch_flush(hs_sketch *h) {
     if (!h) return fail(HS_ERR_ARG, "handle is NULL");
+    if (h->super) {
+        hs_status st = drain(h->super);
+        if (st != HS_OK) return st;
+    }
     return drain(h);
+}
+
+hs_status sketch_set_hierarchy(hs_sketch *h, uint32_t super_factor, uint32_t super_log2_width,
+                               uint32_t c_mult) {
+    if (!h) return fail(HS_ERR_ARG, "handle is NULL");
+    if (h->super) return fail(HS_ERR_STATE, "the sketch already has a hierarchy");
+    if (h->n_seen != 0 || h->is_view || h->routing)
+        return fail(HS_ERR_STATE, "set the hierarchy on a fresh, plain sketch");
+    if (super_factor < 2 || super_factor > 64 || h->d.G % super_factor != 0 || h->d.G > 65535)
+        return fail(HS_ERR_ARG, "super_factor must be in [2, 64] and divide a mesh below 2^16");
+    if (c_mult < 1) return fail(HS_ERR_ARG, "c_mult must be >= 1");
+    hs_params q = h->p;
+    q.log2_width = super_log2_width;
+    q.cell = h->p.cell * super_factor;
+    q.hash_seed = h->p.hash_seed + 1;
+    hs_sketch *s = nullptr;
+    hs_status st = sketch_create(&q, h->stream, &s);
+    if (st != HS_OK) return st;
+    if (s->d.G * super_factor != h->d.G) {
+        sketch_destroy(s);
+        return fail(HS_ERR_ARG, "box / (cell * super_factor) is not the super grid");
+    }
+    s->d.Gq = h->d.G;
+    s->d.inv_cell = h->d.inv_cell;
+    s->d.F = super_factor;
+    s->d.fmagic = (uint32_t)((0x100000000ull + super_factor - 1) / super_factor);
+    h->super = s;
+    h->super_mult = c_mult;
+    return HS_OK;
+}
+
+hs_status sketch_super(hs_sketch *h, hs_sketch **out) {
+    if (!h || !out) return fail(HS_ERR_ARG, "NULL argument");
+    *out = h->super;
+    return HS_OK;
 }
 
 hs_status sketch_synchronize(hs_sketch *h) {
@@ -1219,6 +1418,8 @@ hs_status batch_create(const hs_params *params, uint32_t n_volumes, const double
     }
     b->d.G = b->G[0];
     b->d.inv_cell = b->inv[0];
+    b->d.Gq = b->d.G;
+    b->d.F = 1;
     b->bl = bin_layout(batch_flat_desc(b), kBinSmemBudget);
     if (b->bl.slot == 0 || b->bl.nbins >= 65536) {
         delete b;
@@ -1360,6 +1561,8 @@ hs_status batch_topk(hs_batch *b, uint32_t k, uint64_t *keys, int32_t *est, uint
         h->C = b->C + (size_t)v * b->d.rows * b->d.W;
         h->probe = b->probe + (size_t)v * kBatchProbe;
         h->d.G = b->G[v];
+        h->d.Gq = b->G[v];
+        h->d.F = 1;
         h->d.inv_cell = b->inv[v];
         h->n_cells = (uint64_t)b->G[v] * b->G[v] * b->G[v];
         h->key_bits = 1;

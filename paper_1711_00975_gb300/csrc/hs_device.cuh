@@ -29,9 +29,13 @@ struct RowSeed {
 struct SketchDesc {
     uint32_t rows;
     uint32_t log2w;
-    uint32_t G;
+    uint32_t G;          // cells per axis of the keys this sketch counts
     float inv_cell;
     uint64_t W;
+    uint32_t Gq;         // cells per axis of the quantisation mesh (G * F)
+    uint32_t F;          // super-item side in cells (1: the cells themselves)
+    uint32_t fmagic;     // ceil(2^32 / F): c / F = umulhi(c, fmagic) for c, F < 2^16
+    uint32_t pad;
     RowSeed seed[kMaxRows];
 };
 
@@ -112,6 +116,21 @@ __device__ __forceinline__ bool axis_cell(float x, float inv, uint32_t G, uint32
     int i = __float2int_rd(p);      // floor, exact for p in range
     c = (unsigned)i < G ? (uint32_t)i : wrap_cell(i, G);
     return true;
+}
+
+// Cell of a particle on the quantisation mesh; for a super-item sketch
+// (Algorithm 3) the F x F x F block holding that cell.
+__device__ __forceinline__ bool particle_cell(const SketchDesc &d, float x, float y, float z,
+                                              uint32_t &cx, uint32_t &cy, uint32_t &cz) {
+    bool valid = axis_cell(x, d.inv_cell, d.Gq, cx);
+    valid &= axis_cell(y, d.inv_cell, d.Gq, cy);
+    valid &= axis_cell(z, d.inv_cell, d.Gq, cz);
+    if (d.F > 1) {
+        cx = __umulhi(cx, d.fmagic);
+        cy = __umulhi(cy, d.fmagic);
+        cz = __umulhi(cz, d.fmagic);
+    }
+    return valid;
 }
 
 __device__ __forceinline__ uint64_t key_of(uint32_t cx, uint32_t cy, uint32_t cz, uint32_t G) {

@@ -100,9 +100,7 @@ __device__ __forceinline__ bool prep_particle(float x, float y, float z, uint64_
                                               uint64_t &cell) {
     bool keep = a.keep_all || splitmix64_at(a.sample_seed, g) < a.thr;
     uint32_t cx = 0, cy = 0, cz = 0;
-    bool valid = axis_cell(x, d.inv_cell, d.G, cx);
-    valid &= axis_cell(y, d.inv_cell, d.G, cy);
-    valid &= axis_cell(z, d.inv_cell, d.G, cz);
+    const bool valid = particle_cell(d, x, y, z, cx, cy, cz);
     bool routed = false;
     if (a.route.bits && valid) routed = routed_cell(a.route, cx, cy, cz);
     if (g - a.probe_base < a.probe_end - a.probe_base)   // the sketch's cells only

@@ -15,6 +15,8 @@
 // |C| >= theta) in shared memory rejects a cell as soon as more than t - need
 // of its rows are cold, before any counter is read.  Survivors are estimated
 // exactly from the counters and compared with theta.
+#include <algorithm>
+
 #include "hs_device.cuh"
 #include "hs_kernels.h"
 
@@ -135,6 +137,56 @@ __global__ void __launch_bounds__(1024, 1)
                 v[r] += step[r];
             }
         }
+    }
+}
+
+// Hierarchical query (Algorithm 3, CSHi), second layer: every cell of the
+// listed super-items (F x F x F blocks on a grid of Gs per axis) is estimated
+// from this sketch and kept when it passes theta and its key lies in
+// [key_lo, key_hi).  One thread per cell; total = ns * F^3 < 2^32.
+template <int T>
+__global__ void __launch_bounds__(256)
+    k_expand(const int32_t *__restrict__ C, const SketchDesc d,
+             const uint64_t *__restrict__ skeys, uint32_t total, uint32_t F, uint32_t Gs,
+             int32_t theta, uint32_t mode, uint64_t key_lo, uint64_t key_hi, SearchOut out) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t F3 = F * F * F;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total;
+         base += stride) {
+        const uint32_t i = base + lane;
+        bool pass = false;
+        int32_t e = 0;
+        uint64_t key = 0;
+        if (i < total) {
+            const uint64_t s = skeys[i / F3];
+            const uint32_t l = i % F3;
+            const uint32_t sx = (uint32_t)(s % Gs);
+            const uint64_t rest = s / Gs;
+            const uint32_t sy = (uint32_t)(rest % Gs), sz = (uint32_t)(rest / Gs);
+            const uint32_t cx = sx * F + l % F, cy = sy * F + (l / F) % F, cz = sz * F + l / (F * F);
+            key = key_of(cx, cy, cz, d.G);
+            if (key >= key_lo && key < key_hi) {
+                if (T == 5) {
+                    int32_t ev[5];
+#pragma unroll
+                    for (int r = 0; r < 5; ++r) {
+                        const uint64_t v = row_value(d.seed[r], cx, cy, cz);
+                        ev[r] = signed_count(__ldg(C + r * d.W + bucket_of(v, d.log2w)), v, d.log2w);
+                    }
+                    e = median5(ev[0], ev[1], ev[2], ev[3], ev[4]);
+                } else {
+                    int32_t ev[kMaxRows];
+                    for (uint32_t r = 0; r < d.rows; ++r) {
+                        const uint64_t v = row_value(d.seed[r], cx, cy, cz);
+                        ev[r] = signed_count(__ldg(C + r * d.W + bucket_of(v, d.log2w)), v, d.log2w);
+                    }
+                    e = lower_median_dyn(ev, (int)d.rows);
+                }
+                pass = passes(e, theta, mode);
+            }
+        }
+        warp_append(pass, key, e, out, lane);
     }
 }
 
@@ -260,6 +312,29 @@ cudaError_t launch_full_search(const int32_t *C, const SketchDesc &d, int32_t th
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k<<<(unsigned)b, 1024, smem, s>>>(C, d, theta, mode, bitmap, nb, prune, line_lo, line_hi,
                                          out, skip);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_expand(const int32_t *C, const SketchDesc &d, const uint64_t *skeys, uint64_t ns,
+                          uint32_t F, uint32_t Gs, int32_t theta, SearchMode mode, uint64_t key_lo,
+                          uint64_t key_hi, SearchOut out, int max_blocks, cudaStream_t s,
+                          int *launches) {
+    const uint64_t F3 = (uint64_t)F * F * F;
+    const uint64_t per = ((1ull << 31) / F3);            // super-items per launch: < 2^31 cells
+    for (uint64_t s0 = 0; s0 < ns; s0 += per) {
+        const uint64_t cnt = std::min<uint64_t>(per, ns - s0);
+        const uint32_t total = (uint32_t)(cnt * F3);
+        uint64_t blocks = ((uint64_t)total + 255) / 256;
+        if (blocks > (uint64_t)max_blocks) blocks = (uint64_t)max_blocks;
+        if (blocks < 1) blocks = 1;
+        if (d.rows == 5)
+            k_expand<5><<<(unsigned)blocks, 256, 0, s>>>(C, d, skeys + s0, total, F, Gs, theta, mode,
+                                                        key_lo, key_hi, out);
+        else
+            k_expand<0><<<(unsigned)blocks, 256, 0, s>>>(C, d, skeys + s0, total, F, Gs, theta, mode,
+                                                        key_lo, key_hi, out);
+        *launches += 1;
     }
     return cudaGetLastError();
 }

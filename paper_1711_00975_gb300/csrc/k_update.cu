@@ -35,9 +35,7 @@ __device__ __forceinline__ void add_particle(float x, float y, float z, uint64_t
                                              uint32_t *__restrict__ C) {
     bool keep = a.keep_all || splitmix64_at(a.sample_seed, g) < a.thr;
     uint32_t cx = 0, cy = 0, cz = 0;
-    bool valid = axis_cell(x, d.inv_cell, d.G, cx);
-    valid &= axis_cell(y, d.inv_cell, d.G, cy);
-    valid &= axis_cell(z, d.inv_cell, d.G, cz);
+    const bool valid = particle_cell(d, x, y, z, cx, cy, cz);
     if (g - a.probe_base < a.probe_end - a.probe_base)
         a.probe[g - a.probe_base] = valid ? key_of(cx, cy, cz, d.G) : kInvalidKey;
     if (!(keep && valid)) return;

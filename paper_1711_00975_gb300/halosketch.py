@@ -85,6 +85,9 @@ def lib():
             sig = {
                 "sketch_create": [ctypes.POINTER(hs_params), vp, ctypes.POINTER(vp)],
                 "sketch_update": [vp, vp, u64, f64],
+                "sketch_set_hierarchy": [vp, u32, u32, u32],
+                "sketch_super": [vp, ctypes.POINTER(vp)],
+                "sketch_wait_copies": [vp],
                 "sketch_query": [vp, vp, u64, vp],
                 "topk_extract": [vp, u32, vp, vp, ctypes.POINTER(u32)],
                 "sketch_destroy": [vp],
@@ -246,6 +249,10 @@ def sketch_seek(h, n_seen: int) -> None:
     _check(lib().sketch_seek(h, n_seen), "sketch_seek")
 
 
+def sketch_wait_copies(h) -> None:
+    _check(lib().sketch_wait_copies(h), "sketch_wait_copies")
+
+
 def sketch_flush(h) -> None:
     _check(lib().sketch_flush(h), "sketch_flush")
 
@@ -337,6 +344,23 @@ class Sketch:
 
     def flush(self):
         sketch_flush(self.h)
+
+    def set_hierarchy(self, super_factor: int, super_log2_width: int, c_mult: int = 2):
+        """Count super-items of super_factor^3 cells too and query hierarchically."""
+        _check(lib().sketch_set_hierarchy(self.h, super_factor, super_log2_width, c_mult),
+               "sketch_set_hierarchy")
+
+    def super_handle(self):
+        out = ctypes.c_void_p()
+        _check(lib().sketch_super(self.h, ctypes.byref(out)), "sketch_super")
+        return out if out.value else None
+
+    def super_counters(self) -> np.ndarray:
+        sh = self.super_handle()
+        info = sketch_info(sh)
+        out = np.empty((info.rows, info.width), np.int32)
+        sketch_counters(sh, out)
+        return out
 
     def seek(self, n_seen: int):
         sketch_seek(self.h, n_seen)
