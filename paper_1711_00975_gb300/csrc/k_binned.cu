@@ -93,20 +93,32 @@ __device__ __noinline__ void route_add(const ScatterArgs &a, uint32_t cx, uint32
     atomicAdd(&a.rblocks[(uint64_t)blk * (f.R * f.R * f.R) + local], 1);
 }
 
+// Scatter variants: one plain sketch, a batch of volumes, a learned sketch that
+// routes some coarse cells to exact counters, a super-item sketch (Algorithm 3).
+constexpr int kModePlain = 0, kModeBatch = 1, kModeRoute = 2, kModeSuper = 3;
+
 // Mesh reduction, sampling and probe entry of one particle; true when it is
 // kept, with its cell packed as cx | cy << 21 | cz << 42 (G <= 2^21).
+template <int MODE>
 __device__ __forceinline__ bool prep_particle(float x, float y, float z, uint64_t g,
                                               const SketchDesc &d, const ScatterArgs &a,
                                               uint64_t &cell) {
     bool keep = a.keep_all || splitmix64_at(a.sample_seed, g) < a.thr;
     uint32_t cx = 0, cy = 0, cz = 0;
-    const bool valid = particle_cell(d, x, y, z, cx, cy, cz);
+    bool valid = axis_cell(x, d.inv_cell, d.Gq, cx);
+    valid &= axis_cell(y, d.inv_cell, d.Gq, cy);
+    valid &= axis_cell(z, d.inv_cell, d.Gq, cz);
+    if (MODE == kModeSuper) {              // the F^3 block holding the cell
+        cx = __umulhi(cx, d.fmagic);
+        cy = __umulhi(cy, d.fmagic);
+        cz = __umulhi(cz, d.fmagic);
+    }
     bool routed = false;
-    if (a.route.bits && valid) routed = routed_cell(a.route, cx, cy, cz);
+    if (MODE == kModeRoute && valid) routed = routed_cell(a.route, cx, cy, cz);
     if (g - a.probe_base < a.probe_end - a.probe_base)   // the sketch's cells only
         write_probe(a.probe, g - a.probe_base, valid && !routed, cx, cy, cz, d.G);
     cell = (uint64_t)cx | ((uint64_t)cy << 21) | ((uint64_t)cz << 42);
-    if (routed && keep) {
+    if (MODE == kModeRoute && routed && keep) {
         route_add(a, cx, cy, cz);
         return false;
     }
@@ -235,10 +247,11 @@ constexpr int kQueuePerWarp = 128;     // 32 lanes x 4 particles
 // (nbins <= kMaxFlushPerThread * 32 * warps per block).
 constexpr int kMaxFlushPerThread = 6;
 
-template <int T, bool VEC, bool BATCH, int THREADS>
+template <int T, bool VEC, int MODE, int THREADS>
 __global__ void __launch_bounds__(THREADS, 1)
     k_bin_scatter(const float *__restrict__ xyz, const SketchDesc d, const ScatterArgs a,
                   uint32_t *__restrict__ C) {
+    constexpr bool BATCH = MODE == kModeBatch;
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t *s_fill = reinterpret_cast<uint32_t *>(smem);
     const uint32_t fill_bytes = (a.nbins * 4 + 15) & ~15u;
@@ -295,10 +308,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                     ok[3] = prep_particle_batch(w.y, w.z, w.w, 4 * g4 + 3, a, vh, cell[3]);
                 } else {
                     uint64_t g = a.g0 + 4 * g4;
-                    ok[0] = prep_particle(u.x, u.y, u.z, g, d, a, cell[0]);
-                    ok[1] = prep_particle(u.w, v.x, v.y, g + 1, d, a, cell[1]);
-                    ok[2] = prep_particle(v.z, v.w, w.x, g + 2, d, a, cell[2]);
-                    ok[3] = prep_particle(w.y, w.z, w.w, g + 3, d, a, cell[3]);
+                    ok[0] = prep_particle<MODE>(u.x, u.y, u.z, g, d, a, cell[0]);
+                    ok[1] = prep_particle<MODE>(u.w, v.x, v.y, g + 1, d, a, cell[1]);
+                    ok[2] = prep_particle<MODE>(v.z, v.w, w.x, g + 2, d, a, cell[2]);
+                    ok[3] = prep_particle<MODE>(w.y, w.z, w.w, g + 3, d, a, cell[3]);
                 }
             } else {
                 uint32_t vh = BATCH ? vol_of(a, 4 * g4 < a.n ? 4 * g4 : a.n - 1) : 0;
@@ -311,7 +324,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                                                     __ldcs(xyz + 3 * i + 2), i, a, vh, cell[j]);
                     else
                         ok[j] = i < a.n &&
-                                prep_particle(__ldcs(xyz + 3 * i), __ldcs(xyz + 3 * i + 1),
+                                prep_particle<MODE>(__ldcs(xyz + 3 * i), __ldcs(xyz + 3 * i + 1),
                                               __ldcs(xyz + 3 * i + 2), a.g0 + i, d, a, cell[j]);
                 }
             }
@@ -325,7 +338,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                             prep_particle_batch(__ldcs(xyz + 3 * i), __ldcs(xyz + 3 * i + 1),
                                                 __ldcs(xyz + 3 * i + 2), i, a, vh, cell[j]);
                 else
-                    ok[j] = i < a.n && prep_particle(__ldcs(xyz + 3 * i), __ldcs(xyz + 3 * i + 1),
+                    ok[j] = i < a.n && prep_particle<MODE>(__ldcs(xyz + 3 * i), __ldcs(xyz + 3 * i + 1),
                                                      __ldcs(xyz + 3 * i + 2), a.g0 + i, d, a,
                                                      cell[j]);
             }
@@ -506,7 +519,9 @@ cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const 
     a.probe_per_vol = probe_per_vol;
     uint32_t *Cu = reinterpret_cast<uint32_t *>(C);
     // the flush phase covers kMaxFlushPerThread due words per warp
-    if (threads != 512 || L.nbins > (uint32_t)kMaxFlushPerThread * 512) threads = kScatterThreads;
+    // only batches are tuned over the block size
+    if (threads != 512 || !vols || L.nbins > (uint32_t)kMaxFlushPerThread * 512)
+        threads = kScatterThreads;
     bool vec = (reinterpret_cast<uintptr_t>(xyz) & 15u) == 0;
     uint64_t per_tile = (uint64_t)threads * 4;
     uint64_t need_blocks = (n + per_tile - 1) / per_tile;
@@ -516,28 +531,28 @@ cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const 
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
         kern<<<blocks, threads, L.smem, s>>>(xyz, d, a, Cu);
     };
-#define HS_SCATTER_DISPATCH(TH)                                                            \
-    if (vols) {                                                                            \
-        if (d.rows == 5) {                                                                 \
-            if (vec) launch(k_bin_scatter<5, true, true, TH>);                            \
-            else launch(k_bin_scatter<5, false, true, TH>);                               \
-        } else {                                                                           \
-            if (vec) launch(k_bin_scatter<0, true, true, TH>);                            \
-            else launch(k_bin_scatter<0, false, true, TH>);                               \
-        }                                                                                  \
-    } else if (d.rows == 5) {                                                              \
-        if (vec) launch(k_bin_scatter<5, true, false, TH>);                               \
-        else launch(k_bin_scatter<5, false, false, TH>);                                  \
+#define HS_SCATTER_ROWS(MODE, TH)                                                          \
+    if (d.rows == 5) {                                                                     \
+        if (vec) launch(k_bin_scatter<5, true, MODE, TH>);                                 \
+        else launch(k_bin_scatter<5, false, MODE, TH>);                                    \
     } else {                                                                               \
-        if (vec) launch(k_bin_scatter<0, true, false, TH>);                               \
-        else launch(k_bin_scatter<0, false, false, TH>);                                  \
+        if (vec) launch(k_bin_scatter<0, true, MODE, TH>);                                 \
+        else launch(k_bin_scatter<0, false, MODE, TH>);                                    \
     }
-    if (threads == 512) {
-        HS_SCATTER_DISPATCH(512)
+    if (vols) {
+        if (threads == 512) {
+            HS_SCATTER_ROWS(kModeBatch, 512)
+        } else {
+            HS_SCATTER_ROWS(kModeBatch, 1024)
+        }
+    } else if (route) {
+        HS_SCATTER_ROWS(kModeRoute, 1024)
+    } else if (d.F > 1) {
+        HS_SCATTER_ROWS(kModeSuper, 1024)
     } else {
-        HS_SCATTER_DISPATCH(1024)
+        HS_SCATTER_ROWS(kModePlain, 1024)
     }
-#undef HS_SCATTER_DISPATCH
+#undef HS_SCATTER_ROWS
     return cudaGetLastError();
 }
 
