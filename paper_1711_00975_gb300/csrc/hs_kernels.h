@@ -134,10 +134,9 @@ cudaError_t launch_probe_distinct(const uint64_t *probe, uint64_t m, uint64_t *s
                                   cudaStream_t s);
 
 // ---- output-sensitive full search (k_dir.cu) ----
-struct DirRecord {           // one mesh line of a row's directory
-    uint64_t L;              // a1*cy + a2*cz + b of that row (mod 2^64)
-    uint32_t cy, cz;
-};
+// one mesh line of a row's directory: cy | cz << 16 (directories exist for
+// G < 2^16 only); the line's value L is recomputed from it when queried
+typedef uint32_t DirRecord;
 // directory of the G^2 lines of row r bucketed by the top D bits of L
 cudaError_t launch_dir_build(const SketchDesc &d, int r, uint32_t D, uint32_t *offsets,
                              uint32_t *cursor, DirRecord *rec, uint32_t *scan_scratch,

@@ -52,7 +52,7 @@ __global__ void k_dir_scatter(const SketchDesc d, int r, uint32_t D, uint32_t *_
         uint32_t cy = (uint32_t)(line % d.G), cz = (uint32_t)(line / d.G);
         uint64_t L = line_value(d.seed[r], cy, cz);
         uint32_t pos = atomicAdd(&cursor[L >> (64 - D)], 1u);
-        rec[pos] = DirRecord{L, cy, cz};
+        rec[pos] = cy | (cz << 16);
     }
 }
 
@@ -166,8 +166,9 @@ __global__ void __launch_bounds__(256)
             const uint64_t slot = (slot0 + j) & (nslots - 1);
             const uint32_t e0 = offsets[slot], e1 = offsets[slot + 1];
             for (uint32_t e = e0; e < e1; ++e) {
-                const DirRecord R = rec[e];
-                if (((R.L + Tx) >> s) != h) continue;
+                const DirRecord p = rec[e];
+                const struct { uint32_t cy, cz; } R = {p & 0xFFFFu, p >> 16};
+                if (((line_value(d.seed[r], R.cy, R.cz) + Tx) >> s) != h) continue;
                 const uint64_t line = (uint64_t)R.cy + (uint64_t)d.G * R.cz;
                 if (line < line_lo || line >= line_hi) continue;
                 if (skip.bits && routed_cell(skip, cx, R.cy, R.cz)) continue;
