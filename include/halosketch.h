@@ -134,8 +134,8 @@ hs_status sketch_create(const hs_params *params, void *cuda_stream, hs_sketch **
  * n_seen += n.  sample_rate in (0, 1]; rate 1 keeps every particle.
  * Device xyz: asynchronous on the handle's stream; the buffer must stay valid
  * until that work completes.  Host xyz: copied in chunks through the
- * library's staging buffers (two device buffers of 2^23 particles: the copy of
- * one, on the handle's own copy stream, overlaps the update of the other); the
+ * library's staging buffers (three device buffers of 2^24 particles: copies on
+ * the handle's own copy stream run ahead of the updates of earlier pieces); the
  * call returns after the last copy is issued (pageable memory may be reused on
  * return; pinned memory after sketch_wait_copies).  n == 0 is a no-op.
  * HS_ERR_ARG for a null handle, a null xyz with n > 0, or a rate outside (0, 1].

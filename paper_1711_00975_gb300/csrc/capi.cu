@@ -41,7 +41,8 @@ hs_status fail(hs_status st, const char *fmt, ...) {
 
 constexpr uint64_t kProbeCap = 1ull << 20;        // keys of the first 2^20 particles
 constexpr uint32_t kProbeSlotsLog2 = 21;
-constexpr uint64_t kStageParticles = 1ull << 23;  // 96 MiB per staging buffer
+constexpr uint64_t kStageParticles = 1ull << 24;  // 192 MiB per staging buffer
+constexpr int kStageBuffers = 3;                    // copies run ahead through a drain
 constexpr size_t kSearchSmemBudget = 192 * 1024;
 constexpr size_t kBinSmemBudget = 224 * 1024;
 constexpr uint64_t kBinBudgetBytes = 4ull << 30;   // global bins, at most
@@ -69,10 +70,10 @@ struct hs_sketch {
     uint64_t n_seen = 0;
 
     // staging for host particle buffers
-    float *stage[2] = {nullptr, nullptr};
+    float *stage[kStageBuffers] = {};
     cudaStream_t copy_stream = nullptr;
-    cudaEvent_t ev_copied[2] = {nullptr, nullptr};
-    cudaEvent_t ev_free[2] = {nullptr, nullptr};
+    cudaEvent_t ev_copied[kStageBuffers] = {};
+    cudaEvent_t ev_free[kStageBuffers] = {};
 
     // top-k scratch
     uint64_t cap = 0;               // candidate capacity
@@ -122,6 +123,8 @@ struct hs_sketch {
     uint16_t *bins = nullptr;
     uint32_t *bin_cursor = nullptr;
     uint32_t bin_cap = 0;
+    uint4 *carry = nullptr;         // scatter rings carried from one launch to the next
+    bool carry_valid = false;
     double pending = 0;          // kept particles binned since the last drain
     double pending_limit = 0;    // drain before the expected bin load passes this
 
@@ -331,7 +334,7 @@ bool ensure_dir(hs_sketch *h, int r) {
 
 hs_status ensure_staging(hs_sketch *h) {
     if (h->stage[0]) return HS_OK;
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kStageBuffers; ++i) {
         HS_CUDA(cudaMalloc(&h->stage[i], kStageParticles * 12));
         HS_CUDA(cudaEventCreateWithFlags(&h->ev_copied[i], cudaEventDisableTiming));
         HS_CUDA(cudaEventCreateWithFlags(&h->ev_free[i], cudaEventDisableTiming));
@@ -362,6 +365,12 @@ hs_status drain(hs_sketch *h) {
     if (h->pending <= 0) return HS_OK;
     EventPair ev = take_events(h);
     cudaEventRecord(ev.a, h->stream);
+    if (h->carry_valid) {
+        HS_CUDA(launch_carry_flush(h->bl, h->carry, (uint32_t)h->num_sms, h->bins, h->bin_cursor,
+                                   h->bin_cap, h->C, h->stream));
+        h->carry_valid = false;
+        h->stats.kernel_launches += 1;
+    }
     HS_CUDA(launch_bin_accumulate(h->bl, h->bins, h->bin_cursor, h->bin_cap, h->C, h->stream));
     cudaEventRecord(ev.b, h->stream);
     h->pending_flush.push_back(ev);
@@ -376,6 +385,7 @@ hs_status discard_pending(hs_sketch *h) {
     if (h->pending > 0 && h->bin_cursor)
         HS_CUDA(cudaMemsetAsync(h->bin_cursor, 0, (size_t)h->bl.nbins * 4, h->stream));
     h->pending = 0;
+    h->carry_valid = false;
     return HS_OK;
 }
 
@@ -396,6 +406,7 @@ hs_status ensure_bins(hs_sketch *h, uint64_t n, double rate) {
     cap = std::max<uint64_t>(cap, 4096);
     cap = std::min<uint64_t>(cap, 0xFFFFFFF0ull);
     cap = (cap + 15) & ~15ull;
+    HS_CUDA(cudaMalloc(&h->carry, (size_t)h->num_sms * carry_words16(h->bl) * 16));
     HS_CUDA(cudaMalloc(&h->bins, (size_t)h->bl.nbins * cap * 2));
     HS_CUDA(cudaMalloc(&h->bin_cursor, (size_t)h->bl.nbins * 4));
     HS_CUDA(cudaMemsetAsync(h->bin_cursor, 0, (size_t)h->bl.nbins * 4, h->stream));
@@ -430,7 +441,9 @@ hs_status launch_update_timed(hs_sketch *h, const float *xyz, uint64_t n, uint64
                                            h->p.sample_seed, h->probe, h->probe_base, kProbeCap,
                                            h->bl, h->bins, h->bin_cursor, h->bin_cap, h->num_sms,
                                            h->stream, nullptr, 0, 0, 1024,
-                                           h->routing ? &h->route : nullptr));
+                                           h->routing ? &h->route : nullptr, h->carry,
+                                           h->carry_valid ? 1 : 0, 1));
+                h->carry_valid = true;
                 cudaEventRecord(ev.b, h->stream);
                 h->pending_update.push_back(ev);
                 h->pending += (double)cnt * rate;
@@ -657,13 +670,14 @@ hs_status sketch_destroy(hs_sketch *h) {
     free_topk_scratch(h);
     free_dir(h);
     if (h->bins) cudaFree(h->bins);
+    if (h->carry) cudaFree(h->carry);
     if (h->bin_cursor) cudaFree(h->bin_cursor);
     if (h->C && !h->is_view) cudaFree(h->C);
     if (h->probe && !h->is_view) cudaFree(h->probe);
     if (h->q_keys) cudaFree(h->q_keys);
     if (h->q_est) cudaFree(h->q_est);
     if (h->flags) cudaFree(h->flags);
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kStageBuffers; ++i) {
         if (h->stage[i]) cudaFree(h->stage[i]);
         if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
         if (h->ev_free[i]) cudaEventDestroy(h->ev_free[i]);
@@ -694,10 +708,16 @@ hs_status sketch_update(hs_sketch *h, const float *xyz, uint64_t n, double sampl
     } else {
         hs_status st = ensure_staging(h);
         if (st != HS_OK) return st;
+        // size the bins for the whole call, not for one staged piece
+        const uint64_t first = std::min(kStageParticles, n);
+        if (want_binned(h, first, sample_rate)) st = ensure_bins(h, n, sample_rate);
+        if (st == HS_OK && h->super && want_binned(h->super, first, sample_rate))
+            st = ensure_bins(h->super, n, sample_rate);
+        if (st != HS_OK) return st;
         int i = 0;
         for (uint64_t off = 0; off < n; off += kStageParticles, ++i) {
             uint64_t cnt = std::min(kStageParticles, n - off);
-            int b = i & 1;
+            int b = i % kStageBuffers;
             HS_CUDA(cudaStreamWaitEvent(h->copy_stream, h->ev_free[b], 0));
             HS_CUDA(cudaMemcpyAsync(h->stage[b], xyz + 3 * off, cnt * 12, cudaMemcpyHostToDevice,
                                     h->copy_stream));

@@ -47,7 +47,14 @@ cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const 
                                uint16_t *bins, uint32_t *cursor, uint32_t cap, int blocks,
                                cudaStream_t s, const VolumeDesc *vols = nullptr, uint32_t nvol = 0,
                                uint32_t probe_per_vol = 0, int threads = 1024,
-                               const RouteTarget *route = nullptr);
+                               const RouteTarget *route = nullptr, uint4 *carry = nullptr,
+                               int carry_in = 0, int carry_out = 0);
+// 16-byte words of one scatter block's carried rings (fill words + rings)
+uint32_t carry_words16(const BinLayout &L);
+// move the carried rings of nblocks scatter blocks into the global bins
+cudaError_t launch_carry_flush(const BinLayout &L, const uint4 *carry, uint32_t nblocks,
+                               uint16_t *bins, uint32_t *cursor, uint32_t cap, int32_t *C,
+                               cudaStream_t s);
 cudaError_t launch_bin_accumulate(const BinLayout &L, uint16_t *bins, uint32_t *cursor,
                                   uint32_t cap, int32_t *C, cudaStream_t s);
 

@@ -47,6 +47,10 @@ struct ScatterArgs {
     RouteFilter route;        // routed cells go to exact dense blocks instead
     const uint32_t *rprefix;
     int32_t *rblocks;
+    uint4 *carry;             // per-block copy of the rings between launches (or nullptr)
+    uint32_t carry_in;        // start from the carried rings instead of empty ones
+    uint32_t carry_out;       // leave the rings in the carry instead of flushing them
+    uint32_t carry16;         // 16-byte words of one block's carry
     const VolumeDesc *vols;   // batch: one entry per volume (nullptr for one sketch)
     uint32_t nvol;
     uint32_t probe_per_vol;   // batch: probe window of each volume
@@ -263,8 +267,14 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t ndue = (a.nbins + 31) / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint64_t *q = s_queue + warp * kQueuePerWarp;
-    for (uint32_t b = threadIdx.x; b < a.nbins; b += blockDim.x)
-        s_fill[b] = ((2u * (b >> 1)) & (a.slot - 1)) << 16;   // rotation, nothing staged
+    if (a.carry_in) {   // the rings this block left at the end of the previous launch
+        const uint4 *src = a.carry + (uint64_t)blockIdx.x * a.carry16;
+        uint4 *dst = reinterpret_cast<uint4 *>(smem);
+        for (uint32_t i = threadIdx.x; i < a.carry16; i += blockDim.x) dst[i] = src[i];
+    } else {
+        for (uint32_t b = threadIdx.x; b < a.nbins; b += blockDim.x)
+            s_fill[b] = ((2u * (b >> 1)) & (a.slot - 1)) << 16;   // rotation, nothing staged
+    }
     for (uint32_t i = threadIdx.x; i < ndue; i += blockDim.x) s_due[i] = 0;
     __syncthreads();
 
@@ -393,6 +403,13 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         __syncthreads();
     }
+    if (a.carry_out) {   // every ring holds fewer than `unit` codes: keep them for the next launch
+        __syncthreads();
+        uint4 *dst = a.carry + (uint64_t)blockIdx.x * a.carry16;
+        const uint4 *src = reinterpret_cast<const uint4 *>(smem);
+        for (uint32_t i = threadIdx.x; i < a.carry16; i += blockDim.x) dst[i] = src[i];
+        return;
+    }
     // what is left in shared memory
     for (uint32_t b = threadIdx.x; b < a.nbins; b += blockDim.x) {
         uint32_t w = s_fill[b];
@@ -406,6 +423,31 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (g + j < a.cap) dst[g + j] = c;
                 else direct_add(C, a, b, c);
             }
+        }
+    }
+}
+
+// The rings carried out of the last scatter launch of every block, moved to
+// the global bins: one thread per (block, bin).
+__global__ void k_carry_flush(const uint4 *__restrict__ carry, uint32_t nblocks, ScatterArgs a,
+                              uint32_t *__restrict__ C) {
+    const uint64_t total = (uint64_t)nblocks * a.nbins;
+    const uint32_t fill_bytes = (a.nbins * 4 + 15) & ~15u;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+        const uint32_t blk = (uint32_t)(t / a.nbins), b = (uint32_t)(t % a.nbins);
+        const unsigned char *base =
+            reinterpret_cast<const unsigned char *>(carry + (uint64_t)blk * a.carry16);
+        const uint32_t w = reinterpret_cast<const uint32_t *>(base)[b];
+        const uint32_t f = min(w & 0xFFFFu, a.slot);
+        if (!f) continue;
+        const uint16_t *ring = reinterpret_cast<const uint16_t *>(base + fill_bytes) + (b << a.log2_slot);
+        const uint32_t g = atomicAdd(&a.cursor[b], f);
+        uint16_t *dst = a.bins + (uint64_t)b * a.cap;
+        for (uint32_t j = 0; j < f; ++j) {
+            const uint16_t c = ring[((w >> 16) + j) & (a.slot - 1)];
+            if (g + j < a.cap) dst[g + j] = c;
+            else direct_add(C, a, b, c);
         }
     }
 }
@@ -459,6 +501,11 @@ __global__ void __launch_bounds__(1024)
 
 }  // namespace
 
+uint32_t carry_words16(const BinLayout &L) {
+    return (uint32_t)((((size_t)L.nbins * 4 + 15) & ~(size_t)15) +
+                      (((size_t)L.nbins * L.slot * 2 + 15) & ~(size_t)15)) / 16;
+}
+
 BinLayout bin_layout(const SketchDesc &d, size_t smem_budget) {
     BinLayout L{};
     L.S = d.log2w < 15 ? d.log2w : 15;
@@ -484,7 +531,8 @@ cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const 
                                uint64_t probe_base, uint64_t probe_cap, const BinLayout &L, uint16_t *bins,
                                uint32_t *cursor, uint32_t cap, int blocks, cudaStream_t s,
                                const VolumeDesc *vols, uint32_t nvol, uint32_t probe_per_vol,
-                               int threads, const RouteTarget *route) {
+                               int threads, const RouteTarget *route, uint4 *carry, int carry_in,
+                               int carry_out) {
     if (n == 0) return cudaSuccess;
     // bin arrays are read and written as 16-byte vectors: every bin must start
     // on a 16-byte boundary
@@ -514,6 +562,10 @@ cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const 
     a.route = route ? route->filter : RouteFilter{nullptr, 0, 0, 0};
     a.rprefix = route ? route->prefix : nullptr;
     a.rblocks = route ? route->blocks : nullptr;
+    a.carry = carry;
+    a.carry_in = carry && carry_in ? 1u : 0u;
+    a.carry_out = carry && carry_out ? 1u : 0u;
+    a.carry16 = carry_words16(L);
     a.vols = vols;
     a.nvol = vols ? nvol : 0;
     a.probe_per_vol = probe_per_vol;
@@ -525,7 +577,8 @@ cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const 
     bool vec = (reinterpret_cast<uintptr_t>(xyz) & 15u) == 0;
     uint64_t per_tile = (uint64_t)threads * 4;
     uint64_t need_blocks = (n + per_tile - 1) / per_tile;
-    if (need_blocks < (uint64_t)blocks) blocks = (int)need_blocks;
+    // a carry belongs to a block index: carrying launches always use every block
+    if (!a.carry_in && !a.carry_out && need_blocks < (uint64_t)blocks) blocks = (int)need_blocks;
     if (blocks < 1) blocks = 1;
     auto launch = [&](auto kern) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
@@ -553,6 +606,26 @@ cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const 
         HS_SCATTER_ROWS(kModePlain, 1024)
     }
 #undef HS_SCATTER_ROWS
+    return cudaGetLastError();
+}
+
+cudaError_t launch_carry_flush(const BinLayout &L, const uint4 *carry, uint32_t nblocks,
+                               uint16_t *bins, uint32_t *cursor, uint32_t cap, int32_t *C,
+                               cudaStream_t s) {
+    ScatterArgs a{};
+    a.S = L.S;
+    a.nbins = L.nbins;
+    a.slot = L.slot;
+    a.cap = cap;
+    a.log2_slot = 0;
+    while ((1u << a.log2_slot) < L.slot) ++a.log2_slot;
+    a.bins = bins;
+    a.cursor = cursor;
+    a.carry16 = carry_words16(L);
+    const uint64_t total = (uint64_t)nblocks * L.nbins;
+    uint64_t blocks = std::min<uint64_t>((total + 255) / 256, 8192);
+    k_carry_flush<<<(unsigned)std::max<uint64_t>(blocks, 1), 256, 0, s>>>(
+        carry, nblocks, a, reinterpret_cast<uint32_t *>(C));
     return cudaGetLastError();
 }
 
