@@ -6,8 +6,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/halosketch.h"
@@ -48,6 +50,7 @@ constexpr size_t kBinSmemBudget = 224 * 1024;
 constexpr uint64_t kBinBudgetBytes = 4ull << 30;   // global bins, at most
 constexpr double kBinnedMinUpdates = 1 << 20;      // smaller calls add directly
 constexpr uint64_t kMaxScanCells = 1ull << 40;      // largest full scan one top-k may run
+constexpr uint32_t kBatchViews = 8;                 // volumes whose top-k run concurrently
 
 struct EventPair {
     cudaEvent_t a, b;
@@ -1314,7 +1317,9 @@ struct hs_batch {
     VolumeDesc *d_vols = nullptr;
     VolumeDesc *h_vols = nullptr;       // pinned: read by the graph's copy node
     int threads = 1024;
-    hs_sketch *view = nullptr;          // top-k of one volume at a time
+    hs_sketch *view = nullptr;          // views[0]
+    std::vector<hs_sketch *> views;     // top-k of one volume each, concurrently, own streams
+    std::vector<cudaEvent_t> vdone;     // each view's stream has finished
     // directories of each volume's enumerated rows, kept across queries
     std::vector<uint32_t *> vdir_off;
     std::vector<DirRecord *> vdir_rec;
@@ -1325,6 +1330,7 @@ struct hs_batch {
     uint64_t g_n = 0;
     double g_rate = -1;
     cudaEvent_t done = nullptr;         // the last graph launch has finished with h_vols
+    cudaEvent_t fork = nullptr;         // the views' streams start after this
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     hs_stats stats;
 };
@@ -1462,29 +1468,35 @@ hs_status batch_create(const hs_params *params, uint32_t n_volumes, const double
     if (e == cudaSuccess) e = cudaMalloc(&b->d_vols, n_volumes * sizeof(VolumeDesc));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_vols, n_volumes * sizeof(VolumeDesc));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev_a);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev_b);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->C, 0, counters * 4, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->probe, 0xFF, (size_t)n_volumes * kBatchProbe * 8, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->cursor, 0, (size_t)b->bl.nbins * 4, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    if (e == cudaSuccess) {
+    const uint32_t nviews = std::min<uint32_t>(n_volumes, kBatchViews);
+    for (uint32_t t = 0; t < nviews && e == cudaSuccess; ++t) {
         hs_sketch *h = new (std::nothrow) hs_sketch();
-        if (!h) e = cudaErrorMemoryAllocation;
-        else {
-            h->p = p;
-            h->d = b->d;
-            h->is_view = true;
-            h->stream = b->stream;
-            h->device = b->device;
-            h->num_sms = b->num_sms;
-            h->probe_cap = kBatchProbe;
-            h->bl = BinLayout{};        // views never bin
-            std::memset(&h->stats, 0, sizeof(h->stats));
-            e = cudaMalloc(&h->flags, 4 * sizeof(uint32_t));
-            b->view = h;
+        if (!h) {
+            e = cudaErrorMemoryAllocation;
+            break;
         }
+        h->p = p;
+        h->d = b->d;
+        h->is_view = true;
+        h->device = b->device;
+        h->num_sms = b->num_sms;
+        h->probe_cap = kBatchProbe;
+        h->bl = BinLayout{};        // views never bin
+        std::memset(&h->stats, 0, sizeof(h->stats));
+        b->views.push_back(h);
+        b->vdone.push_back(nullptr);
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->vdone.back(), cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMalloc(&h->flags, 4 * sizeof(uint32_t));
     }
+    if (e == cudaSuccess) b->view = b->views[0];
     if (e != cudaSuccess) {
         hs_status code = e == cudaErrorMemoryAllocation ? HS_ERR_OOM : HS_ERR_CUDA;
         batch_destroy(b);
@@ -1498,10 +1510,14 @@ hs_status batch_destroy(hs_batch *b) {
     if (!b) return HS_OK;
     if (b->stream) cudaStreamSynchronize(b->stream);
     batch_drop_graph(b);
-    if (b->view) {
-        b->view->C = nullptr;
-        b->view->probe = nullptr;
-        sketch_destroy(b->view);
+    for (size_t t = 0; t < b->views.size(); ++t) {
+        hs_sketch *h = b->views[t];
+        h->C = nullptr;
+        h->probe = nullptr;
+        cudaStream_t vs = h->stream;
+        sketch_destroy(h);
+        if (vs) cudaStreamDestroy(vs);
+        if (b->vdone[t]) cudaEventDestroy(b->vdone[t]);
     }
     void *ps[] = {b->C, b->probe, b->cursor, b->d_vols, b->bins};
     for (void *q : ps)
@@ -1512,6 +1528,7 @@ hs_status batch_destroy(hs_batch *b) {
         if (q) cudaFree(q);
     if (b->h_vols) cudaFreeHost(b->h_vols);
     if (b->done) cudaEventDestroy(b->done);
+    if (b->fork) cudaEventDestroy(b->fork);
     if (b->ev_a) cudaEventDestroy(b->ev_a);
     if (b->ev_b) cudaEventDestroy(b->ev_b);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
@@ -1560,48 +1577,80 @@ hs_status batch_update(hs_batch *b, const float *xyz, const uint64_t *offsets, d
     return HS_OK;
 }
 
+// Top-k of volume v on view h (the view borrows the volume's counters, probe
+// and directories, and returns the directories it built).
+static hs_status batch_topk_one(hs_batch *b, hs_sketch *h, uint32_t v, uint32_t F, uint32_t k,
+                                uint64_t *keys, int32_t *est, uint32_t *n_out) {
+    for (uint32_t r = 0; r < F; ++r) {
+        h->dir_off[r] = b->vdir_off[v * F + r];
+        h->dir_rec[r] = b->vdir_rec[v * F + r];
+        h->dir_G[r] = b->vdir_G[v * F + r];
+        h->dir_lines_cap[r] = b->vdir_cap[v * F + r];
+    }
+    h->C = b->C + (size_t)v * b->d.rows * b->d.W;
+    h->probe = b->probe + (size_t)v * kBatchProbe;
+    h->d.G = b->G[v];
+    h->d.Gq = b->G[v];
+    h->d.F = 1;
+    h->d.inv_cell = b->inv[v];
+    h->n_cells = (uint64_t)b->G[v] * b->G[v] * b->G[v];
+    h->key_bits = 1;
+    while (h->key_bits < 64 && (1ull << h->key_bits) < h->n_cells) ++h->key_bits;
+    h->n_seen = b->n_seen[v];
+    h->probe_base = b->probe_base[v];
+    hs_status st = topk_extract(h, k, keys + (size_t)v * k, est + (size_t)v * k, &n_out[v]);
+    for (uint32_t r = 0; r < F; ++r) {
+        b->vdir_off[v * F + r] = h->dir_off[r];
+        b->vdir_rec[v * F + r] = h->dir_rec[r];
+        b->vdir_G[v * F + r] = h->dir_G[r];
+        b->vdir_cap[v * F + r] = h->dir_lines_cap[r];
+        h->dir_off[r] = nullptr;
+        h->dir_rec[r] = nullptr;
+        h->dir_G[r] = 0;
+        h->dir_lines_cap[r] = 0;
+    }
+    return st;
+}
+
 hs_status batch_topk(hs_batch *b, uint32_t k, uint64_t *keys, int32_t *est, uint32_t *n_out) {
     if (!b) return fail(HS_ERR_ARG, "batch is NULL");
     if (k == 0 || !keys || !est || !n_out) return fail(HS_ERR_ARG, "k == 0 or NULL output");
-    hs_sketch *h = b->view;
-    const uint32_t F = enum_rows(h);
+    const uint32_t F = enum_rows(b->view);
     if (b->vdir_off.size() != (size_t)b->nvol * F) {
         b->vdir_off.assign((size_t)b->nvol * F, nullptr);
         b->vdir_rec.assign((size_t)b->nvol * F, nullptr);
         b->vdir_G.assign((size_t)b->nvol * F, 0);
         b->vdir_cap.assign((size_t)b->nvol * F, 0);
     }
-    for (uint32_t v = 0; v < b->nvol; ++v) {
-        for (uint32_t r = 0; r < F; ++r) {     // lend volume v's directories to the view
-            h->dir_off[r] = b->vdir_off[v * F + r];
-            h->dir_rec[r] = b->vdir_rec[v * F + r];
-            h->dir_G[r] = b->vdir_G[v * F + r];
-            h->dir_lines_cap[r] = b->vdir_cap[v * F + r];
+    // the views start after the batch's pending work; the batch resumes after theirs
+    HS_CUDA(cudaEventRecord(b->fork, b->stream));
+    for (hs_sketch *h : b->views) HS_CUDA(cudaStreamWaitEvent(h->stream, b->fork, 0));
+    // each host thread drives one view over volumes taken from a shared counter
+    std::atomic<uint32_t> next{0};
+    std::vector<hs_status> status(b->views.size(), HS_OK);
+    std::vector<std::string> msg(b->views.size());
+    auto work = [&](size_t t) {
+        cudaSetDevice(b->device);
+        for (uint32_t v = next.fetch_add(1); v < b->nvol; v = next.fetch_add(1)) {
+            hs_status st = batch_topk_one(b, b->views[t], v, F, k, keys, est, n_out);
+            if (st != HS_OK) {
+                status[t] = st;
+                msg[t] = hs_last_error();
+                next.store(b->nvol);
+                break;
+            }
         }
-        h->C = b->C + (size_t)v * b->d.rows * b->d.W;
-        h->probe = b->probe + (size_t)v * kBatchProbe;
-        h->d.G = b->G[v];
-        h->d.Gq = b->G[v];
-        h->d.F = 1;
-        h->d.inv_cell = b->inv[v];
-        h->n_cells = (uint64_t)b->G[v] * b->G[v] * b->G[v];
-        h->key_bits = 1;
-        while (h->key_bits < 64 && (1ull << h->key_bits) < h->n_cells) ++h->key_bits;
-        h->n_seen = b->n_seen[v];
-        h->probe_base = b->probe_base[v];
-        hs_status st = topk_extract(h, k, keys + (size_t)v * k, est + (size_t)v * k, &n_out[v]);
-        for (uint32_t r = 0; r < F; ++r) {     // keep what the view built
-            b->vdir_off[v * F + r] = h->dir_off[r];
-            b->vdir_rec[v * F + r] = h->dir_rec[r];
-            b->vdir_G[v * F + r] = h->dir_G[r];
-            b->vdir_cap[v * F + r] = h->dir_lines_cap[r];
-            h->dir_off[r] = nullptr;
-            h->dir_rec[r] = nullptr;
-            h->dir_G[r] = 0;
-            h->dir_lines_cap[r] = 0;
-        }
-        if (st != HS_OK) return st;
+    };
+    std::vector<std::thread> pool;
+    for (size_t t = 1; t < b->views.size(); ++t) pool.emplace_back(work, t);
+    work(0);
+    for (auto &th : pool) th.join();
+    for (size_t t = 0; t < b->views.size(); ++t) {
+        HS_CUDA(cudaEventRecord(b->vdone[t], b->views[t]->stream));
+        HS_CUDA(cudaStreamWaitEvent(b->stream, b->vdone[t], 0));
     }
+    for (size_t t = 0; t < b->views.size(); ++t)
+        if (status[t] != HS_OK) return fail(status[t], "%s", msg[t].c_str());
     return HS_OK;
 }
 
@@ -1642,14 +1691,20 @@ hs_status batch_stats(hs_batch *b, hs_stats *out, int reset) {
     if (b->stats.update_launches && cudaEventElapsedTime(&ms, b->ev_a, b->ev_b) == cudaSuccess)
         b->stats.update_ms = ms;                     // the last update
     cudaGetLastError();
-    hs_stats vs{};
-    sketch_stats(b->view, &vs, reset);
     *out = b->stats;
-    out->kernel_launches += vs.kernel_launches;
-    out->search_launches = vs.search_launches;
-    out->search_ms = vs.search_ms;
-    out->topk_ms = vs.topk_ms;
-    out->topk_calls = vs.topk_calls;
+    out->search_launches = 0;
+    out->search_ms = 0;
+    out->topk_ms = 0;
+    out->topk_calls = 0;
+    for (hs_sketch *h : b->views) {
+        hs_stats vs{};
+        sketch_stats(h, &vs, reset);
+        out->kernel_launches += vs.kernel_launches;
+        out->search_launches += vs.search_launches;
+        out->search_ms += vs.search_ms;
+        out->topk_ms += vs.topk_ms;     // summed over concurrent views
+        out->topk_calls += vs.topk_calls;
+    }
     if (reset) std::memset(&b->stats, 0, sizeof(b->stats));
     return HS_OK;
 }
