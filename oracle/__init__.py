@@ -76,6 +76,8 @@ def _load():
                                             f64], None),
                 "or_topk_hier": ([vp, u32, u32, vp, vp, u32, u32, vp, u32, u32, u32, u32, vp, vp,
                                   ci], u64),
+                "or_topk_hier_unrouted": ([vp, u32, u32, vp, vp, u32, u32, vp, u32, u32, u32, u32,
+                                           vp, u32, vp, vp, ci], u64),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(lib, name)

@@ -647,3 +647,48 @@ uint64_t or_topk_hier(const int32_t *C2, uint32_t t2, uint32_t log2w2, const uin
     free(h);
     return cnt;
 }
+
+/*
+ * The hierarchical query of a learned sketch: the c*k best super-items of M1
+ * (which counts every kept particle), then the k best cells inside them that
+ * are not in routed coarse cells (routed: one byte per coarse cell of R^3
+ * cells), by M2's estimates.  The exact counts of routed cells are merged by
+ * the caller.
+ */
+uint64_t or_topk_hier_unrouted(const int32_t *C2, uint32_t t2, uint32_t log2w2, const uint64_t *seeds2,
+                               const int32_t *C1, uint32_t t1, uint32_t log2w1, const uint64_t *seeds1,
+                               uint32_t G, uint32_t F, uint32_t k, uint32_t c_mult,
+                               const uint8_t *routed, uint32_t R,
+                               uint64_t *keys_out, int32_t *est_out, int nthreads) {
+    uint32_t Gs = G / F, Gc = G / R;
+    uint64_t ns = (uint64_t)Gs * Gs * Gs;
+    uint64_t m = (uint64_t)c_mult * k;
+    if (m > ns) m = ns;
+    if (k == 0 || m == 0) return 0;
+    uint64_t *skeys = (uint64_t *)malloc(sizeof(uint64_t) * m);
+    int32_t *sest = (int32_t *)malloc(sizeof(int32_t) * m);
+    or_entry *h = (or_entry *)malloc(sizeof(or_entry) * k);
+    if (!skeys || !sest || !h) { free(skeys); free(sest); free(h); return 0; }
+    uint64_t got = or_topk_range(C1, t1, log2w1, seeds1, Gs, 0, ns, (uint32_t)m, skeys, sest, nthreads);
+    uint64_t cnt = 0;
+    for (uint64_t s = 0; s < got; ++s) {
+        uint32_t q[3];
+        or_key_decode(skeys[s], Gs, q);
+        for (uint32_t lz = 0; lz < F; ++lz)
+            for (uint32_t ly = 0; ly < F; ++ly)
+                for (uint32_t lx = 0; lx < F; ++lx) {
+                    uint32_t c[3] = {q[0] * F + lx, q[1] * F + ly, q[2] * F + lz};
+                    if (or_routed(routed, c, R, Gc)) continue;
+                    or_entry e;
+                    e.est = or_estimate_cell(C2, t2, log2w2, seeds2, c);
+                    e.key = or_key_of(c, G);
+                    or_offer(h, &cnt, k, e);
+                }
+    }
+    qsort(h, cnt, sizeof(or_entry), or_cmp_rank);
+    for (uint64_t i = 0; i < cnt; ++i) { keys_out[i] = h[i].key; est_out[i] = h[i].est; }
+    free(skeys);
+    free(sest);
+    free(h);
+    return cnt;
+}

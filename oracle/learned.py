@@ -161,3 +161,19 @@ def learned_topk(C, p, routed, R: int, table_keys, table_counts, k: int):
     alle = np.concatenate([est[:n], np.asarray(table_counts, np.int32)])
     order = sorted(range(allk.size), key=lambda i: (-int(alle[i]), int(allk[i])))[:k]
     return allk[order], alle[order]
+
+
+def learned_topk_hier(C2, p, C1, q, F: int, c_mult: int, routed, R: int, table_keys,
+                      table_counts, k: int, nthreads: int = 1):
+    """Hierarchical query of a learned sketch (super sketch C1 of every kept
+    particle, fine sketch C2 of the unrouted ones) merged with the exact counts."""
+    routed = np.ascontiguousarray(routed, np.uint8)
+    keys = np.empty(max(k, 1), np.uint64)
+    est = np.empty(max(k, 1), np.int32)
+    n = _load().or_topk_hier_unrouted(_ptr(C2), p.rows, p.log2_width, _ptr(p.seeds), _ptr(C1),
+                                      q.rows, q.log2_width, _ptr(q.seeds), p.G, F, k, c_mult,
+                                      _ptr(routed), R, _ptr(keys), _ptr(est), nthreads)
+    allk = np.concatenate([keys[:n], np.asarray(table_keys, np.uint64)])
+    alle = np.concatenate([est[:n], np.asarray(table_counts, np.int32)])
+    order = sorted(range(allk.size), key=lambda i: (-int(alle[i]), int(allk[i])))[:k]
+    return allk[order], alle[order]

@@ -72,3 +72,45 @@ def test_hier_with_every_super_item_is_the_full_search():
     hk, he = oracle.topk_hier(C2, p, C1, q, F, k, cm)
     fk, fe = oracle.topk_full(C2, p, k)
     assert np.array_equal(hk, fk) and np.array_equal(he, fe)
+
+
+def test_hier_unrouted_reductions_and_brute_force():
+    import oracle.learned as OL
+    x = box(4)
+    F = R = 4
+    p = oracle.Params(3, 11, 12.8, 0.1, 5, 0)
+    q = oracle.super_params(p, F, 9)
+    Gc = p.G // R
+    rng = np.random.default_rng(6)
+    routed = (rng.random(Gc ** 3) < 0.15).astype(np.uint8)
+    C2 = oracle.new_counters(p)
+    tk, tc = OL.learned_update(C2, p, x, routed, R)
+    C1 = oracle.sketch_update_super(oracle.new_counters(q), p, q, F, x)
+    k, cm = 60, 3
+    # nothing routed: the plain hierarchical query
+    none = np.zeros(Gc ** 3, np.uint8)
+    a = OL.learned_topk_hier(C2, p, C1, q, F, cm, none, R, [], [], k)
+    b = oracle.topk_hier(C2, p, C1, q, F, k, cm)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    # brute force with routing
+    sk = np.arange(q.n_cells, dtype=np.uint64)
+    se = oracle.estimate(C1, q, sk).astype(np.int64)
+    top_s = sk[np.lexsort((sk, -se))[:cm * k]].astype(np.int64)
+    sx, sy, sz = top_s % q.G, (top_s // q.G) % q.G, top_s // (q.G * q.G)
+    l = np.arange(F ** 3)
+    cx = (sx[:, None] * F + (l % F)[None, :]).ravel()
+    cy = (sy[:, None] * F + ((l // F) % F)[None, :]).ravel()
+    cz = (sz[:, None] * F + (l // (F * F))[None, :]).ravel()
+    keep = routed[cx // R + Gc * (cy // R + Gc * (cz // R))] == 0
+    fk = (cx + p.G * (cy + p.G * cz)).astype(np.uint64)[keep]
+    fe = oracle.estimate(C2, p, fk).astype(np.int64)
+    allk = np.concatenate([fk, tk])
+    alle = np.concatenate([fe, tc.astype(np.int64)])
+    o = np.lexsort((allk, -alle))[:k]
+    hk, he = OL.learned_topk_hier(C2, p, C1, q, F, cm, routed, R, tk, tc, k)
+    assert np.array_equal(hk, allk[o]) and np.array_equal(he, alle[o])
+    # c*k covering every super-item: the flat search over unrouted cells
+    cm_all = (q.n_cells + k - 1) // k
+    hk, he = OL.learned_topk_hier(C2, p, C1, q, F, cm_all, routed, R, tk, tc, k)
+    fk2, fe2 = OL.learned_topk(C2, p, routed, R, tk, tc, k)
+    assert np.array_equal(hk, fk2) and np.array_equal(he, fe2)
