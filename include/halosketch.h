@@ -378,16 +378,27 @@ hs_status learned_capacity(hs_learned *L, uint64_t *max_routed, uint64_t *table_
  * sample: bf16(float(log10(1 + count))) of the cell and its 26 periodic
  * neighbours, neighbour (dx, dy, dz) at index (dz+1)*9 + (dy+1)*3 + (dx+1) ->
  * MLP -> a coarse cell is routed iff its logit > 0 and it is among the B cells
- * of largest logit (ties: smaller coarse key first).  Device xyz.  Zeroes the
- * exact counters; call it before the updates (a fresh or reset sketch). */
+ * of largest logit (ties: smaller coarse key first).  xyz host or device (host
+ * memory goes through the sketch's staging buffers).  Zeroes the exact
+ * counters; call it before the updates (a fresh or reset sketch).
+ * learned_prepare(xyz, n) = learned_sample(xyz, n) + learned_route. */
 hs_status learned_prepare(hs_learned *L, const float *xyz, uint64_t n, hs_mlp *mlp,
                           uint64_t *n_routed);
+/* The sample pass in pieces (an out-of-core stream): each call adds the
+ * sampled particles of xyz[0, n) to the coarse counts, their indices following
+ * those of the previous calls since the last learned_route. */
+hs_status learned_sample(hs_learned *L, const float *xyz, uint64_t n);
+/* Features, MLP and routing from the coarse counts of the learned_sample
+ * calls so far (then the next learned_sample starts new counts). */
+hs_status learned_route(hs_learned *L, hs_mlp *mlp, uint64_t *n_routed);
 /* Each kept particle of a routed coarse cell increments its fine cell's exact
  * count; every other kept particle is added to the sketch (sketch_update). */
 hs_status learned_update(hs_learned *L, const float *xyz, uint64_t n, double sample_rate);
 /* The k best of: sketch estimates of cells that are not routed (full search,
- * Algorithm 1) and exact counts of the fine cells of routed coarse cells with
- * a particle; ranked by (value desc, key asc); HOST outputs. */
+ * Algorithm 1, or the hierarchical query when sketch_set_hierarchy was called
+ * on learned_sketch before learned_prepare) and exact counts of the fine cells
+ * of routed coarse cells with a particle; ranked by (value desc, key asc);
+ * HOST outputs. */
 hs_status learned_topk(hs_learned *L, uint32_t k, uint64_t *keys, int32_t *est, uint32_t *n_out);
 /* the non-zero exact counts (fine key, count), in block order; cap 0: count only */
 hs_status learned_table(hs_learned *L, uint64_t *keys, int32_t *counts, uint64_t cap,

@@ -783,7 +783,8 @@ static hs_status expand_pass(hs_sketch *h, const uint64_t *skeys, uint64_t ns, i
         cudaEventRecord(ev.a, h->stream);
         int launches = 0;
         HS_CUDA(launch_expand(h->C, h->d, skeys, ns, h->super->d.F, h->super->d.G, theta, mode,
-                              key_lo, key_hi, out, h->num_sms * 8, h->stream, &launches));
+                              key_lo, key_hi, out, h->num_sms * 8, h->stream, &launches,
+                              h->route.filter));
         cudaEventRecord(ev.b, h->stream);
         h->pending_search.push_back(ev);
         h->stats.search_launches += 1;
@@ -1806,6 +1807,7 @@ struct hs_learned {
     uint32_t coarse_key_bits = 1;
     uint64_t feature_seed = 0;
     double feature_rate = 1.0 / 64;
+    uint64_t n_sampled = 0;        // particles passed to learned_sample since the last route
     int32_t *coarse = nullptr;     // Gc^3 sample counts
     uint64_t *clist = nullptr;     // coarse cells with a sample
     uint64_t clist_cap = 0, n_list = 0, n_routed = 0;
@@ -2248,17 +2250,46 @@ hs_status learned_capacity(hs_learned *L, uint64_t *max_routed, uint64_t *table_
     return HS_OK;
 }
 
-hs_status learned_prepare(hs_learned *L, const float *xyz, uint64_t n, hs_mlp *mlp,
-                          uint64_t *n_routed) {
-    if (!L || !mlp || (n && !xyz)) return fail(HS_ERR_ARG, "NULL argument");
-    if (n && !is_device_ptr(xyz)) return fail(HS_ERR_ARG, "xyz must be device memory");
+hs_status learned_sample(hs_learned *L, const float *xyz, uint64_t n) {
+    if (!L || (n && !xyz)) return fail(HS_ERR_ARG, "NULL argument");
+    hs_sketch *sk = L->sk;
+    cudaStream_t s = sk->stream;
+    if (L->n_sampled == 0) HS_CUDA(cudaMemsetAsync(L->coarse, 0, L->ncoarse * 4, s));
+    if (n == 0) return HS_OK;
+    if (is_device_ptr(xyz)) {
+        HS_CUDA(launch_coarse_hist(xyz, n, L->n_sampled, sk->d, L->R, L->Gc, L->feature_seed,
+                                   L->feature_rate, L->coarse, s));
+        sk->stats.kernel_launches += 1;
+    } else {   // through the sketch's staging buffers, as sketch_update does
+        hs_status st = ensure_staging(sk);
+        if (st != HS_OK) return st;
+        int i = 0;
+        for (uint64_t off = 0; off < n; off += kStageParticles, ++i) {
+            const uint64_t cnt = std::min(kStageParticles, n - off);
+            const int b = i % kStageBuffers;
+            HS_CUDA(cudaStreamWaitEvent(sk->copy_stream, sk->ev_free[b], 0));
+            HS_CUDA(cudaMemcpyAsync(sk->stage[b], xyz + 3 * off, cnt * 12, cudaMemcpyHostToDevice,
+                                    sk->copy_stream));
+            HS_CUDA(cudaEventRecord(sk->ev_copied[b], sk->copy_stream));
+            HS_CUDA(cudaStreamWaitEvent(s, sk->ev_copied[b], 0));
+            HS_CUDA(launch_coarse_hist(sk->stage[b], cnt, L->n_sampled + off, sk->d, L->R, L->Gc,
+                                       L->feature_seed, L->feature_rate, L->coarse, s));
+            HS_CUDA(cudaEventRecord(sk->ev_free[b], s));
+            sk->stats.kernel_launches += 1;
+        }
+    }
+    L->n_sampled += n;
+    return HS_OK;
+}
+
+hs_status learned_route(hs_learned *L, hs_mlp *mlp, uint64_t *n_routed) {
+    if (!L || !mlp) return fail(HS_ERR_ARG, "NULL argument");
     hs_sketch *sk = L->sk;
     cudaStream_t s = sk->stream;
     int launches = 0;
-    HS_CUDA(cudaMemsetAsync(L->coarse, 0, L->ncoarse * 4, s));
+    if (L->n_sampled == 0) HS_CUDA(cudaMemsetAsync(L->coarse, 0, L->ncoarse * 4, s));
+    L->n_sampled = 0;                     // the next learned_sample starts a new histogram
     HS_CUDA(cudaMemsetAsync(L->ctr, 0, 4 * 8, s));
-    HS_CUDA(launch_coarse_hist(xyz, n, 0, sk->d, L->R, L->Gc, L->feature_seed, L->feature_rate,
-                               L->coarse, s));
     // list the coarse cells with a sample (size known only on the device: count first)
     HS_CUDA(launch_coarse_list(L->coarse, L->ncoarse, nullptr, &L->ctr[0], 0, s));
     unsigned long long nl = 0;
@@ -2286,7 +2317,7 @@ hs_status learned_prepare(hs_learned *L, const float *xyz, uint64_t n, hs_mlp *m
     unsigned long long npos = 0;
     HS_CUDA(cudaMemcpyAsync(&npos, &L->ctr[1], 8, cudaMemcpyDeviceToHost, s));
     HS_CUDA(cudaStreamSynchronize(s));
-    launches += 6;
+    launches += 5;
     // over budget: keep the max_blocks cells of largest logit (ties: smaller key)
     const int use_sel = npos > L->max_blocks;
     if (use_sel) {
@@ -2311,6 +2342,15 @@ hs_status learned_prepare(hs_learned *L, const float *xyz, uint64_t n, hs_mlp *m
     sk->routing = true;
     if (n_routed) *n_routed = nr;
     return HS_OK;
+}
+
+hs_status learned_prepare(hs_learned *L, const float *xyz, uint64_t n, hs_mlp *mlp,
+                          uint64_t *n_routed) {
+    if (!L || !mlp || (n && !xyz)) return fail(HS_ERR_ARG, "NULL argument");
+    L->n_sampled = 0;
+    hs_status st = learned_sample(L, xyz, n);
+    if (st != HS_OK) return st;
+    return learned_route(L, mlp, n_routed);
 }
 
 hs_status learned_update(hs_learned *L, const float *xyz, uint64_t n, double sample_rate) {

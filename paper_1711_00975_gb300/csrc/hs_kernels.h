@@ -131,7 +131,7 @@ cudaError_t launch_full_search(const int32_t *C, const SketchDesc &d, int32_t th
 cudaError_t launch_expand(const int32_t *C, const SketchDesc &d, const uint64_t *skeys, uint64_t ns,
                           uint32_t F, uint32_t Gs, int32_t theta, SearchMode mode, uint64_t key_lo,
                           uint64_t key_hi, SearchOut out, int max_blocks, cudaStream_t s,
-                          int *launches);
+                          int *launches, RouteFilter skip = RouteFilter{nullptr, 0, 0, 0});
 cudaError_t launch_point_query(const int32_t *C, const SketchDesc &d, const uint64_t *keys,
                                uint64_t m, int32_t *est, uint32_t *bad, cudaStream_t s);
 // distinct valid keys of probe[0..m) via an open-addressing set of 2^log2_slots slots

@@ -143,12 +143,14 @@ __global__ void __launch_bounds__(1024, 1)
 // Hierarchical query (Algorithm 3, CSHi), second layer: every cell of the
 // listed super-items (F x F x F blocks on a grid of Gs per axis) is estimated
 // from this sketch and kept when it passes theta and its key lies in
-// [key_lo, key_hi).  One thread per cell; total = ns * F^3 < 2^32.
+// [key_lo, key_hi) and it is not routed to exact counts.  One thread per cell;
+// total = ns * F^3 < 2^32.
 template <int T>
 __global__ void __launch_bounds__(256)
     k_expand(const int32_t *__restrict__ C, const SketchDesc d,
              const uint64_t *__restrict__ skeys, uint32_t total, uint32_t F, uint32_t Gs,
-             int32_t theta, uint32_t mode, uint64_t key_lo, uint64_t key_hi, SearchOut out) {
+             int32_t theta, uint32_t mode, uint64_t key_lo, uint64_t key_hi, SearchOut out,
+             RouteFilter skip) {
     const int lane = threadIdx.x & 31;
     const uint32_t F3 = F * F * F;
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(256)
             const uint32_t sy = (uint32_t)(rest % Gs), sz = (uint32_t)(rest / Gs);
             const uint32_t cx = sx * F + l % F, cy = sy * F + (l / F) % F, cz = sz * F + l / (F * F);
             key = key_of(cx, cy, cz, d.G);
-            if (key >= key_lo && key < key_hi) {
+            if (key >= key_lo && key < key_hi && !(skip.bits && routed_cell(skip, cx, cy, cz))) {
                 if (T == 5) {
                     int32_t ev[5];
 #pragma unroll
@@ -319,7 +321,7 @@ cudaError_t launch_full_search(const int32_t *C, const SketchDesc &d, int32_t th
 cudaError_t launch_expand(const int32_t *C, const SketchDesc &d, const uint64_t *skeys, uint64_t ns,
                           uint32_t F, uint32_t Gs, int32_t theta, SearchMode mode, uint64_t key_lo,
                           uint64_t key_hi, SearchOut out, int max_blocks, cudaStream_t s,
-                          int *launches) {
+                          int *launches, RouteFilter skip) {
     const uint64_t F3 = (uint64_t)F * F * F;
     const uint64_t per = ((1ull << 31) / F3);            // super-items per launch: < 2^31 cells
     for (uint64_t s0 = 0; s0 < ns; s0 += per) {
@@ -330,10 +332,10 @@ cudaError_t launch_expand(const int32_t *C, const SketchDesc &d, const uint64_t 
         if (blocks < 1) blocks = 1;
         if (d.rows == 5)
             k_expand<5><<<(unsigned)blocks, 256, 0, s>>>(C, d, skeys + s0, total, F, Gs, theta, mode,
-                                                        key_lo, key_hi, out);
+                                                        key_lo, key_hi, out, skip);
         else
             k_expand<0><<<(unsigned)blocks, 256, 0, s>>>(C, d, skeys + s0, total, F, Gs, theta, mode,
-                                                        key_lo, key_hi, out);
+                                                        key_lo, key_hi, out, skip);
         *launches += 1;
     }
     return cudaGetLastError();

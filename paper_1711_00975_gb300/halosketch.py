@@ -131,6 +131,8 @@ def lib():
                 "learned_capacity": [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)],
                 "learned_routed": [vp, vp, u64, ctypes.POINTER(u64)],
                 "learned_prepare": [vp, vp, u64, vp, ctypes.POINTER(u64)],
+                "learned_sample": [vp, vp, u64],
+                "learned_route": [vp, vp, ctypes.POINTER(u64)],
                 "learned_update": [vp, vp, u64, f64],
                 "learned_topk": [vp, u32, vp, vp, ctypes.POINTER(u32)],
                 "learned_table": [vp, vp, vp, u64, ctypes.POINTER(u64)],
@@ -651,6 +653,29 @@ class Learned:
         nr = ctypes.c_uint64()
         _check(lib().learned_prepare(self.h, _ptr(xyz), n, mlp.h, ctypes.byref(nr)), "learned_prepare")
         return nr.value
+
+    def sample(self, xyz, n: int | None = None):
+        if n is None:
+            n = (xyz.numel() if hasattr(xyz, "numel") else xyz.size) // 3
+        _check(lib().learned_sample(self.h, _ptr(xyz), n), "learned_sample")
+
+    def route(self, mlp: MLP) -> int:
+        nr = ctypes.c_uint64()
+        _check(lib().learned_route(self.h, mlp.h, ctypes.byref(nr)), "learned_route")
+        return nr.value
+
+    def set_hierarchy(self, super_factor: int, super_log2_width: int, c_mult: int = 2):
+        """Hierarchical query of the inner sketch; call before prepare/route."""
+        _check(lib().sketch_set_hierarchy(self.sketch_h, super_factor, super_log2_width, c_mult),
+               "sketch_set_hierarchy")
+
+    def super_counters(self) -> np.ndarray:
+        out = ctypes.c_void_p()
+        _check(lib().sketch_super(self.sketch_h, ctypes.byref(out)), "sketch_super")
+        info = sketch_info(out)
+        arr = np.empty((info.rows, info.width), np.int32)
+        sketch_counters(out, arr)
+        return arr
 
     def update(self, xyz, n: int | None = None, rate: float = 1.0):
         if n is None:

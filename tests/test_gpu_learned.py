@@ -291,3 +291,61 @@ def test_trained_router_beats_plain_sketch_at_no_more_memory(hs):
           f"({mem_learned} B, {L.max_routed} routed cells)")
     assert mem_learned <= mem_plain
     assert r_learned >= r_plain + 0.05
+
+
+def test_learned_sample_in_pieces_equals_one_pass(hs, learned_box):
+    x = learned_box
+    R, fseed, frate = 8, 5, 0.25
+    P = rand_params(12, scale=2.0)
+    mlp = hs.MLP()
+    mlp.set_params(P)
+    one = hs.Learned(3, 14, BOX["box"], 0.1, 21, 22, coarse_factor=R, table_log2=14,
+                     feature_seed=fseed, feature_rate=frate)
+    nr1 = one.prepare(_dev(x), mlp)
+    pieces = hs.Learned(3, 14, BOX["box"], 0.1, 21, 22, coarse_factor=R, table_log2=14,
+                        feature_seed=fseed, feature_rate=frate)
+    cut = len(x) // 3 + 5
+    pieces.sample(_dev(x[:cut]))
+    pieces.sample(np.ascontiguousarray(x[cut:]))            # host memory, staged
+    nr2 = pieces.route(mlp)
+    p = oracle.Params(3, 14, BOX["box"], 0.1, 21, 22)
+    counts = OL.coarse_hist(x, p, R, fseed, frate)
+    assert np.array_equal(one.coarse_counts(), counts)
+    assert np.array_equal(pieces.coarse_counts(), counts)
+    assert nr1 == nr2
+    assert np.array_equal(one.routed(), pieces.routed())
+    # a second round of sampling starts a new histogram
+    pieces.sample(_dev(x[:cut]))
+    pieces.route(mlp)
+    assert np.array_equal(pieces.coarse_counts(), OL.coarse_hist(x[:cut], p, R, fseed, frate))
+
+
+@pytest.mark.parametrize("rate", [1.0, 0.5])
+def test_learned_with_hierarchy_bitexact(hs, learned_box, rate):
+    x = learned_box
+    R = F = 8
+    cm, slog2w, k = 3, 11, 400
+    L = hs.Learned(5, 14, BOX["box"], 0.1, 31, 32, coarse_factor=R, table_log2=14,
+                   feature_seed=7, feature_rate=0.25)
+    L.set_hierarchy(F, slog2w, cm)
+    P = centre_router(3)
+    mlp = hs.MLP()
+    mlp.set_params(P)
+    L.prepare(np.ascontiguousarray(x), mlp)                  # host memory
+    cut = len(x) // 2 + 3
+    L.update(_dev(x[:cut]), rate=rate)
+    L.update(np.ascontiguousarray(x[cut:]), rate=rate)
+    p = oracle.Params(5, 14, BOX["box"], 0.1, 31, 32)
+    q = oracle.super_params(p, F, slog2w)
+    routed = oracle_routing(x, p, R, 7, 0.25, P, 14)[4]
+    assert np.array_equal(L.routed(), np.flatnonzero(routed).astype(np.uint64))
+    C2 = oracle.new_counters(p)
+    tk, tc = OL.learned_update(C2, p, x, routed, R, rate=rate)
+    C1 = oracle.sketch_update_super(oracle.new_counters(q), p, q, F, x, rate=rate)
+    assert np.array_equal(L.counters(), C2)
+    assert np.array_equal(L.super_counters(), C1)
+    gk, gc = L.table()
+    assert np.array_equal(gk, tk) and np.array_equal(gc, tc)
+    lk, le = L.topk(k)
+    wk, we = OL.learned_topk_hier(C2, p, C1, q, F, cm, routed, R, tk, tc, k, nthreads=NT)
+    assert np.array_equal(lk, wk) and np.array_equal(le, we)
