@@ -253,11 +253,10 @@ LEARNED = dict(coarse_factor=10, table_log2=20, sketch_log2_width=23, feature_se
                feature_rate=1.0 / 64, k_label=80, exact_log2_slots=31)
 
 
-def run_learned(dev, n: int, main_keys: np.ndarray, train_boxes: int, stream):
-    """The learned router on the 10^9-particle box: train on 100 Mpc/h boxes,
-    then top-k recall against exact counts for the plain sketch at 5 x 2^24
-    (320 MiB, the main leg's last top-k) and 5 x 2^23 (160 MiB), and for the
-    learned sketch (5 x 2^23 + exact blocks of a 2^20-slot table's bytes)."""
+def train_router(spec_of, n_boxes: int, k_label: int, stream):
+    """Train the router's MLP on n_boxes generated boxes (spec_of(i)): features
+    from the library's sample pass, labels from its exact counter; box i+1 is
+    generated on the host while box i is on the GPU."""
     import torch
 
     import synth
@@ -266,37 +265,34 @@ def run_learned(dev, n: int, main_keys: np.ndarray, train_boxes: int, stream):
 
     W = WORKLOAD
     C = LEARNED
-    k = W["k"]
-    out = {"workload": W["name"], "k": k, "train_boxes": train_boxes}
-    # ---- training set: features from the library's sample pass, labels from exact counts
     t0 = time.time()
     mlp = hs.MLP(seed=1, stream=stream)
-    tspec = synth.training_box(1000)
+    tspec = spec_of(0)
     bufs = [torch.empty((tspec.n, 3), dtype=torch.float32).pin_memory() for _ in range(2)]
     gen_s = [0.0]
 
     def gen(i, buf):
         t = time.time()
-        synth.HaloBox(synth.training_box(1000 + i)).generate_into_ptr(buf.data_ptr(), 0, tspec.n)
+        synth.HaloBox(spec_of(i)).generate_into_ptr(buf.data_ptr(), 0, tspec.n)
         gen_s[0] += time.time() - t
 
     Lt = hs.Learned(1, 16, tspec.box, W["cell"], coarse_factor=C["coarse_factor"], table_log2=12,
                     feature_seed=C["feature_seed"], feature_rate=C["feature_rate"], stream=stream)
     Et = hs.Exact(tspec.box, W["cell"], 24, stream)
-    dbox = torch.empty((tspec.n, 3), dtype=torch.float32, device=dev.device)
+    dbox = torch.empty((tspec.n, 3), dtype=torch.float32, device="cuda")
     feats, ys = [], []
     th = threading.Thread(target=gen, args=(0, bufs[0]))
     th.start()
-    for i in range(train_boxes):
+    for i in range(n_boxes):
         th.join()
         dbox.copy_(bufs[i % 2])
         torch.cuda.synchronize()
-        if i + 1 < train_boxes:
+        if i + 1 < n_boxes:
             th = threading.Thread(target=gen, args=(i + 1, bufs[(i + 1) % 2]))
             th.start()
         f, y, _ = router.box_examples(dbox, tspec.n, tspec.box, W["cell"], mlp,
                                       C["coarse_factor"], C["feature_seed"], C["feature_rate"],
-                                      C["k_label"], learned=Lt, exact=Et)
+                                      k_label, learned=Lt, exact=Et)
         feats.append(f)
         ys.append(y)
     Lt.close()
@@ -307,11 +303,30 @@ def run_learned(dev, n: int, main_keys: np.ndarray, train_boxes: int, stream):
     t1 = time.time()
     losses = router.train(mlp, F, Y, epochs=4, batch=65536, lr=1e-3, seed=0)
     torch.cuda.synchronize()
-    out["training"] = {"examples": int(Y.size), "positives": int(Y.sum()),
-                       "examples_s": t1 - t0, "generation_s": gen_s[0],
-                       "train_s": time.time() - t1, "epoch_losses": losses,
-                       "label": f"coarse cell holds a fine cell >= the {C['k_label']}-th largest "
-                                f"exact count of its box"}
+    info = {"boxes": n_boxes, "box": f"{tspec.n} particles / {tspec.box} Mpc/h / {tspec.n_halo} halos",
+            "examples": int(Y.size), "positives": int(Y.sum()), "examples_s": t1 - t0,
+            "generation_s": gen_s[0], "train_s": time.time() - t1, "epoch_losses": losses,
+            "label": f"coarse cell holds a fine cell >= the {k_label}-th largest exact count "
+                     f"of its box"}
+    return mlp, info
+
+
+def run_learned(dev, n: int, main_keys: np.ndarray, train_boxes: int, stream):
+    """The learned router on the 10^9-particle box: train on 100 Mpc/h boxes,
+    then top-k recall against exact counts for the plain sketch at 5 x 2^24
+    (320 MiB, the main leg's last top-k) and 5 x 2^23 (160 MiB), and for the
+    learned sketch (5 x 2^23 + exact blocks of a 2^20-slot table's bytes)."""
+    import torch
+
+    import synth
+    from paper_1711_00975_gb300 import halosketch as hs
+
+    W = WORKLOAD
+    C = LEARNED
+    k = W["k"]
+    out = {"workload": W["name"], "k": k, "train_boxes": train_boxes}
+    mlp, out["training"] = train_router(lambda i: synth.training_box(1000 + i), train_boxes,
+                                        C["k_label"], stream)
     # ---- evaluation on the main box
     E = hs.Exact(W["box"], W["cell"], C["exact_log2_slots"], stream)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -366,7 +381,8 @@ def run_learned(dev, n: int, main_keys: np.ndarray, train_boxes: int, stream):
 
 STREAM = dict(name="stream-2e10", box=2000.0, n_halo=64 * 10**6, cell=0.1, rows=5,
               log2_width=26, k=10**5, rate=0.1, chunk_bytes=10**9, pool_chunks=4, box_seed=4,
-              hash_seed=5, sample_seed=6, super_factor=10, super_log2_width=26, c_mult=2)
+              hash_seed=5, sample_seed=6, super_factor=10, super_log2_width=26, c_mult=2,
+              learned_log2_width=25, train_boxes=100, k_label=12)
 
 
 def measure_h2d(src, dst, stream, reps: int = 5) -> float:
@@ -384,7 +400,7 @@ def measure_h2d(src, dst, stream, reps: int = 5) -> float:
     return best
 
 
-def run_stream(n_total: int, hbm: float):
+def run_stream(n_total: int, hbm: float, learned_leg: bool = True):
     """Out-of-core stream: n_total particles of a 2000 Mpc/h box pass from pinned
     host chunks of 1 GB through the library's double-buffered staging (copy
     stream + compute stream) into a 5 x 2^26 sketch at sample rate 0.1, then
@@ -458,6 +474,7 @@ def run_stream(n_total: int, hbm: float):
     kernel_ms = st["update_ms"] + st1["update_ms"]
     kern_gbs = 12.0 * n_total / (kernel_ms * 1e-3) / 1e9 if kernel_ms > 0 else None
     sk.close()
+    learned = run_stream_learned(n_total, pool, C, stream, note) if learned_leg else None
     return {"workload": S["name"], "particles": n_total, "box_mpc_h": S["box"], "grid": round(S["box"] / S["cell"]),
             "rows": S["rows"], "width": 1 << S["log2_width"], "k": S["k"], "sample_rate": S["rate"],
             "chunk_bytes": C * 12, "chunks": nchunks, "pool_chunks": S["pool_chunks"],
@@ -475,7 +492,67 @@ def run_stream(n_total: int, hbm: float):
                       "c_mult": S["c_mult"], "super_topk_ms": st1["topk_ms"],
                       "update_ms_fine": st["update_ms"], "update_ms_super": st1["update_ms"]},
             "generation": {"seconds": gen_s, "particles_per_s": gen_rate,
-                           "note": "host generator rate; the stream cycles a pool of chunks"}}
+                           "note": "host generator rate; the stream cycles a pool of chunks"},
+            "learned": learned}
+
+
+def run_stream_learned(n_total: int, pool, C: int, stream, note):
+    """The same stream through the learned router: a 1/64 sample pass over the
+    whole stream, routing of the 2000^3 coarse cells, then the update pass into
+    a 5 x 2^25 sketch (half the plain one) with exact blocks for routed cells,
+    and the hierarchical top-10^5 merged with the exact counts.  The router is
+    trained on 100 Mpc/h boxes at this stream's density."""
+    import torch
+
+    import synth
+    from paper_1711_00975_gb300 import halosketch as hs
+
+    S = STREAM
+    L_ = LEARNED
+    spec_of = lambda i: synth.BoxSpec(n=n_total * 10**6 // 8 // 10**9, box=100.0,
+                                      n_halo=S["n_halo"] // 8000, seed=2000 + i)
+    mlp, training = train_router(spec_of, S["train_boxes"], S["k_label"], stream)
+    note(f"stream router trained ({training['examples']} examples)")
+    L = hs.Learned(S["rows"], S["learned_log2_width"], S["box"], S["cell"], S["hash_seed"],
+                   S["sample_seed"], coarse_factor=L_["coarse_factor"], table_log2=L_["table_log2"],
+                   feature_seed=L_["feature_seed"], feature_rate=L_["feature_rate"], stream=stream)
+    L.set_hierarchy(S["super_factor"], S["learned_log2_width"], S["c_mult"])
+    nchunks = (n_total + C - 1) // C
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    e[0].record(stream)
+    for c in range(nchunks):
+        L.sample(pool[c % len(pool)], min(C, n_total - c * C))
+    e[1].record(stream)
+    nr = L.route(mlp)
+    e[2].record(stream)
+    for c in range(nchunks):
+        L.update(pool[c % len(pool)], min(C, n_total - c * C), S["rate"])
+    hs.sketch_flush(L.sketch_h)
+    e[3].record(stream)
+    keys, est = L.topk(S["k"])
+    e[4].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    note("learned stream done")
+    ms = [e[i].elapsed_time(e[i + 1]) for i in range(4)]
+    total = max(sum(ms), wall * 1e3)
+    sketch_bytes = 2 * (S["rows"] * 4 << S["learned_log2_width"])
+    out = {"value": n_total / (total * 1e-3), "unit": "particles/s", "ms": total,
+           "sample_pass_ms": ms[0], "route_ms": ms[1], "update_pass_ms": ms[2], "topk_ms": ms[3],
+           "h2d_gbs_sample_pass": 12.0 * n_total / (ms[0] * 1e-3) / 1e9,
+           "h2d_gbs_update_pass": 12.0 * n_total / (ms[2] * 1e-3) / 1e9,
+           "routed_coarse_cells": int(nr), "max_routed": int(L.max_routed),
+           "memory_bytes": {"sketches": sketch_bytes, "exact_blocks": L.table_bytes,
+                            "plain_stream_sketches": 2 * (S["rows"] * 4 << S["log2_width"])},
+           "sketch": f"{S['rows']} x 2^{S['learned_log2_width']} + hierarchy {S['rows']} x "
+                     f"2^{S['learned_log2_width']}", "training": training,
+           "top_count": int(est[0]) if len(est) else 0,
+           "note": "no recall: exact counts of 2e10 particles (~1e10 cells) exceed device memory"}
+    L.close()
+    mlp.close()
+    return out
 
 
 def run_ours(args):
@@ -627,7 +704,7 @@ def run_ours(args):
         del dev
         torch.cuda.empty_cache()
         dev = None
-        stream_leg = run_stream(int(args.stream_n), hbm)
+        stream_leg = run_stream(int(args.stream_n), hbm, not args.no_learned)
 
     batched = None
     if not args.no_batch:
