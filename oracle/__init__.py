@@ -76,6 +76,9 @@ def _load():
                                             f64], None),
                 "or_topk_hier": ([vp, u32, u32, vp, vp, u32, u32, vp, u32, u32, u32, u32, vp, vp,
                                   ci], u64),
+                "or_mlp_forward_f32_mt": ([vp, vp, u64, vp, ci], None),
+                "or_learned_update_mt": ([vp, u32, u32, vp, vp, u64, u64, f32, u32, u64, f64, vp,
+                                          u32, vp, vp, u64, ci], u64),
                 "or_topk_hier_unrouted": ([vp, u32, u32, vp, vp, u32, u32, vp, u32, u32, u32, u32,
                                            vp, u32, vp, vp, ci], u64),
             }

@@ -692,3 +692,90 @@ uint64_t or_topk_hier_unrouted(const int32_t *C2, uint32_t t2, uint32_t log2w2, 
     free(h);
     return cnt;
 }
+
+/* ---- threaded forms of the learned-router oracle (for 10^9-particle checks) ----
+ * Same arithmetic as the single-threaded functions above: the forward pass is
+ * independent per sample, and the update's private counters and maps are
+ * integer sums, so the results are equal bit for bit. */
+
+void or_mlp_forward_f32_mt(const float *P, const uint16_t *feats, uint64_t m, float *logits,
+                           int nthreads) {
+#ifdef _OPENMP
+    int nt = nthreads < 1 ? 1 : nthreads;
+#pragma omp parallel num_threads(nt)
+    {
+        int me = omp_get_thread_num(), k = omp_get_num_threads();
+        uint64_t lo = m * (uint64_t)me / (uint64_t)k, hi = m * (uint64_t)(me + 1) / (uint64_t)k;
+        if (hi > lo) or_mlp_forward_f32(P, feats + lo * OR_MLP_IN, hi - lo, logits + lo);
+    }
+#else
+    (void)nthreads;
+    or_mlp_forward_f32(P, feats, m, logits);
+#endif
+}
+
+uint64_t or_learned_update_mt(int32_t *C, uint32_t t, uint32_t log2w, const uint64_t *seeds,
+                              const float *xyz, uint64_t n, uint64_t g0, float inv, uint32_t G,
+                              uint64_t sample_seed, double rate, const uint8_t *routed, uint32_t R,
+                              uint64_t *keys_out, uint32_t *cnt_out, uint64_t cap, int nthreads) {
+#ifdef _OPENMP
+    if (nthreads <= 1)
+#endif
+        return or_learned_update(C, t, log2w, seeds, xyz, n, g0, inv, G, sample_seed, rate, routed,
+                                 R, keys_out, cnt_out, cap);
+#ifdef _OPENMP
+    const uint64_t total = (uint64_t)t << log2w;
+    const uint32_t Gc = G / R;
+    const int nt = nthreads;
+    uint32_t **priv = (uint32_t **)calloc((size_t)nt, sizeof(uint32_t *));
+    or_map *maps = (or_map *)calloc((size_t)nt, sizeof(or_map));
+    int bad = !priv || !maps;
+    for (int k = 0; k < nt && !bad; ++k) {
+        priv[k] = (uint32_t *)calloc(total, sizeof(uint32_t));
+        bad = !priv[k] || or_map_grow(&maps[k]);
+    }
+    if (!bad) {
+#pragma omp parallel num_threads(nt)
+        {
+            int me = omp_get_thread_num();
+            uint64_t lo = n * (uint64_t)me / (uint64_t)nt, hi = n * (uint64_t)(me + 1) / (uint64_t)nt;
+            for (uint64_t i = lo; i < hi; ++i) {
+                if (!or_keep(g0 + i, sample_seed, rate)) continue;
+                uint32_t c[3];
+                if (!or_cell(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], inv, G, c)) continue;
+                if (or_routed(routed, c, R, Gc)) or_map_add(&maps[me], or_key_of(c, G), 1);
+                else or_add((int32_t *)priv[me], t, log2w, seeds, c);
+            }
+        }
+#pragma omp parallel for num_threads(nt) schedule(static)
+        for (int64_t j = 0; j < (int64_t)total; ++j) {
+            uint32_t acc = (uint32_t)C[j];
+            for (int k = 0; k < nt; ++k) acc += priv[k][j];
+            C[j] = (int32_t)acc;
+        }
+        for (int k = 1; k < nt; ++k)
+            for (uint64_t i = 0; i < maps[k].cap; ++i)
+                if (maps[k].keys[i]) or_map_add(&maps[0], maps[k].keys[i] - 1, maps[k].cnt[i]);
+    }
+    uint64_t D = 0;
+    if (!bad) {
+        D = maps[0].used;
+        if (D <= cap) {
+            or_entry *e = (or_entry *)malloc(sizeof(or_entry) * (D ? D : 1));
+            uint64_t q = 0;
+            for (uint64_t i = 0; i < maps[0].cap; ++i)
+                if (maps[0].keys[i]) { e[q].key = maps[0].keys[i] - 1; e[q].est = (int32_t)maps[0].cnt[i]; ++q; }
+            qsort(e, D, sizeof(or_entry), or_cmp_key);
+            for (uint64_t i = 0; i < D; ++i) { keys_out[i] = e[i].key; cnt_out[i] = (uint32_t)e[i].est; }
+            free(e);
+        }
+    }
+    for (int k = 0; k < nt; ++k) {
+        if (priv) free(priv[k]);
+        if (maps) { free(maps[k].keys); free(maps[k].cnt); }
+    }
+    free(priv);
+    free(maps);
+    return D;
+#endif
+}

@@ -72,12 +72,15 @@ def features(counts, Gc: int, keys) -> np.ndarray:
     return out
 
 
-def forward_f32(P, feats) -> np.ndarray:
+def forward_f32(P, feats, nthreads: int = 1) -> np.ndarray:
     P = np.ascontiguousarray(P, np.float32)
     feats = np.ascontiguousarray(feats, np.uint16)
     m = feats.size // MLP_IN
     out = np.empty(m, np.float32)
-    _load().or_mlp_forward_f32(_ptr(P), _ptr(feats), m, _ptr(out))
+    if nthreads > 1:
+        _load().or_mlp_forward_f32_mt(_ptr(P), _ptr(feats), m, _ptr(out), nthreads)
+    else:
+        _load().or_mlp_forward_f32(_ptr(P), _ptr(feats), m, _ptr(out))
     return out
 
 
@@ -128,8 +131,8 @@ def route_bytes(keys, logits, Gc: int, budget: int | None = None) -> np.ndarray:
     `budget` cells of largest logit (ties: smaller key first)."""
     keys = np.asarray(keys, np.int64)
     logits = np.asarray(logits, np.float32)
-    pos = [i for i in range(keys.size) if logits[i] > 0]
-    pos.sort(key=lambda i: (-float(logits[i]), int(keys[i])))
+    pos = np.flatnonzero(logits > 0)
+    pos = pos[np.lexsort((keys[pos], -logits[pos].astype(np.float64)))]
     if budget is not None:
         pos = pos[:budget]
     r = np.zeros(Gc ** 3, np.uint8)
@@ -137,16 +140,19 @@ def route_bytes(keys, logits, Gc: int, budget: int | None = None) -> np.ndarray:
     return r
 
 
-def learned_update(C, p, xyz, routed, R: int, g0: int = 0, rate: float = 1.0):
+def learned_update(C, p, xyz, routed, R: int, g0: int = 0, rate: float = 1.0,
+                   nthreads: int = 1, cap: int | None = None):
     """Routed particles -> exact table (sorted (keys, counts)); others -> C."""
     xyz = np.ascontiguousarray(xyz, np.float32)
     n = xyz.size // 3
-    keys = np.empty(n + 1, np.uint64)
-    cnt = np.empty(n + 1, np.uint32)
+    cap = n + 1 if cap is None else cap
+    keys = np.empty(cap, np.uint64)
+    cnt = np.empty(cap, np.uint32)
     routed = np.ascontiguousarray(routed, np.uint8)
-    D = _load().or_learned_update(_ptr(C), p.rows, p.log2_width, _ptr(p.seeds), _ptr(xyz), n, g0,
-                                  p.inv_cell, p.G, p.sample_seed, rate, _ptr(routed), R,
-                                  _ptr(keys), _ptr(cnt), n + 1)
+    D = _load().or_learned_update_mt(_ptr(C), p.rows, p.log2_width, _ptr(p.seeds), _ptr(xyz), n,
+                                     g0, p.inv_cell, p.G, p.sample_seed, rate, _ptr(routed), R,
+                                     _ptr(keys), _ptr(cnt), cap, nthreads)
+    assert D <= cap, "raise cap"
     return keys[:D].copy(), cnt[:D].astype(np.int32)
 
 

@@ -278,3 +278,19 @@ def test_topk_unrouted_brute_force():
     nk, ne = OL.learned_topk(C, p, np.zeros(Gc ** 3, np.uint8), R, np.zeros(0, np.uint64),
                              np.zeros(0, np.int32), 50)
     assert np.array_equal(fk, nk) and np.array_equal(fe, ne)
+
+
+def test_threaded_forms_equal_single_threaded():
+    P = rand_params(21)
+    F = rand_feats(22, 3001)
+    assert np.array_equal(OL.forward_f32(P, F).view(np.uint32),
+                          OL.forward_f32(P, F, nthreads=4).view(np.uint32))
+    x, p = small_case(5)
+    R = 8
+    Gc = p.G // R
+    routed = (np.random.default_rng(7).random(Gc ** 3) < 0.25).astype(np.uint8)
+    C1, C4 = oracle.new_counters(p), oracle.new_counters(p)
+    a = OL.learned_update(C1, p, x, routed, R, g0=3, rate=0.7)
+    b = OL.learned_update(C4, p, x, routed, R, g0=3, rate=0.7, nthreads=4)
+    assert np.array_equal(C1, C4)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
