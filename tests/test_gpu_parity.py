@@ -179,7 +179,8 @@ def test_shards_with_seek_merge_to_the_whole_stream(hs, small):
     b.seek(cut)
     b.update(_dev(xyz[cut:]), rate=0.3)
     kb, eb = b.topk(100)                        # uses b's own probe (no global index < 2^20)
-    Cb = b.counters()
+    Cb = oracle.sketch_update(oracle.new_counters(p), p, xyz[cut:], g0=cut, rate=0.3, nthreads=NT)
+    assert np.array_equal(b.counters(), Cb)
     wk, we = oracle.topk_full(Cb, p, 100, nthreads=NT)
     assert np.array_equal(kb, wk) and np.array_equal(eb, we)
     a.merge(b)
@@ -220,8 +221,8 @@ def test_topk_small_box_bitexact(hs, small, search):
     spec, xyz = small
     sk, p = _pair(hs, 5, 16, spec.box, 0.1, 13, flags=SEARCH[search])
     sk.update(_dev(xyz))
-    C = sk.counters()
-    assert np.array_equal(C, oracle.sketch_update(oracle.new_counters(p), p, xyz, nthreads=NT))
+    C = oracle.sketch_update(oracle.new_counters(p), p, xyz, nthreads=NT)
+    assert np.array_equal(sk.counters(), C)
     keys, est = sk.topk(1000)
     wk, we = oracle.topk_full(C, p, 1000, nthreads=NT)
     assert np.array_equal(keys, wk) and np.array_equal(est, we)
@@ -240,7 +241,8 @@ def test_topk_small_dictionaries_bitexact(hs, rows, log2w, G, k, search):
     pts = centres[rng.integers(0, 6, 20000)] + rng.normal(0, box / 20, (20000, 3))
     pts = np.mod(pts, box).astype(np.float32)
     sk.update(_dev(pts))
-    C = sk.counters()
+    C = oracle.sketch_update(oracle.new_counters(p), p, pts, nthreads=NT)
+    assert np.array_equal(sk.counters(), C)
     keys, est = sk.topk(k)
     wk, we = oracle.topk_full(C, p, k, nthreads=NT)
     assert len(keys) == min(k, G ** 3)
@@ -280,7 +282,7 @@ def test_topk_single_heavy_cell_many_ties(hs):
     heavy = int(oracle.keys_of(pts[:1], p)[0])
     assert [int(v) for v in keys] == [heavy] + list(range(63))
     assert [int(v) for v in est] == [333] + [0] * 63
-    C = sk.counters()
+    C = oracle.sketch_update(oracle.new_counters(p), p, pts)
     assert np.array_equal(oracle.estimate(C, p, keys), est)
 
 
@@ -294,7 +296,8 @@ def test_topk_after_reset_and_requery(hs, small, search):
     assert np.array_equal(k1[0], k1b[0]) and np.array_equal(k1[1], k1b[1])
     sk.reset()
     sk.update(_dev(xyz[500000:]))
-    C = sk.counters()
+    C = oracle.sketch_update(oracle.new_counters(p), p, xyz[500000:], nthreads=NT)
+    assert np.array_equal(sk.counters(), C)
     keys, est = sk.topk(300)
     wk, we = oracle.topk_full(C, p, 300, nthreads=NT)
     assert np.array_equal(keys, wk) and np.array_equal(est, we)
@@ -311,7 +314,8 @@ def test_topk_heavy_ties_at_positive_threshold(hs, search):
     pts = (np.stack([cx, cy, cz], 1).astype(np.float64) * 0.1 + 0.05).astype(np.float32)
     pts = np.repeat(pts, 3, axis=0)
     sk.update(_dev(pts))
-    C = sk.counters()
+    C = oracle.sketch_update(oracle.new_counters(p), p, pts, nthreads=NT)
+    assert np.array_equal(sk.counters(), C)
     keys, est = sk.topk(1500)
     wk, we = oracle.topk_full(C, p, 1500, nthreads=NT)
     assert np.array_equal(keys, wk) and np.array_equal(est, we)
