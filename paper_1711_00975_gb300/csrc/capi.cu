@@ -96,6 +96,7 @@ struct hs_sketch {
     unsigned long long *hist = nullptr;
     uint64_t *tmp_key = nullptr;
     int32_t *tmp_est = nullptr;
+    uint32_t *tmp_rank = nullptr;
     uint64_t *out_key = nullptr;
     int32_t *out_est = nullptr;
     uint64_t out_cap = 0;
@@ -210,7 +211,7 @@ void drain_timings(hs_sketch *h) {
 void free_topk_scratch(hs_sketch *h) {
     void *ps[] = {h->cand_key, h->cand_est, h->counters, h->bitmap,  h->slots,
                   h->distinct, h->distinct_est, h->sel, h->hist,  h->tmp_key, h->tmp_est,
-                  h->out_key, h->out_est};
+                  h->tmp_rank, h->out_key, h->out_est};
     for (void *p : ps)
         if (p) cudaFree(p);
     h->cand_key = nullptr;
@@ -224,6 +225,7 @@ void free_topk_scratch(hs_sketch *h) {
     h->hist = nullptr;
     h->tmp_key = nullptr;
     h->tmp_est = nullptr;
+    h->tmp_rank = nullptr;
     h->out_key = nullptr;
     h->out_est = nullptr;
     h->cap = 0;
@@ -249,6 +251,7 @@ hs_status ensure_topk_scratch(hs_sketch *h, uint64_t k) {
     HS_CUDA(cudaMalloc(&h->hist, 256 * sizeof(unsigned long long)));
     HS_CUDA(cudaMalloc(&h->tmp_key, h->out_cap * 8));
     HS_CUDA(cudaMalloc(&h->tmp_est, h->out_cap * 4));
+    HS_CUDA(cudaMalloc(&h->tmp_rank, h->out_cap * 4));
     HS_CUDA(cudaMalloc(&h->out_key, h->out_cap * 8));
     HS_CUDA(cudaMalloc(&h->out_est, h->out_cap * 4));
     return HS_OK;
@@ -498,14 +501,16 @@ hs_status search_pass_dir(hs_sketch *h, int32_t theta, SearchMode mode, int64_t 
     HS_CUDA(cudaMemcpyAsync(cnt, h->hot_cnt, F * sizeof(unsigned long long),
                             cudaMemcpyDeviceToHost, h->stream));
     HS_CUDA(cudaStreamSynchronize(h->stream));
-    // relative costs: one scanned cell ~ 1; one (cx, hot bucket) query ~ 20
-    // units per directory line it reads; building a directory ~ 60 units/line
+    // relative costs, from GB300 timings: one scanned cell ~ 1 (about 1e10
+    // cells/s); one (cx, hot bucket) query ~ 0.25 per directory slot it reads
+    // (about 4e10 queries/s); building a directory ~ 1 per line.  The query
+    // and build weights are kept about 4x above the measured ones.
     const double per_slot = (double)lines / (double)(1ull << h->dir_D);
     double cost_dir = 0, cost_scan = (double)G * G * G;
     for (uint32_t r = 0; r < F; ++r) {
         if (cnt[r] > h->hot_cap) return HS_OK;
-        cost_dir += 20.0 * (double)G * (double)cnt[r] * (2.0 + 2.0 * per_slot);
-        if (!h->dir_off[r] || h->dir_G[r] != h->d.G) cost_dir += 60.0 * (double)lines;
+        cost_dir += 1.0 * (double)G * (double)cnt[r] * (1.0 + per_slot);
+        if (!h->dir_off[r] || h->dir_G[r] != h->d.G) cost_dir += 4.0 * (double)lines;
     }
     const uint32_t force = h->p.flags & (HS_FLAG_SEARCH_SCAN | HS_FLAG_SEARCH_DIRECTORY);
     if (force == HS_FLAG_SEARCH_SCAN) return HS_OK;
@@ -609,7 +614,7 @@ hs_status finalize(hs_sketch *h, uint64_t m, uint64_t k) {
                                   h->num_sms * 4, h->stream, &launches));
     uint64_t n_take = all ? m : k;
     HS_CUDA(launch_take_sorted(h->cand_key, h->cand_est, m, h->sel, all, h->tmp_key, h->tmp_est,
-                               &h->counters[1], n_take, h->out_key, h->out_est, h->num_sms * 4,
+                               &h->counters[1], h->tmp_rank, n_take, h->out_key, h->out_est, h->num_sms * 4,
                                h->stream, &launches));
     h->stats.kernel_launches += launches;
     return HS_OK;
@@ -771,6 +776,27 @@ hs_status sketch_query(hs_sketch *h, const uint64_t *keys, uint64_t m, int32_t *
     return HS_OK;
 }
 
+// The k-th best estimate among the distinct cells of the first particles of
+// the stream (kept in the probe), or INT32_MIN when there are fewer than k.
+static hs_status probe_theta(hs_sketch *h, uint64_t kk, int32_t *theta) {
+    *theta = INT32_MIN;
+    const uint64_t m_probe = std::min<uint64_t>(h->n_seen - h->probe_base, h->probe_cap);
+    if (m_probe < kk) return HS_OK;
+    HS_CUDA(cudaMemsetAsync(h->counters, 0, 4 * sizeof(unsigned long long), h->stream));
+    HS_CUDA(cudaMemsetAsync(h->flags, 0, 4 * sizeof(uint32_t), h->stream));
+    HS_CUDA(launch_probe_distinct(h->probe, m_probe, h->slots, kProbeSlotsLog2, h->distinct,
+                                  &h->counters[2], &h->flags[1], h->stream));
+    unsigned long long nd = 0;
+    HS_CUDA(cudaMemcpyAsync(&nd, &h->counters[2], 8, cudaMemcpyDeviceToHost, h->stream));
+    HS_CUDA(cudaStreamSynchronize(h->stream));
+    h->stats.kernel_launches += 1;
+    if (nd < kk) return HS_OK;
+    HS_CUDA(launch_point_query(h->C, h->d, h->distinct, nd, h->distinct_est, &h->flags[0],
+                               h->stream));
+    h->stats.kernel_launches += 1;
+    return kth_estimate(h, h->distinct, h->distinct_est, nd, kk, theta);
+}
+
 // One pass of the hierarchy's second layer over the key window [key_lo, key_hi).
 static hs_status expand_pass(hs_sketch *h, const uint64_t *skeys, uint64_t ns, int32_t theta,
                              SearchMode mode, uint64_t key_lo, uint64_t key_hi,
@@ -822,7 +848,11 @@ static hs_status topk_hier(hs_sketch *h, uint64_t kk, uint64_t *keys, int32_t *e
     EventPair whole = take_events(h);
     cudaEventRecord(whole.a, h->stream);
     const uint64_t n_cells = h->n_cells;
+    // a first threshold from the probe; if the selected super-items hold fewer
+    // than k cells above it, the loop below starts again without one
     int32_t theta = INT32_MIN;
+    st = probe_theta(h, kk, &theta);
+    if (st != HS_OK) return st;
     uint64_t final_m = 0;
     for (int round = 0;; ++round) {
         if (round > 64) return fail(HS_ERR_STATE, "top-k threshold did not converge");
@@ -911,24 +941,8 @@ hs_status topk_extract(hs_sketch *h, uint32_t k, uint64_t *keys, int32_t *est, u
     // 1. a lower bound on the k-th estimate: the k-th best estimate among the
     //    distinct cells of the first particles of the stream
     int32_t theta = INT32_MIN;
-    uint64_t m_probe = std::min<uint64_t>(h->n_seen - h->probe_base, h->probe_cap);
-    if (m_probe >= kk) {
-        HS_CUDA(cudaMemsetAsync(h->counters, 0, 4 * sizeof(unsigned long long), h->stream));
-        HS_CUDA(cudaMemsetAsync(h->flags, 0, 4 * sizeof(uint32_t), h->stream));
-        HS_CUDA(launch_probe_distinct(h->probe, m_probe, h->slots, kProbeSlotsLog2, h->distinct,
-                                      &h->counters[2], &h->flags[1], h->stream));
-        unsigned long long nd = 0;
-        HS_CUDA(cudaMemcpyAsync(&nd, &h->counters[2], 8, cudaMemcpyDeviceToHost, h->stream));
-        HS_CUDA(cudaStreamSynchronize(h->stream));
-        h->stats.kernel_launches += 1;
-        if (nd >= kk) {
-            HS_CUDA(launch_point_query(h->C, h->d, h->distinct, nd, h->distinct_est, &h->flags[0],
-                                       h->stream));
-            h->stats.kernel_launches += 1;
-            st = kth_estimate(h, h->distinct, h->distinct_est, nd, kk, &theta);
-            if (st != HS_OK) return st;
-        }
-    }
+    st = probe_theta(h, kk, &theta);
+    if (st != HS_OK) return st;
 
     // 2. full search with that threshold; raise it on overflow
     uint64_t final_m = 0;
@@ -1797,6 +1811,7 @@ struct hs_exact {
     unsigned long long *hist = nullptr;
     uint64_t *tmp_key = nullptr, *out_key = nullptr;
     int32_t *tmp_est = nullptr, *out_est = nullptr;
+    uint32_t *tmp_rank = nullptr;
     uint64_t out_cap = 0;
 };
 
@@ -1999,7 +2014,7 @@ hs_status mlp_train_step(hs_mlp *m, const uint16_t *feats, const float *y, const
 hs_status exact_destroy(hs_exact *E) {
     if (!E) return HS_OK;
     void *ps[] = {E->keys, E->counts, E->overflow, E->ctr, E->sel, E->hist,
-                  E->tmp_key, E->tmp_est, E->out_key, E->out_est};
+                  E->tmp_key, E->tmp_est, E->out_key, E->out_est, E->tmp_rank};
     for (void *q : ps)
         if (q) cudaFree(q);
     delete E;
@@ -2108,14 +2123,16 @@ hs_status exact_topk(hs_exact *E, uint32_t k, uint64_t *keys, int32_t *counts, u
     *n_out = 0;
     if (kk == 0) return HS_OK;
     if (E->out_cap < kk) {
-        void *ps[] = {E->tmp_key, E->tmp_est, E->out_key, E->out_est};
+        void *ps[] = {E->tmp_key, E->tmp_est, E->out_key, E->out_est, E->tmp_rank};
         for (void *q : ps)
             if (q) cudaFree(q);
         E->tmp_key = E->out_key = nullptr;
         E->tmp_est = E->out_est = nullptr;
+        E->tmp_rank = nullptr;
         E->out_cap = 0;
         HS_CUDA(cudaMalloc(&E->tmp_key, kk * 8));
         HS_CUDA(cudaMalloc(&E->tmp_est, kk * 4));
+        HS_CUDA(cudaMalloc(&E->tmp_rank, kk * 4));
         HS_CUDA(cudaMalloc(&E->out_key, kk * 8));
         HS_CUDA(cudaMalloc(&E->out_est, kk * 4));
         E->out_cap = kk;
@@ -2127,7 +2144,7 @@ hs_status exact_topk(hs_exact *E, uint32_t k, uint64_t *keys, int32_t *counts, u
     HS_CUDA(launch_select_kth(tk, E->counts, E->slots, kk, E->key_bits, E->sel, E->hist,
                               E->num_sms * 4, E->stream, &launches));
     HS_CUDA(launch_take_sorted(tk, E->counts, E->slots, E->sel, 0, E->tmp_key, E->tmp_est,
-                               &E->ctr[1], kk, E->out_key, E->out_est, E->num_sms * 4, E->stream,
+                               &E->ctr[1], E->tmp_rank, kk, E->out_key, E->out_est, E->num_sms * 4, E->stream,
                                &launches));
     HS_CUDA(cudaMemcpyAsync(keys, E->out_key, kk * 8, cudaMemcpyDefault, E->stream));
     HS_CUDA(cudaMemcpyAsync(counts, E->out_est, kk * 4, cudaMemcpyDefault, E->stream));

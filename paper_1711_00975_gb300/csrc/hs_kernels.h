@@ -175,11 +175,12 @@ cudaError_t launch_select_kth(const uint64_t *key, const int32_t *est, uint64_t 
                               int blocks, cudaStream_t s, int *launches);
 // Entries ranked at or above the threshold, written in rank order to
 // out_key/out_est (exactly min(k, m) of them when the threshold came from
-// launch_select_kth with the same k).  tmp_* hold min(k, m) entries of scratch.
+// launch_select_kth with the same k).  tmp_* hold min(k, m) entries of scratch
+// (tmp_rank: min(k, m) uint32).
 cudaError_t launch_take_sorted(const uint64_t *key, const int32_t *est, uint64_t m,
                                const SelectState *state, int all, uint64_t *tmp_key,
-                               int32_t *tmp_est, unsigned long long *tmp_count,
-                               uint64_t n_take, uint64_t *out_key, int32_t *out_est,
-                               int blocks, cudaStream_t s, int *launches);
+                               int32_t *tmp_est, unsigned long long *tmp_count, uint32_t *tmp_rank,
+                               uint64_t n_take, uint64_t *out_key, int32_t *out_est, int blocks,
+                               cudaStream_t s, int *launches);
 
 }  // namespace hs

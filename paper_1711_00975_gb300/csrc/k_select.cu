@@ -97,9 +97,14 @@ __global__ void k_take(const uint64_t *__restrict__ key, const int32_t *__restri
     }
 }
 
-// out[rank(i)] = entry i, rank = number of entries ranked before it
-__global__ void k_rank_place(const uint64_t *__restrict__ tk, const int32_t *__restrict__ te,
-                             uint64_t n, uint64_t *__restrict__ ok, int32_t *__restrict__ oe) {
+// rank[i] += number of entries of slice blockIdx.y ranked before entry i: the
+// entries are split over blockIdx.x (one per thread) and the slices of the
+// comparison range over blockIdx.y, staged through shared memory.
+constexpr uint32_t kRankSlice = 8192;
+
+__global__ void __launch_bounds__(1024)
+    k_rank_count(const uint64_t *__restrict__ tk, const int32_t *__restrict__ te, uint64_t n,
+                 uint32_t *__restrict__ rank) {
     __shared__ uint32_t s_hi[1024];
     __shared__ uint64_t s_lo[1024];
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -109,25 +114,35 @@ __global__ void k_rank_place(const uint64_t *__restrict__ tk, const int32_t *__r
         hi = rank_hi(te[i]);
         lo = rank_lo(tk[i]);
     }
-    uint64_t before = 0;
-    for (uint64_t base = 0; base < n; base += blockDim.x) {
-        uint64_t j = base + threadIdx.x;
+    const uint64_t s0 = (uint64_t)blockIdx.y * kRankSlice;
+    const uint64_t s1 = s0 + kRankSlice < n ? s0 + kRankSlice : n;
+    uint32_t before = 0;
+    for (uint64_t base = s0; base < s1; base += blockDim.x) {
+        const uint64_t j = base + threadIdx.x;
         __syncthreads();
-        if (j < n) {
+        if (j < s1) {
             s_hi[threadIdx.x] = rank_hi(te[j]);
             s_lo[threadIdx.x] = rank_lo(tk[j]);
         }
         __syncthreads();
-        uint64_t lim = n - base < blockDim.x ? n - base : blockDim.x;
-        for (uint64_t q = 0; q < lim; ++q) {
-            uint32_t h2 = s_hi[q];
-            uint64_t l2 = s_lo[q];
+        const uint32_t lim = (uint32_t)(s1 - base < blockDim.x ? s1 - base : blockDim.x);
+        for (uint32_t q = 0; q < lim; ++q) {
+            const uint32_t h2 = s_hi[q];
+            const uint64_t l2 = s_lo[q];
             before += (h2 > hi) || (h2 == hi && l2 > lo);
         }
     }
+    if (i < n && before) atomicAdd(&rank[i], before);
+}
+
+// out[rank(i)] = entry i
+__global__ void k_rank_place(const uint64_t *__restrict__ tk, const int32_t *__restrict__ te,
+                             const uint32_t *__restrict__ rank, uint64_t n,
+                             uint64_t *__restrict__ ok, int32_t *__restrict__ oe) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
-        ok[before] = tk[i];
-        oe[before] = te[i];
+        ok[rank[i]] = tk[i];
+        oe[rank[i]] = te[i];
     }
 }
 
@@ -211,9 +226,9 @@ cudaError_t launch_select_kth(const uint64_t *key, const int32_t *est, uint64_t 
 
 cudaError_t launch_take_sorted(const uint64_t *key, const int32_t *est, uint64_t m,
                                const SelectState *state, int all, uint64_t *tmp_key,
-                               int32_t *tmp_est, unsigned long long *tmp_count, uint64_t n_take,
-                               uint64_t *out_key, int32_t *out_est, int blocks, cudaStream_t s,
-                               int *launches) {
+                               int32_t *tmp_est, unsigned long long *tmp_count, uint32_t *tmp_rank,
+                               uint64_t n_take, uint64_t *out_key, int32_t *out_est, int blocks,
+                               cudaStream_t s, int *launches) {
     cudaError_t e = cudaMemsetAsync(tmp_count, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     uint64_t b = (m + 255) / 256;
@@ -221,10 +236,17 @@ cudaError_t launch_take_sorted(const uint64_t *key, const int32_t *est, uint64_t
     if (b < 1) b = 1;
     k_take<<<(unsigned)b, 256, 0, s>>>(key, est, m, state, all, tmp_key, tmp_est, tmp_count,
                                        n_take);
-    uint64_t rb = (n_take + 1023) / 1024;
-    if (rb < 1) rb = 1;
-    k_rank_place<<<(unsigned)rb, 1024, 0, s>>>(tmp_key, tmp_est, n_take, out_key, out_est);
-    *launches += 2;
+    if (n_take == 0) {
+        *launches += 1;
+        return cudaGetLastError();
+    }
+    e = cudaMemsetAsync(tmp_rank, 0, n_take * 4, s);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((unsigned)((n_take + 1023) / 1024), (unsigned)((n_take + kRankSlice - 1) / kRankSlice));
+    k_rank_count<<<grid, 1024, 0, s>>>(tmp_key, tmp_est, n_take, tmp_rank);
+    k_rank_place<<<(unsigned)((n_take + 255) / 256), 256, 0, s>>>(tmp_key, tmp_est, tmp_rank, n_take,
+                                                                 out_key, out_est);
+    *launches += 3;
     return cudaGetLastError();
 }
 
