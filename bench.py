@@ -69,14 +69,15 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def scatter_traffic_per_particle():
-    """DRAM bytes per particle of the scatter kernel from the committed ncu
-    capture, or None when the kernel's source changed since the capture."""
+def scatter_capture():
+    """The committed ncu record of the scatter kernel (DRAM bytes and warp
+    instructions per particle), or None when the kernel's source changed since
+    the capture."""
     try:
         with open(TRAFFIC) as f:
             rec = json.load(f)["k_bin_scatter"]
         sha = hashlib.sha256(b"".join(open(p, "rb").read() for p in SCATTER_SOURCES)).hexdigest()
-        return rec["dram_bytes_per_particle"] if sha[:16] == rec["source_sha256_16"] else None
+        return rec if sha[:16] == rec["source_sha256_16"] else None
     except (OSError, KeyError, ValueError):
         return None
 
@@ -644,7 +645,8 @@ def run_ours(args):
     per_launch = n * args.steps / scatter_launches
     scatter_per_step = st["update_ms"] - st["flush_ms"]
     scatter_gbs = 12.0 * per_launch / (scatter_ms * 1e-3) / 1e9
-    bpp = scatter_traffic_per_particle()
+    cap = scatter_capture()
+    bpp = cap["dram_bytes_per_particle"] if cap else None
     roof = {"kernel": "k_bin_scatter", "bound": "hbm", "achieved": scatter_gbs, "peak": hbm,
             "unit": "GB/s", "frac": scatter_gbs / hbm,
             "traffic": bpp * per_launch if bpp is not None else None,
@@ -654,6 +656,17 @@ def run_ours(args):
             "note": "12 B of float32 xyz per particle read once; bins are not algorithmic"}
     if search_per_step > scatter_per_step / args.steps:
         roof["note"] += "; the full search took longer than the scatter this run"
+    if cap and cap.get("warp_inst_per_particle"):
+        # what binds the scatter: instruction issue, one warp instruction per
+        # clock per SM sub-partition at the clock sampled during the run
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = clocks.get("sm_mhz") or 2070.0
+        peak_issue = sms * 4 * mhz * 1e6
+        got = cap["warp_inst_per_particle"] * per_launch / (scatter_ms * 1e-3)
+        roof["issue"] = {"achieved": got, "peak": peak_issue, "unit": "warp instructions/s",
+                         "frac": got / peak_issue,
+                         "warp_inst_per_particle": cap["warp_inst_per_particle"],
+                         "note": "instruction count from the committed ncu capture"}
     search_roof = {"kernel": "k_dir_query", "cells_per_s": G ** 3 / (search_per_step * 1e-3)
                    if search_per_step > 0 else None, "ms_per_step": search_per_step}
 
