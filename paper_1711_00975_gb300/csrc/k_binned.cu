@@ -56,7 +56,9 @@ struct ScatterArgs {
     uint32_t probe_per_vol;   // batch: probe window of each volume
 };
 
-__device__ __noinline__ void direct_add(uint32_t *C, const ScatterArgs &a, uint32_t bin,
+// (inlined: a call in the staging path costs register moves around every call
+// site, which measured 20 % more instructions than the rare adds it guards)
+__device__ __forceinline__ void direct_add(uint32_t *C, const ScatterArgs &a, uint32_t bin,
                                         uint16_t code) {
     uint64_t idx = ((uint64_t)bin << a.S) | (uint64_t)(code >> 1);
     atomicAdd(&C[idx], (code & 1) ? 0xFFFFFFFFu : 1u);
@@ -77,7 +79,7 @@ __device__ __forceinline__ void bin_code(const RowSeed &sd, uint32_t cx, uint32_
     bin = (h >> (a.S + 1)) + r * a.bins_per_row;
 }
 
-__device__ __noinline__ void write_probe(uint64_t *probe, uint64_t g, bool valid, uint32_t cx,
+__device__ __forceinline__ void write_probe(uint64_t *probe, uint64_t g, bool valid, uint32_t cx,
                                          uint32_t cy, uint32_t cz, uint32_t G) {
     probe[g] = valid ? key_of(cx, cy, cz, G) : kInvalidKey;
 }
