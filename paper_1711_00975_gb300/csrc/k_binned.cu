@@ -87,7 +87,7 @@ __device__ __forceinline__ void write_probe(uint64_t *probe, uint64_t g, bool va
 // one exact count for a particle of a routed coarse cell: its block is the
 // cell's rank among the routed cells, its counter the fine cell's offset
 // (x fastest) inside the coarse cell
-__device__ __noinline__ void route_add(const ScatterArgs &a, uint32_t cx, uint32_t cy,
+__device__ __forceinline__ void route_add(const ScatterArgs &a, uint32_t cx, uint32_t cy,
                                        uint32_t cz) {
     const RouteFilter &f = a.route;
     const uint32_t qx = __umulhi(cx, f.rmagic), qy = __umulhi(cy, f.rmagic),
