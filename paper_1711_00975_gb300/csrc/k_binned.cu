@@ -17,6 +17,9 @@
 // Integer addition commutes, so the counters equal those of the direct update
 // bit for bit.  Whatever does not fit - a full shared-memory buffer or a full
 // global bin - is added directly with a global atomic, so nothing is dropped.
+#include <algorithm>
+#include <cmath>
+
 #include "hs_device.cuh"
 #include "hs_kernels.h"
 
@@ -51,6 +54,7 @@ struct ScatterArgs {
     uint32_t carry_in;        // start from the carried rings instead of empty ones
     uint32_t carry_out;       // leave the rings in the carry instead of flushing them
     uint32_t carry16;         // 16-byte words of one block's carry
+    uint32_t rounds;          // tiles staged between two flush phases
     const VolumeDesc *vols;   // batch: one entry per volume (nullptr for one sketch)
     uint32_t nvol;
     uint32_t probe_per_vol;   // batch: probe window of each volume
@@ -299,7 +303,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
     }
     const unsigned lt = (1u << lane) - 1u;
-    for (; tile < ntiles; tile += gridDim.x) {
+    for (; tile < ntiles;) {
+      // a.rounds tiles between flushes: at sample rate r about 1/r tiles stage
+      // as many codes as one tile at rate 1
+      for (uint32_t rnd = 0; rnd < a.rounds && tile < ntiles; ++rnd, tile += gridDim.x) {
         uint64_t cell[4];
         bool ok[4];
         const uint64_t g4 = tile * blockDim.x + threadIdx.x;     // this thread's group
@@ -370,7 +377,9 @@ __global__ void __launch_bounds__(THREADS, 1)
             __syncwarp();
             for (uint32_t i = lane; i < nq; i += 32)
                 stage_cell<T, BATCH>(q[i], d, a, s_fill, s_buf, s_due, C);
+            __syncwarp();
         }
+      }
         __syncthreads();
         // flush the due bins: warp w reads due words w, w + nwarps, ... (one
         // broadcast load each) and lane l flushes the bin of bit l.  All global
@@ -568,6 +577,8 @@ cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const 
     a.carry_in = carry && carry_in ? 1u : 0u;
     a.carry_out = carry && carry_out ? 1u : 0u;
     a.carry16 = carry_words16(L);
+    // at sample rate r a tile stages about r times the codes of a full tile
+    a.rounds = rate >= 1.0 ? 1u : (uint32_t)std::min(16.0, std::max(1.0, std::floor(1.0 / rate)));
     a.vols = vols;
     a.nvol = vols ? nvol : 0;
     a.probe_per_vol = probe_per_vol;
