@@ -76,6 +76,10 @@ def _load():
                                             f64], None),
                 "or_topk_hier": ([vp, u32, u32, vp, vp, u32, u32, vp, u32, u32, u32, u32, vp, vp,
                                   ci], u64),
+                "or_pack": ([vp, u64, f64, vp], None),
+                "or_cell_packed": ([u64, u32, vp], ci),
+                "or_sketch_update_packed": ([vp, u32, u32, vp, vp, u64, u64, u32, u32, u64, f64, ci],
+                                            ci),
                 "or_mlp_forward_f32_mt": ([vp, vp, u64, vp, ci], None),
                 "or_learned_update_mt": ([vp, u32, u32, vp, vp, u64, u64, f32, u32, u64, f64, vp,
                                           u32, vp, vp, u64, ci], u64),
@@ -231,6 +235,39 @@ def topk_full(C: np.ndarray, p: Params, k: int, nthreads: int = 1, key_lo: int =
     n = _load().or_topk_range(_ptr(C), p.rows, p.log2_width, _ptr(p.seeds), p.G, key_lo, key_hi, k,
                               _ptr(keys), _ptr(est), nthreads)
     return keys[:n].copy(), est[:n].copy()
+
+
+# ---- packed records (64 bits: three 21-bit coordinates, bit 63 = invalid) ----
+
+PACK_INVALID = np.uint64(1 << 63)
+
+
+def pack(xyz: np.ndarray, box: float) -> np.ndarray:
+    xyz = np.ascontiguousarray(xyz, np.float32)
+    out = np.empty(xyz.size // 3, np.uint64)
+    _load().or_pack(_ptr(xyz), out.size, box, _ptr(out))
+    return out
+
+
+def cell_packed(p: int, G: int):
+    c = np.zeros(3, np.uint32)
+    ok = _load().or_cell_packed(int(p), G, _ptr(c))
+    return (int(c[0]), int(c[1]), int(c[2])) if ok else None
+
+
+def sketch_update_packed(C: np.ndarray, p: Params, packed: np.ndarray, g0: int = 0,
+                         rate: float = 1.0, nthreads: int = 1, F: int = 1,
+                         fine: Params | None = None) -> np.ndarray:
+    """Add packed records; for a super-item sketch pass its params as p, the
+    fine mesh's params as fine and the super factor F."""
+    packed = np.ascontiguousarray(packed, np.uint64)
+    G = (fine or p).G
+    rc = _load().or_sketch_update_packed(_ptr(C), p.rows, p.log2_width, _ptr(p.seeds),
+                                         _ptr(packed), packed.size, g0, G, F, p.sample_seed, rate,
+                                         nthreads)
+    if rc:
+        raise MemoryError("oracle sketch_update_packed out of memory")
+    return C
 
 
 # ---- hierarchy (Algorithm 3, CSHi) ----

@@ -779,3 +779,84 @@ uint64_t or_learned_update_mt(int32_t *C, uint32_t t, uint32_t log2w, const uint
     return D;
 #endif
 }
+
+/* ======================================================================
+ * Packed particle records (the evaluation setup of Sec. 4: "every 64 bits
+ * contains 3 coordinates for one particle").  Reading: 21 bits per
+ * coordinate, q = floor(fl32(x * fl32(2^21 / L))) reduced periodically into
+ * [0, 2^21), x in bits 0-20, y in 21-41, z in 42-62; bit 63 marks a particle
+ * whose coordinates were not finite (skipped).  The cell of a record on a mesh
+ * of G cells per axis is (q * G) >> 21 per axis.
+ * ====================================================================== */
+
+#define OR_PACK_BITS 21
+#define OR_PACK_LEVELS (1u << OR_PACK_BITS)
+#define OR_PACK_INVALID (1ull << 63)
+
+void or_pack(const float *xyz, uint64_t n, double box, uint64_t *out) {
+    float inv = (float)((double)OR_PACK_LEVELS / box);
+    for (uint64_t i = 0; i < n; ++i) {
+        uint32_t q[3];
+        if (!or_cell(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], inv, OR_PACK_LEVELS, q)) {
+            out[i] = OR_PACK_INVALID;
+            continue;
+        }
+        out[i] = (uint64_t)q[0] | ((uint64_t)q[1] << OR_PACK_BITS) | ((uint64_t)q[2] << (2 * OR_PACK_BITS));
+    }
+}
+
+int or_cell_packed(uint64_t p, uint32_t G, uint32_t *c3) {
+    if (p & OR_PACK_INVALID) return 0;
+    const uint64_t m = OR_PACK_LEVELS - 1;
+    for (int a = 0; a < 3; ++a) c3[a] = (uint32_t)((((p >> (OR_PACK_BITS * a)) & m) * (uint64_t)G) >> OR_PACK_BITS);
+    return 1;
+}
+
+/* Processing a packed stream (Algorithm 1): cells of the records, divided by F
+ * per axis for a super-item sketch (F = 1: the cells themselves). */
+int or_sketch_update_packed(int32_t *C, uint32_t t, uint32_t log2w, const uint64_t *seeds,
+                            const uint64_t *packed, uint64_t n, uint64_t g0, uint32_t G, uint32_t F,
+                            uint64_t sample_seed, double rate, int nthreads) {
+    const uint64_t total = (uint64_t)t << log2w;
+    int nt = nthreads < 1 ? 1 : nthreads;
+#ifndef _OPENMP
+    nt = 1;
+#endif
+    uint32_t **priv = (uint32_t **)calloc((size_t)nt, sizeof(uint32_t *));
+    if (!priv) return 1;
+    for (int k = 0; k < nt; ++k) {
+        priv[k] = (uint32_t *)calloc(total, sizeof(uint32_t));
+        if (!priv[k]) {
+            for (int q = 0; q < k; ++q) free(priv[q]);
+            free(priv);
+            return 1;
+        }
+    }
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nt)
+#endif
+    {
+        int me = 0;
+#ifdef _OPENMP
+        me = omp_get_thread_num();
+#endif
+        uint64_t lo = n * (uint64_t)me / (uint64_t)nt, hi = n * (uint64_t)(me + 1) / (uint64_t)nt;
+        for (uint64_t i = lo; i < hi; ++i) {
+            if (!or_keep(g0 + i, sample_seed, rate)) continue;
+            uint32_t c[3];
+            if (!or_cell_packed(packed[i], G, c)) continue;
+            c[0] /= F;
+            c[1] /= F;
+            c[2] /= F;
+            or_add((int32_t *)priv[me], t, log2w, seeds, c);
+        }
+    }
+    for (uint64_t j = 0; j < total; ++j) {
+        uint32_t acc = (uint32_t)C[j];
+        for (int k = 0; k < nt; ++k) acc += priv[k][j];
+        C[j] = (int32_t)acc;
+    }
+    for (int k = 0; k < nt; ++k) free(priv[k]);
+    free(priv);
+    return 0;
+}
