@@ -158,6 +158,26 @@ hs_status sketch_set_hierarchy(hs_sketch *h, uint32_t super_factor, uint32_t sup
 /* M1 of a hierarchical sketch (NULL without a hierarchy); owned by h. */
 hs_status sketch_super(hs_sketch *h, hs_sketch **out);
 
+/*
+ * Packed particle records (the data layout of the paper's evaluation, Sec. 4:
+ * 64 bits hold the three coordinates of one particle).  Each coordinate is
+ * q = floor(fl32(x * fl32(2^21 / box))) reduced periodically into [0, 2^21)
+ * (the mesh reduction of Sec. 2.1 on a 2^21-cell mesh); x in bits 0-20, y in
+ * 21-41, z in 42-62; bit 63 set marks coordinates that were not finite (the
+ * record is skipped).  On the sketch's mesh of G cells per axis the record's
+ * cell is (q * G) >> 21 per axis, which can differ by one cell from the cell of
+ * the float32 position for particles within box / 2^21 of a cell boundary.
+ *
+ * pack_positions writes n records for n float32 xyz triples (device arrays;
+ * asynchronous on cuda_stream).  sketch_update_packed is sketch_update for
+ * records (8 bytes a particle instead of 12; host or device; plain and
+ * hierarchical sketches, HS_ERR_ARG for a learned sketch).
+ */
+hs_status pack_positions(const float *xyz, uint64_t n, double box, void *cuda_stream,
+                         uint64_t *records);
+hs_status sketch_update_packed(hs_sketch *h, const uint64_t *records, uint64_t n,
+                               double sample_rate);
+
 /* Block until every host -> device copy issued by sketch_update has completed,
  * so the host buffers may be reused, without waiting for the updates (an
  * out-of-core stream refills one pinned chunk while the GPU consumes another). */

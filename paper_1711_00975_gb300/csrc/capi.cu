@@ -364,7 +364,7 @@ hs_status ensure_query_scratch(hs_sketch *h, uint64_t m) {
 }
 
 hs_status launch_update_direct(hs_sketch *h, const float *xyz, uint64_t n, uint64_t g0,
-                               double rate);
+                               double rate, bool packed = false);
 
 // add every binned code to the counters (before anything reads them)
 hs_status drain(hs_sketch *h) {
@@ -425,8 +425,10 @@ hs_status ensure_bins(hs_sketch *h, uint64_t n, double rate) {
     return HS_OK;
 }
 
+// xyz: float32 positions, or packed 64-bit records when packed is set
 hs_status launch_update_timed(hs_sketch *h, const float *xyz, uint64_t n, uint64_t g0,
-                              double rate) {
+                              double rate, bool packed = false) {
+    const size_t esz = packed ? 8 : 12;
     if (want_binned(h, n, rate)) {
         hs_status st = ensure_bins(h, n, rate);
         if (st != HS_OK) return st;
@@ -443,12 +445,14 @@ hs_status launch_update_timed(hs_sketch *h, const float *xyz, uint64_t n, uint64
                 }
                 EventPair ev = take_events(h);
                 cudaEventRecord(ev.a, h->stream);
-                HS_CUDA(launch_bin_scatter(xyz + 3 * off, cnt, g0 + off, h->d, h->C, rate,
+                const float *src = reinterpret_cast<const float *>(
+                    reinterpret_cast<const char *>(xyz) + off * esz);
+                HS_CUDA(launch_bin_scatter(src, cnt, g0 + off, h->d, h->C, rate,
                                            h->p.sample_seed, h->probe, h->probe_base, kProbeCap,
                                            h->bl, h->bins, h->bin_cursor, h->bin_cap, h->num_sms,
                                            h->stream, nullptr, 0, 0, 1024,
                                            h->routing ? &h->route : nullptr, h->carry,
-                                           h->carry_valid ? 1 : 0, 1));
+                                           h->carry_valid ? 1 : 0, 1, packed ? 1 : 0));
                 h->carry_valid = true;
                 cudaEventRecord(ev.b, h->stream);
                 h->pending_update.push_back(ev);
@@ -459,16 +463,21 @@ hs_status launch_update_timed(hs_sketch *h, const float *xyz, uint64_t n, uint64
             return HS_OK;
         }
     }
-    return launch_update_direct(h, xyz, n, g0, rate);
+    return launch_update_direct(h, xyz, n, g0, rate, packed);
 }
 
 hs_status launch_update_direct(hs_sketch *h, const float *xyz, uint64_t n, uint64_t g0,
-                               double rate) {
+                               double rate, bool packed) {
     EventPair ev = take_events(h);
     cudaEventRecord(ev.a, h->stream);
-    HS_CUDA(launch_update(xyz, n, g0, h->d, h->C, rate, h->p.sample_seed, h->probe,
-                          h->probe_base, kProbeCap, 0,
-                          (uint32_t)h->d.W, h->num_sms * 8, h->stream));
+    if (packed)
+        HS_CUDA(launch_update_packed(reinterpret_cast<const uint64_t *>(xyz), n, g0, h->d, h->C,
+                                     rate, h->p.sample_seed, h->probe, h->probe_base, kProbeCap,
+                                     h->num_sms * 8, h->stream));
+    else
+        HS_CUDA(launch_update(xyz, n, g0, h->d, h->C, rate, h->p.sample_seed, h->probe,
+                              h->probe_base, kProbeCap, 0,
+                              (uint32_t)h->d.W, h->num_sms * 8, h->stream));
     cudaEventRecord(ev.b, h->stream);
     h->pending_update.push_back(ev);
     h->stats.update_launches += 1;
@@ -701,17 +710,24 @@ hs_status sketch_destroy(hs_sketch *h) {
     return HS_OK;
 }
 
-hs_status sketch_update(hs_sketch *h, const float *xyz, uint64_t n, double sample_rate) {
+// sketch_update and sketch_update_packed: src holds n float32 xyz triples or n
+// packed records, in host or device memory
+static hs_status update_common(hs_sketch *h, const void *src, uint64_t n, double sample_rate,
+                               bool packed) {
     if (!h) return fail(HS_ERR_ARG, "handle is NULL");
     if (!(sample_rate > 0.0 && sample_rate <= 1.0))
         return fail(HS_ERR_ARG, "sample_rate=%g outside (0, 1]", sample_rate);
     if (n == 0) return HS_OK;
-    if (!xyz) return fail(HS_ERR_ARG, "xyz is NULL");
+    if (!src) return fail(HS_ERR_ARG, "input is NULL");
     if (n > (~0ull - h->n_seen)) return fail(HS_ERR_ARG, "particle index overflow");
-    if (is_device_ptr(xyz)) {
-        hs_status st = launch_update_timed(h, xyz, n, h->n_seen, sample_rate);
+    if (packed && (h->routing || h->is_view))
+        return fail(HS_ERR_ARG, "packed records need a plain or hierarchical sketch");
+    const size_t esz = packed ? 8 : 12;
+    const float *xyz = static_cast<const float *>(src);
+    if (is_device_ptr(src)) {
+        hs_status st = launch_update_timed(h, xyz, n, h->n_seen, sample_rate, packed);
         if (st == HS_OK && h->super)
-            st = launch_update_timed(h->super, xyz, n, h->n_seen, sample_rate);
+            st = launch_update_timed(h->super, xyz, n, h->n_seen, sample_rate, packed);
         if (st != HS_OK) return st;
     } else {
         hs_status st = ensure_staging(h);
@@ -727,19 +743,39 @@ hs_status sketch_update(hs_sketch *h, const float *xyz, uint64_t n, double sampl
             uint64_t cnt = std::min(kStageParticles, n - off);
             int b = i % kStageBuffers;
             HS_CUDA(cudaStreamWaitEvent(h->copy_stream, h->ev_free[b], 0));
-            HS_CUDA(cudaMemcpyAsync(h->stage[b], xyz + 3 * off, cnt * 12, cudaMemcpyHostToDevice,
-                                    h->copy_stream));
+            HS_CUDA(cudaMemcpyAsync(h->stage[b], static_cast<const char *>(src) + off * esz,
+                                    cnt * esz, cudaMemcpyHostToDevice, h->copy_stream));
             HS_CUDA(cudaEventRecord(h->ev_copied[b], h->copy_stream));
             HS_CUDA(cudaStreamWaitEvent(h->stream, h->ev_copied[b], 0));
-            st = launch_update_timed(h, h->stage[b], cnt, h->n_seen + off, sample_rate);
+            st = launch_update_timed(h, h->stage[b], cnt, h->n_seen + off, sample_rate, packed);
             if (st == HS_OK && h->super)
-                st = launch_update_timed(h->super, h->stage[b], cnt, h->n_seen + off, sample_rate);
+                st = launch_update_timed(h->super, h->stage[b], cnt, h->n_seen + off, sample_rate,
+                                         packed);
             if (st != HS_OK) return st;
             HS_CUDA(cudaEventRecord(h->ev_free[b], h->stream));
         }
     }
     h->n_seen += n;
     if (h->super) h->super->n_seen += n;
+    return HS_OK;
+}
+
+hs_status sketch_update(hs_sketch *h, const float *xyz, uint64_t n, double sample_rate) {
+    return update_common(h, xyz, n, sample_rate, false);
+}
+
+hs_status sketch_update_packed(hs_sketch *h, const uint64_t *records, uint64_t n,
+                               double sample_rate) {
+    return update_common(h, records, n, sample_rate, true);
+}
+
+hs_status pack_positions(const float *xyz, uint64_t n, double box, void *cuda_stream,
+                         uint64_t *records) {
+    if (n && (!xyz || !records)) return fail(HS_ERR_ARG, "NULL argument");
+    if (!(box > 0)) return fail(HS_ERR_ARG, "box must be positive");
+    if (n && (!is_device_ptr(xyz) || !is_device_ptr(records)))
+        return fail(HS_ERR_ARG, "xyz and records must be device memory");
+    HS_CUDA(launch_pack(xyz, n, box, records, (cudaStream_t)cuda_stream));
     return HS_OK;
 }
 

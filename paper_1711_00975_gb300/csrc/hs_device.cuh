@@ -133,6 +133,33 @@ __device__ __forceinline__ bool particle_cell(const SketchDesc &d, float x, floa
     return valid;
 }
 
+// ---- packed particle records: 64 bits, three 21-bit coordinates ----
+// q = floor(fl32(x * fl32(2^21 / L))) reduced into [0, 2^21), x in bits 0-20,
+// y in 21-41, z in 42-62; bit 63 marks coordinates that were not finite.  The
+// cell on a mesh of G cells per axis is (q * G) >> 21.
+constexpr uint32_t kPackBits = 21;
+constexpr uint64_t kPackMask = (1ull << kPackBits) - 1;
+constexpr uint64_t kPackInvalid = 1ull << 63;
+
+__device__ __forceinline__ uint32_t packed_axis(uint64_t p, uint32_t a, uint32_t G) {
+    return (uint32_t)((((p >> (kPackBits * a)) & kPackMask) * (uint64_t)G) >> kPackBits);
+}
+
+// Cell of a packed record on the quantisation mesh; for a super-item sketch
+// the F x F x F block holding it.
+__device__ __forceinline__ bool packed_cell(const SketchDesc &d, uint64_t p, uint32_t &cx,
+                                            uint32_t &cy, uint32_t &cz) {
+    cx = packed_axis(p, 0, d.Gq);
+    cy = packed_axis(p, 1, d.Gq);
+    cz = packed_axis(p, 2, d.Gq);
+    if (d.F > 1) {
+        cx = __umulhi(cx, d.fmagic);
+        cy = __umulhi(cy, d.fmagic);
+        cz = __umulhi(cz, d.fmagic);
+    }
+    return !(p & kPackInvalid);
+}
+
 __device__ __forceinline__ uint64_t key_of(uint32_t cx, uint32_t cy, uint32_t cz, uint32_t G) {
     return (uint64_t)cx + (uint64_t)G * ((uint64_t)cy + (uint64_t)G * (uint64_t)cz);
 }

@@ -41,6 +41,8 @@ struct RouteTarget {
     const uint32_t *prefix;   // exclusive prefix count of routed cells per bitmap word
     int32_t *blocks;
 };
+// xyz: float32 positions, or 64-bit packed records when packed != 0 (plain and
+// super-item sketches only)
 cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const SketchDesc &d,
                                int32_t *C, double rate, uint64_t sample_seed, uint64_t *probe,
                                uint64_t probe_base, uint64_t probe_cap, const BinLayout &L,
@@ -48,7 +50,7 @@ cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const 
                                cudaStream_t s, const VolumeDesc *vols = nullptr, uint32_t nvol = 0,
                                uint32_t probe_per_vol = 0, int threads = 1024,
                                const RouteTarget *route = nullptr, uint4 *carry = nullptr,
-                               int carry_in = 0, int carry_out = 0);
+                               int carry_in = 0, int carry_out = 0, int packed = 0);
 // 16-byte words of one scatter block's carried rings (fill words + rings)
 uint32_t carry_words16(const BinLayout &L);
 // move the carried rings of nblocks scatter blocks into the global bins
@@ -99,6 +101,11 @@ cudaError_t launch_exact_query(const unsigned long long *tkeys, const int32_t *t
                                cudaStream_t s);
 
 // dst[i] += src[i] (int32 wrap-around), the merge of two sketches
+cudaError_t launch_update_packed(const uint64_t *rec, uint64_t n, uint64_t g0,
+                                 const SketchDesc &d, int32_t *C, double rate,
+                                 uint64_t sample_seed, uint64_t *probe, uint64_t probe_base,
+                                 uint64_t probe_cap, int max_blocks, cudaStream_t s);
+cudaError_t launch_pack(const float *xyz, uint64_t n, double box, uint64_t *out, cudaStream_t s);
 cudaError_t launch_add_counters(int32_t *dst, const int32_t *src, uint64_t n, cudaStream_t s);
 cudaError_t launch_red_rate(uint32_t *table, uint64_t n_counters, uint64_t ops_per_thread,
                             int blocks, cudaStream_t s);

@@ -106,6 +106,8 @@ __device__ __forceinline__ void route_add(const ScatterArgs &a, uint32_t cx, uin
 // Scatter variants: one plain sketch, a batch of volumes, a learned sketch that
 // routes some coarse cells to exact counters, a super-item sketch (Algorithm 3).
 constexpr int kModePlain = 0, kModeBatch = 1, kModeRoute = 2, kModeSuper = 3;
+// the same for packed 64-bit particle records instead of float32 xyz
+constexpr int kModePlainPacked = 4, kModeSuperPacked = 5;
 
 // Mesh reduction, sampling and probe entry of one particle; true when it is
 // kept, with its cell packed as cx | cy << 21 | cz << 42 (G <= 2^21).
@@ -132,6 +134,24 @@ __device__ __forceinline__ bool prep_particle(float x, float y, float z, uint64_
         route_add(a, cx, cy, cz);
         return false;
     }
+    return keep && valid;
+}
+
+// prep_particle for a packed record
+template <int MODE>
+__device__ __forceinline__ bool prep_record(uint64_t p, uint64_t g, const SketchDesc &d,
+                                            const ScatterArgs &a, uint64_t &cell) {
+    bool keep = a.keep_all || splitmix64_at(a.sample_seed, g) < a.thr;
+    uint32_t cx = packed_axis(p, 0, d.Gq), cy = packed_axis(p, 1, d.Gq), cz = packed_axis(p, 2, d.Gq);
+    const bool valid = !(p & kPackInvalid);
+    if (MODE == kModeSuperPacked) {
+        cx = __umulhi(cx, d.fmagic);
+        cy = __umulhi(cy, d.fmagic);
+        cz = __umulhi(cz, d.fmagic);
+    }
+    if (g - a.probe_base < a.probe_end - a.probe_base)
+        write_probe(a.probe, g - a.probe_base, valid, cx, cy, cz, d.G);
+    cell = (uint64_t)cx | ((uint64_t)cy << 21) | ((uint64_t)cz << 42);
     return keep && valid;
 }
 
@@ -262,6 +282,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     k_bin_scatter(const float *__restrict__ xyz, const SketchDesc d, const ScatterArgs a,
                   uint32_t *__restrict__ C) {
     constexpr bool BATCH = MODE == kModeBatch;
+    constexpr bool PACKED = MODE == kModePlainPacked || MODE == kModeSuperPacked;
+    // PACKED: xyz holds 64-bit records, two per 16-byte vector
+    const uint64_t *rec = reinterpret_cast<const uint64_t *>(xyz);
+    const uint4 *r4 = reinterpret_cast<const uint4 *>(xyz);
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t *s_fill = reinterpret_cast<uint32_t *>(smem);
     const uint32_t fill_bytes = (a.nbins * 4 + 15) & ~15u;
@@ -294,12 +318,18 @@ __global__ void __launch_bounds__(THREADS, 1)
     const float4 *p4 = reinterpret_cast<const float4 *>(xyz);
     float4 nu = make_float4(0, 0, 0, 0), nv = nu, nw = nu;
     uint64_t tile = blockIdx.x;
+    uint4 na = make_uint4(0, 0, 0, 0), nb = na;
     if (VEC && tile < ntiles) {
         uint64_t g4 = tile * blockDim.x + threadIdx.x;
         if (g4 < full_groups) {
-            nu = __ldcs(p4 + 3 * g4);
-            nv = __ldcs(p4 + 3 * g4 + 1);
-            nw = __ldcs(p4 + 3 * g4 + 2);
+            if (PACKED) {
+                na = __ldcs(r4 + 2 * g4);
+                nb = __ldcs(r4 + 2 * g4 + 1);
+            } else {
+                nu = __ldcs(p4 + 3 * g4);
+                nv = __ldcs(p4 + 3 * g4 + 1);
+                nw = __ldcs(p4 + 3 * g4 + 2);
+            }
         }
     }
     const unsigned lt = (1u << lane) - 1u;
@@ -310,7 +340,37 @@ __global__ void __launch_bounds__(THREADS, 1)
         uint64_t cell[4];
         bool ok[4];
         const uint64_t g4 = tile * blockDim.x + threadIdx.x;     // this thread's group
-        if (VEC) {
+        if (PACKED) {
+            if (VEC) {
+                const uint4 ua = na, ub = nb;
+                const uint64_t gn = (tile + gridDim.x) * blockDim.x + threadIdx.x;
+                if (tile + gridDim.x < ntiles && gn < full_groups) {
+                    na = __ldcs(r4 + 2 * gn);
+                    nb = __ldcs(r4 + 2 * gn + 1);
+                }
+                if (g4 < full_groups) {
+                    const uint64_t g = a.g0 + 4 * g4;
+                    ok[0] = prep_record<MODE>(ua.x | ((uint64_t)ua.y << 32), g, d, a, cell[0]);
+                    ok[1] = prep_record<MODE>(ua.z | ((uint64_t)ua.w << 32), g + 1, d, a, cell[1]);
+                    ok[2] = prep_record<MODE>(ub.x | ((uint64_t)ub.y << 32), g + 2, d, a, cell[2]);
+                    ok[3] = prep_record<MODE>(ub.z | ((uint64_t)ub.w << 32), g + 3, d, a, cell[3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const uint64_t i = 4 * g4 + j;
+                        ok[j] = i < a.n && prep_record<MODE>(__ldcs(reinterpret_cast<const unsigned long long *>(rec) + i),
+                                                             a.g0 + i, d, a, cell[j]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint64_t i = 4 * g4 + j;
+                    ok[j] = i < a.n && prep_record<MODE>(__ldcs(reinterpret_cast<const unsigned long long *>(rec) + i),
+                                                         a.g0 + i, d, a, cell[j]);
+                }
+            }
+        } else if (VEC) {
             float4 u = nu, v = nv, w = nw;
             const uint64_t gn = (tile + gridDim.x) * blockDim.x + threadIdx.x;
             if (tile + gridDim.x < ntiles && gn < full_groups) {
@@ -543,7 +603,7 @@ cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const 
                                uint32_t *cursor, uint32_t cap, int blocks, cudaStream_t s,
                                const VolumeDesc *vols, uint32_t nvol, uint32_t probe_per_vol,
                                int threads, const RouteTarget *route, uint4 *carry, int carry_in,
-                               int carry_out) {
+                               int carry_out, int packed) {
     if (n == 0) return cudaSuccess;
     // bin arrays are read and written as 16-byte vectors: every bin must start
     // on a 16-byte boundary
@@ -587,6 +647,7 @@ cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const 
     // only batches are tuned over the block size
     if (threads != 512 || !vols || L.nbins > (uint32_t)kMaxFlushPerThread * 512)
         threads = kScatterThreads;
+    if (packed && (vols || route)) return cudaErrorInvalidValue;   // float input only there
     bool vec = (reinterpret_cast<uintptr_t>(xyz) & 15u) == 0;
     uint64_t per_tile = (uint64_t)threads * 4;
     uint64_t need_blocks = (n + per_tile - 1) / per_tile;
@@ -613,6 +674,12 @@ cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const 
         }
     } else if (route) {
         HS_SCATTER_ROWS(kModeRoute, 1024)
+    } else if (packed) {
+        if (d.F > 1) {
+            HS_SCATTER_ROWS(kModeSuperPacked, 1024)
+        } else {
+            HS_SCATTER_ROWS(kModePlainPacked, 1024)
+        }
     } else if (d.F > 1) {
         HS_SCATTER_ROWS(kModeSuper, 1024)
     } else {

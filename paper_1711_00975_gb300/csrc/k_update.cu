@@ -9,6 +9,8 @@
 // coalesced loads (three float4 = four xyz triples) marked evict-first, and the
 // counter updates are fire-and-forget reductions (RED) that resolve in L2.
 // Counters are uint32 so the wrap-around of int32 two's complement is defined.
+#include <algorithm>
+
 #include "hs_device.cuh"
 #include "hs_kernels.h"
 
@@ -87,6 +89,53 @@ __global__ void __launch_bounds__(256) k_update_scalar(const float *__restrict__
                         a.g0 + i, d, a, C);
 }
 
+// packed records: one 8-byte record per particle
+template <int T>
+__device__ __forceinline__ void add_record(uint64_t p, uint64_t g, const SketchDesc &d,
+                                           const UpdateArgs &a, uint32_t *__restrict__ C) {
+    bool keep = a.keep_all || splitmix64_at(a.sample_seed, g) < a.thr;
+    uint32_t cx, cy, cz;
+    const bool valid = packed_cell(d, p, cx, cy, cz);
+    if (g - a.probe_base < a.probe_end - a.probe_base)
+        a.probe[g - a.probe_base] = valid ? key_of(cx, cy, cz, d.G) : kInvalidKey;
+    if (!(keep && valid)) return;
+    constexpr int kRows = T > 0 ? T : kMaxRows;
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        if (T == 0 && r >= (int)d.rows) break;
+        uint64_t v = row_value(d.seed[r], cx, cy, cz);
+        uint32_t b = bucket_of(v, d.log2w);
+        if (b >= a.band_lo && b < a.band_hi)
+            atomicAdd(&C[(uint64_t)r * d.W + b], sign_of(v, d.log2w));
+    }
+}
+
+template <int T>
+__global__ void __launch_bounds__(256) k_update_packed(const uint64_t *__restrict__ rec,
+                                                       const SketchDesc d, const UpdateArgs a,
+                                                       uint32_t *__restrict__ C) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride)
+        add_record<T>(__ldcs(reinterpret_cast<const unsigned long long *>(rec) + i), a.g0 + i, d,
+                      a, C);
+}
+
+// packed records of float32 positions (the quantisation of the mesh reduction
+// on a mesh of 2^21 cells per axis)
+__global__ void __launch_bounds__(256) k_pack(const float *__restrict__ xyz, uint64_t n,
+                                              float inv, uint64_t *__restrict__ out) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        uint32_t q[3];
+        bool ok = axis_cell(xyz[3 * i], inv, 1u << kPackBits, q[0]);
+        ok &= axis_cell(xyz[3 * i + 1], inv, 1u << kPackBits, q[1]);
+        ok &= axis_cell(xyz[3 * i + 2], inv, 1u << kPackBits, q[2]);
+        out[i] = ok ? (uint64_t)q[0] | ((uint64_t)q[1] << kPackBits) |
+                          ((uint64_t)q[2] << (2 * kPackBits))
+                    : kPackInvalid;
+    }
+}
+
 // Random fire-and-forget adds into an n_counters table (power of two): the
 // L2 reduction rate that bounds the update when the particle stream does not.
 __global__ void __launch_bounds__(256) k_red_rate(uint32_t *__restrict__ T, uint64_t mask,
@@ -147,6 +196,38 @@ cudaError_t launch_update(const float *xyz, uint64_t n, uint64_t g0, const Sketc
         if (vec) k_update_vec4<0><<<(unsigned)blocks, threads, 0, s>>>(xyz, d, a, Cu);
         else k_update_scalar<0><<<(unsigned)blocks, threads, 0, s>>>(xyz, d, a, Cu);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_packed(const uint64_t *rec, uint64_t n, uint64_t g0,
+                                 const SketchDesc &d, int32_t *C, double rate,
+                                 uint64_t sample_seed, uint64_t *probe, uint64_t probe_base,
+                                 uint64_t probe_cap, int max_blocks, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    UpdateArgs a;
+    a.n = n;
+    a.g0 = g0;
+    a.keep_all = rate >= 1.0 ? 1u : 0u;
+    a.thr = rate >= 1.0 ? 0 : (uint64_t)ldexp(rate, 64);
+    a.sample_seed = sample_seed;
+    a.probe = probe;
+    a.probe_base = probe_base;
+    a.probe_end = probe ? probe_base + probe_cap : probe_base;
+    a.band_lo = 0;
+    a.band_hi = (uint32_t)d.W;
+    uint32_t *Cu = reinterpret_cast<uint32_t *>(C);
+    uint64_t blocks = (n + 255) / 256;
+    if (blocks > (uint64_t)max_blocks) blocks = (uint64_t)max_blocks;
+    if (blocks < 1) blocks = 1;
+    if (d.rows == 5) k_update_packed<5><<<(unsigned)blocks, 256, 0, s>>>(rec, d, a, Cu);
+    else k_update_packed<0><<<(unsigned)blocks, 256, 0, s>>>(rec, d, a, Cu);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const float *xyz, uint64_t n, double box, uint64_t *out, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    uint64_t blocks = std::min<uint64_t>((n + 255) / 256, 16384);
+    k_pack<<<(unsigned)blocks, 256, 0, s>>>(xyz, n, (float)((double)(1u << kPackBits) / box), out);
     return cudaGetLastError();
 }
 

@@ -88,6 +88,8 @@ def lib():
                 "sketch_set_hierarchy": [vp, u32, u32, u32],
                 "sketch_super": [vp, ctypes.POINTER(vp)],
                 "sketch_wait_copies": [vp],
+                "sketch_update_packed": [vp, vp, u64, f64],
+                "pack_positions": [vp, u64, f64, vp, vp],
                 "sketch_query": [vp, vp, u64, vp],
                 "topk_extract": [vp, u32, vp, vp, ctypes.POINTER(u32)],
                 "sketch_destroy": [vp],
@@ -251,6 +253,20 @@ def sketch_seek(h, n_seen: int) -> None:
     _check(lib().sketch_seek(h, n_seen), "sketch_seek")
 
 
+def sketch_update_packed(h, records, n: int | None = None, sample_rate: float = 1.0) -> None:
+    if n is None:
+        n = records.numel() if hasattr(records, "numel") else records.size
+    _check(lib().sketch_update_packed(h, _ptr(records), n, sample_rate), "sketch_update_packed")
+
+
+def pack_positions(xyz, box: float, out, n: int | None = None, stream=None) -> None:
+    """64-bit records of n float32 positions (device tensors)."""
+    if n is None:
+        n = xyz.numel() // 3
+    _check(lib().pack_positions(_ptr(xyz), n, box, _stream_ptr(stream), _ptr(out)),
+           "pack_positions")
+
+
 def sketch_wait_copies(h) -> None:
     _check(lib().sketch_wait_copies(h), "sketch_wait_copies")
 
@@ -306,6 +322,9 @@ class Sketch:
 
     def update(self, xyz, n=None, rate: float = 1.0):
         sketch_update(self.h, xyz, n, rate)
+
+    def update_packed(self, records, n=None, rate: float = 1.0):
+        sketch_update_packed(self.h, records, n, rate)
 
     def query(self, keys) -> np.ndarray:
         keys = np.ascontiguousarray(keys, np.uint64)
