@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the sub-volume batch leg")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-router leg")
     ap.add_argument("--no-stream", action="store_true", help="skip the out-of-core stream leg")
+    ap.add_argument("--no-packed", action="store_true",
+                    help="skip the legs on 64-bit packed particle records")
     ap.add_argument("--stream-n", type=float, default=2e10, help="particles of the stream leg")
     ap.add_argument("--train-boxes", type=int, default=200,
                     help="100 Mpc/h training boxes of the learned router (seeds 1000..)")
@@ -401,7 +403,7 @@ def measure_h2d(src, dst, stream, reps: int = 5) -> float:
     return best
 
 
-def run_stream(n_total: int, hbm: float, learned_leg: bool = True):
+def run_stream(n_total: int, hbm: float, learned_leg: bool = True, packed_leg: bool = True):
     """Out-of-core stream: n_total particles of a 2000 Mpc/h box pass from pinned
     host chunks of 1 GB through the library's double-buffered staging (copy
     stream + compute stream) into a 5 x 2^26 sketch at sample rate 0.1, then
@@ -474,6 +476,7 @@ def run_stream(n_total: int, hbm: float, learned_leg: bool = True):
     h2d = 12.0 * n_total / (upd_ms * 1e-3) / 1e9
     kernel_ms = st["update_ms"] + st1["update_ms"]
     kern_gbs = 12.0 * n_total / (kernel_ms * 1e-3) / 1e9 if kernel_ms > 0 else None
+    packed = run_stream_packed(n_total, pool, sk, sup, stream, note) if packed_leg else None
     sk.close()
     learned = run_stream_learned(n_total, pool, C, stream, note) if learned_leg else None
     return {"workload": S["name"], "particles": n_total, "box_mpc_h": S["box"], "grid": round(S["box"] / S["cell"]),
@@ -494,7 +497,56 @@ def run_stream(n_total: int, hbm: float, learned_leg: bool = True):
                       "update_ms_fine": st["update_ms"], "update_ms_super": st1["update_ms"]},
             "generation": {"seconds": gen_s, "particles_per_s": gen_rate,
                            "note": "host generator rate; the stream cycles a pool of chunks"},
-            "learned": learned}
+            "packed": packed, "learned": learned}
+
+
+def run_stream_packed(n_total: int, pool, sk, sup, stream, note):
+    """The same stream as 64-bit records: 8 bytes a particle over the link.
+    The pool chunks are packed once on the GPU (Sec. 4 stores the dataset in
+    this layout); the chunk count stays, each chunk holds the same particles."""
+    import torch
+
+    from paper_1711_00975_gb300 import halosketch as hs
+
+    S = STREAM
+    C = pool[0].shape[0]
+    dchunk = torch.empty((C, 3), dtype=torch.float32, device="cuda")
+    drec = torch.empty(C, dtype=torch.int64, device="cuda")
+    rpool = []
+    for buf in pool:
+        dchunk.copy_(buf)
+        hs.pack_positions(dchunk, S["box"], drec, C, stream)
+        r = torch.empty(C, dtype=torch.int64).pin_memory()
+        r.copy_(drec)
+        rpool.append(r)
+    del dchunk, drec
+    torch.cuda.synchronize()
+    nchunks = (n_total + C - 1) // C
+    sk.reset()
+    sk.stats(reset=True)
+    hs.sketch_stats(sup, reset=True)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    w0 = time.perf_counter()
+    e[0].record(stream)
+    for c in range(nchunks):
+        hs.sketch_update_packed(sk.h, rpool[c % len(rpool)], min(C, n_total - c * C), S["rate"])
+    hs.sketch_flush(sk.h)
+    e[1].record(stream)
+    keys, est = sk.topk(S["k"])
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    note("packed stream done")
+    st = sk.stats(reset=True)
+    st1 = hs.sketch_stats(sup, reset=True)
+    upd = e[0].elapsed_time(e[1])
+    total = max(e[0].elapsed_time(e[2]), wall * 1e3)
+    return {"value": n_total / (total * 1e-3), "unit": "particles/s", "ms": total,
+            "stream_ms": upd, "topk_ms": e[1].elapsed_time(e[2]),
+            "h2d_gbs": 8.0 * n_total / (upd * 1e-3) / 1e9,
+            "update_kernel_ms": st["update_ms"] + st1["update_ms"],
+            "bytes_per_particle": 8}
 
 
 def run_stream_learned(n_total: int, pool, C: int, stream, note):
@@ -708,16 +760,62 @@ def run_ours(args):
                "h2d_bytes_per_step": 12 * n, "d2h_bytes_per_step": 12 * k,
                "ms_per_step": max(ems, wall * 1e3)}
 
+    main_keys = keys.copy()            # the float path's top-k, for the recall comparison
+    packed = None
+    if not args.no_packed:
+        # the same particles as 64-bit records (Sec. 4's data layout): 8 bytes
+        # a particle in HBM and over the host link
+        rec = torch.empty(n, dtype=torch.int64, device=dev.device)
+        hs.pack_positions(dev, WORKLOAD["box"], rec, n, stream)
+        rec_host = torch.empty(n, dtype=torch.int64).pin_memory()
+        rec_host.copy_(rec)
+        torch.cuda.synchronize()
+
+        def pstep(src):
+            hs.sketch_reset(sk.h)
+            hs.sketch_update_packed(sk.h, src, n, args.rate)
+            hs.sketch_flush(sk.h)
+            return hs.topk_extract(sk.h, k, keys, ests)
+
+        def ptimed(src, steps, warmup):
+            for _ in range(warmup):
+                pstep(src)
+            sk.stats(reset=True)
+            barrier()
+            w0 = time.perf_counter()
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(stream)
+            for _ in range(steps):
+                pstep(src)
+            b_.record(stream)
+            barrier()
+            return max(a_.elapsed_time(b_), (time.perf_counter() - w0) * 1e3) / steps, \
+                sk.stats(reset=True)
+
+        pms, pst = ptimed(rec, args.steps, args.warmup)
+        packed = {"records": "64-bit, three 21-bit coordinates", "value": n * world / (pms * 1e-3),
+                  "unit": "particles/s", "ms_per_step": pms,
+                  "update_ms": pst["update_ms"] / args.steps,
+                  "stream_gbs": 8.0 * n / (pst["update_ms"] / args.steps * 1e-3) / 1e9,
+                  "gpu_launches": int(pst["kernel_launches"])}
+        if not args.no_e2e:
+            ems, _ = ptimed(rec_host, max(2, args.steps // 2), 2)
+            packed["e2e"] = {"value": n * world / (ems * 1e-3), "unit": "particles/s",
+                             "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 12 * k,
+                             "ms_per_step": ems}
+        del rec, rec_host
+        torch.cuda.empty_cache()
+
     learned = None
     if not args.no_learned and rank == 0:
-        learned = run_learned(dev, n, keys.copy(), args.train_boxes, stream)
+        learned = run_learned(dev, n, main_keys, args.train_boxes, stream)
 
     stream_leg = None
     if not args.no_stream and rank == 0:
         del dev
         torch.cuda.empty_cache()
         dev = None
-        stream_leg = run_stream(int(args.stream_n), hbm, not args.no_learned)
+        stream_leg = run_stream(int(args.stream_n), hbm, not args.no_learned, not args.no_packed)
 
     batched = None
     if not args.no_batch:
@@ -751,7 +849,8 @@ def run_ours(args):
                           "candidates": st["last_candidates"], "threshold": st["last_threshold"],
                           "passes": st["last_passes"]},
             "roofline": roof, "search": search_roof, "red_rate": red, "second_rate": second, "e2e": e2e,
-            "batched": batched, "learned": learned, "stream": stream_leg, "cpu_baseline": cpu, "clocks": clocks,
+            "packed": packed, "batched": batched, "learned": learned, "stream": stream_leg,
+            "cpu_baseline": cpu, "clocks": clocks,
             "gpu_launches": int(st["kernel_launches"])}
     if rank == 0:
         print(json.dumps(line), flush=True)
