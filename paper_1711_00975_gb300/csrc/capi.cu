@@ -1,24 +1,16 @@
-// capi.cu - the library's C ABI (include/halosketch.h): handle lifetime, the
-// update path (device buffers directly, host buffers through double-buffered
-// staging), point queries and the exact full-search top-k.
-#include <algorithm>
-#include <cmath>
-#include <cstdarg>
-#include <cstdio>
-#include <cstring>
+// capi.cu - the library's C ABI (include/halosketch.h), single sketches:
+// handle lifetime, the update path (device buffers directly, host buffers
+// through staged copies), point queries, the exact full-search top-k and the
+// hierarchical query.  Batches, the no-allocation query and the learned
+// router live in capi_batch.cu, capi_noalloc.cu and capi_learned.cu.
 #include <atomic>
 #include <mutex>
-#include <string>
 #include <thread>
-#include <vector>
 
-#include "../../include/halosketch.h"
-#include "hs_device.cuh"
-#include "hs_kernels.h"
+#include "capi_internal.h"
 
-using namespace hs;
-
-namespace {
+namespace hs {
+namespace capi {
 
 thread_local std::string g_last_error;
 
@@ -32,112 +24,6 @@ hs_status fail(hs_status st, const char *fmt, ...) {
     return st;
 }
 
-#define HS_CUDA(call)                                                                      \
-    do {                                                                                   \
-        cudaError_t e_ = (call);                                                           \
-        if (e_ != cudaSuccess)                                                             \
-            return fail(e_ == cudaErrorMemoryAllocation ? HS_ERR_OOM : HS_ERR_CUDA,        \
-                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
-                        __LINE__);                                                         \
-    } while (0)
-
-constexpr uint64_t kProbeCap = 1ull << 20;        // keys of the first 2^20 particles
-constexpr uint32_t kProbeSlotsLog2 = 21;
-constexpr uint64_t kStageParticles = 1ull << 24;  // 192 MiB per staging buffer
-constexpr int kStageBuffers = 3;                    // copies run ahead through a drain
-constexpr size_t kSearchSmemBudget = 192 * 1024;
-constexpr size_t kBinSmemBudget = 224 * 1024;
-constexpr uint64_t kBinBudgetBytes = 4ull << 30;   // global bins, at most
-constexpr double kBinnedMinUpdates = 1 << 20;      // smaller calls add directly
-constexpr uint64_t kMaxScanCells = 1ull << 40;      // largest full scan one top-k may run
-constexpr uint32_t kBatchViews = 8;                 // volumes whose top-k run concurrently
-
-struct EventPair {
-    cudaEvent_t a, b;
-};
-
-}  // namespace
-
-struct hs_sketch {
-    hs_params p;
-    SketchDesc d;
-    uint64_t n_cells = 0;
-    uint32_t key_bits = 0;
-    int device = 0;
-    int num_sms = 0;
-    cudaStream_t stream = nullptr;
-    int32_t *C = nullptr;
-    uint64_t *probe = nullptr;
-    uint64_t probe_cap = kProbeCap;   // probe slots
-    uint64_t probe_base = 0;    // global index of probe slot 0
-    uint64_t n_seen = 0;
-
-    // staging for host particle buffers
-    float *stage[kStageBuffers] = {};
-    cudaStream_t copy_stream = nullptr;
-    cudaEvent_t ev_copied[kStageBuffers] = {};
-    cudaEvent_t ev_free[kStageBuffers] = {};
-
-    // top-k scratch
-    uint64_t cap = 0;               // candidate capacity
-    uint64_t min_cap = 0;           // extra candidates a learned top-k appends
-    hs_sketch *super = nullptr;     // hierarchy: sketch of F^3 super-items (Algorithm 3)
-    uint32_t super_mult = 0;        // hierarchy: c of the top-(c*k) super-items
-    uint64_t *cand_key = nullptr;
-    int32_t *cand_est = nullptr;
-    unsigned long long *counters = nullptr;   // [0] candidates, [1] tmp, [2] distinct
-    uint32_t *flags = nullptr;                // [0] bad key, [1] probe overflow
-    uint32_t *bitmap = nullptr;
-    uint32_t nb = 0;
-    uint64_t *slots = nullptr;
-    uint64_t *distinct = nullptr;
-    int32_t *distinct_est = nullptr;
-    SelectState *sel = nullptr;
-    unsigned long long *hist = nullptr;
-    uint64_t *tmp_key = nullptr;
-    int32_t *tmp_est = nullptr;
-    uint32_t *tmp_rank = nullptr;
-    uint64_t *out_key = nullptr;
-    int32_t *out_est = nullptr;
-    uint64_t out_cap = 0;
-    uint64_t *q_keys = nullptr;
-    int32_t *q_est = nullptr;
-    uint64_t q_cap = 0;
-
-    // output-sensitive search: exact hot bitmap, hot-bucket lists, and one
-    // directory of mesh lines per enumerated row (kept across queries)
-    uint32_t *xbits = nullptr;
-    uint32_t *hot_list = nullptr;
-    unsigned long long *hot_cnt = nullptr;
-    uint64_t hot_cap = 0;
-    uint32_t dir_D = 0;
-    uint32_t *dir_off[kMaxRows] = {};
-    DirRecord *dir_rec[kMaxRows] = {};
-    uint32_t *dir_cursor = nullptr;
-    uint32_t *scan_scratch = nullptr;
-    bool dir_failed = false;
-    uint32_t dir_G[kMaxRows] = {};        // mesh the directory of row r was built for
-    uint64_t dir_lines_cap[kMaxRows] = {};
-    bool is_view = false;                 // counters and probe belong to a batch
-    bool routing = false;                 // learned router: routed cells go to a table
-    RouteTarget route{};
-
-    // binned update: codes waiting in global bins until the next drain
-    BinLayout bl{};
-    uint16_t *bins = nullptr;
-    uint32_t *bin_cursor = nullptr;
-    uint32_t bin_cap = 0;
-    uint4 *carry = nullptr;         // scatter rings carried from one launch to the next
-    bool carry_valid = false;
-    double pending = 0;          // kept particles binned since the last drain
-    double pending_limit = 0;    // drain before the expected bin load passes this
-
-    // benchmarking
-    hs_stats stats;
-    std::vector<EventPair> pending_update, pending_search, pending_flush, pool;
-};
-
-namespace {
 
 bool is_device_ptr(const void *p) {
     cudaPointerAttributes a;
@@ -363,8 +249,6 @@ hs_status ensure_query_scratch(hs_sketch *h, uint64_t m) {
     return HS_OK;
 }
 
-hs_status launch_update_direct(hs_sketch *h, const float *xyz, uint64_t n, uint64_t g0,
-                               double rate, bool packed = false);
 
 // add every binned code to the counters (before anything reads them)
 hs_status drain(hs_sketch *h) {
@@ -427,7 +311,7 @@ hs_status ensure_bins(hs_sketch *h, uint64_t n, double rate) {
 
 // xyz: float32 positions, or packed 64-bit records when packed is set
 hs_status launch_update_timed(hs_sketch *h, const float *xyz, uint64_t n, uint64_t g0,
-                              double rate, bool packed = false) {
+                              double rate, bool packed) {
     const size_t esz = packed ? 8 : 12;
     if (want_binned(h, n, rate)) {
         hs_status st = ensure_bins(h, n, rate);
@@ -629,7 +513,8 @@ hs_status finalize(hs_sketch *h, uint64_t m, uint64_t k) {
     return HS_OK;
 }
 
-}  // namespace
+}  // namespace capi
+}  // namespace hs
 
 extern "C" {
 
@@ -1217,1312 +1102,6 @@ hs_status hs_measure_red_rate(uint64_t n_counters, uint64_t total_ops, double *o
     cudaFree(t);
     if (e != cudaSuccess) return fail(HS_ERR_CUDA, "red-rate kernel: %s", cudaGetErrorString(e));
     *ops_per_s = (double)per * blocks * 256 / (ms * 1e-3);
-    return HS_OK;
-}
-
-}  // extern "C"
-
-// ---------------------------------------------------------------------------
-// sketch_query_noalloc: point queries without any device allocation.
-//
-// Some callers cannot call cudaMalloc at the moment they query: code running
-// while a CUDA stream is being captured into a graph (allocation is not a
-// capturable operation), processes whose device memory is fully reserved by
-// another allocator or a fixed budget, and latency-critical loops where an
-// allocation's synchronisation is not acceptable.  sketch_query may allocate
-// staging buffers on its first call with host arrays; this variant instead
-// uses one file-scope device array, sized for at most
-// HS_NOALLOC_QUERY_MAX keys, that every GPU loading this library holds until
-// the process exits.
-// ---------------------------------------------------------------------------
-
-namespace {
-
-constexpr uint64_t kNoallocMax = HS_NOALLOC_QUERY_MAX;
-constexpr size_t kNoallocKeysOff = 0;
-constexpr size_t kNoallocEstOff = kNoallocMax * 8;
-constexpr size_t kNoallocFlagOff = kNoallocMax * 12;
-constexpr size_t kNoallocBytes = kNoallocMax * 12 + 256;
-constexpr int kNoallocMaxDevices = 64;
-
-// keys staging | estimates staging | out-of-range flag; shared by every call
-static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
-
-std::mutex g_noalloc_mu;
-unsigned char *g_noalloc_ptr[kNoallocMaxDevices] = {};
-
-// Device address of the scratch array on `dev` (which must be current).  The
-// host-side name g_noalloc_scratch is only a stand-in, never a device address.
-hs_status noalloc_scratch(int dev, unsigned char **out) {
-    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(HS_ERR_ARG, "device %d unsupported", dev);
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(HS_ERR_CUDA, "cudaGetSymbolAddress of the query scratch failed: %s",
-                        cudaGetErrorString(e));
-        g_noalloc_ptr[dev] = static_cast<unsigned char *>(p);
-    }
-    *out = g_noalloc_ptr[dev];
-    return HS_OK;
-}
-
-// Estimate (Sec. 2.2) of each key; keys >= G^3 give 0 and set *bad.
-__global__ void k_point_query_noalloc(const int32_t *__restrict__ C, const SketchDesc d,
-                                      const uint64_t *__restrict__ keys, uint64_t m,
-                                      int32_t *__restrict__ est, uint32_t *__restrict__ bad) {
-    const uint64_t n_cells = (uint64_t)d.G * d.G * d.G;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-        uint64_t key = keys[i];
-        if (key >= n_cells) {
-            est[i] = 0;
-            atomicOr(bad, 1u);
-            continue;
-        }
-        uint32_t cx = (uint32_t)(key % d.G);
-        uint64_t rest = key / d.G;
-        uint32_t cy = (uint32_t)(rest % d.G), cz = (uint32_t)(rest / d.G);
-        int32_t ev[kMaxRows];
-        for (uint32_t r = 0; r < d.rows; ++r) {
-            uint64_t v = row_value(d.seed[r], cx, cy, cz);
-            ev[r] = signed_count(C[r * d.W + bucket_of(v, d.log2w)], v, d.log2w);
-        }
-        est[i] = d.rows == 5 ? median5(ev[0], ev[1], ev[2], ev[3], ev[4])
-                             : lower_median_dyn(ev, (int)d.rows);
-    }
-}
-
-}  // namespace
-
-extern "C" hs_status sketch_query_noalloc(hs_sketch *h, const uint64_t *keys, uint64_t m,
-                                          int32_t *est) {
-    if (!h) return fail(HS_ERR_ARG, "handle is NULL");
-    if (m == 0) return HS_OK;
-    if (!keys || !est) return fail(HS_ERR_ARG, "keys/est is NULL");
-    if (m > kNoallocMax)
-        return fail(HS_ERR_ARG, "m=%llu exceeds HS_NOALLOC_QUERY_MAX=%llu; split the query",
-                    (unsigned long long)m, (unsigned long long)kNoallocMax);
-    int dev = -1;
-    HS_CUDA(cudaGetDevice(&dev));
-    if (dev != h->device)
-        return fail(HS_ERR_STATE, "make the sketch's device %d current (current: %d)", h->device,
-                    dev);
-    unsigned char *scratch = nullptr;
-    hs_status st = noalloc_scratch(dev, &scratch);
-    if (st != HS_OK) return st;
-    st = drain(h);   // pending binned increments use buffers that already exist
-    if (st != HS_OK) return st;
-    uint64_t *s_keys = reinterpret_cast<uint64_t *>(scratch + kNoallocKeysOff);
-    int32_t *s_est = reinterpret_cast<int32_t *>(scratch + kNoallocEstOff);
-    uint32_t *s_flag = reinterpret_cast<uint32_t *>(scratch + kNoallocFlagOff);
-    const bool kd = is_device_ptr(keys), ed = is_device_ptr(est);
-    const uint64_t *dk = keys;
-    int32_t *de = ed ? est : s_est;
-    if (!kd) {
-        HS_CUDA(cudaMemcpyAsync(s_keys, keys, m * 8, cudaMemcpyHostToDevice, h->stream));
-        dk = s_keys;
-    }
-    HS_CUDA(cudaMemsetAsync(s_flag, 0, 4, h->stream));   // the previous call's flag stays otherwise
-    uint64_t blocks = std::min<uint64_t>((m + 255) / 256, 65535);
-    k_point_query_noalloc<<<(unsigned)blocks, 256, 0, h->stream>>>(h->C, h->d, dk, m, de, s_flag);
-    HS_CUDA(cudaGetLastError());
-    h->stats.kernel_launches += 1;
-    if (!ed) HS_CUDA(cudaMemcpyAsync(est, de, m * 4, cudaMemcpyDeviceToHost, h->stream));
-    uint32_t bad = 0;
-    HS_CUDA(cudaMemcpyAsync(&bad, s_flag, 4, cudaMemcpyDeviceToHost, h->stream));
-    HS_CUDA(cudaStreamSynchronize(h->stream));
-    if (bad) return fail(HS_ERR_ARG, "a key is >= G^3 = %llu", (unsigned long long)h->n_cells);
-    return HS_OK;
-}
-
-// ---------------------------------------------------------------------------
-// Batches of independent sub-volumes (each with its own mesh, stream index,
-// sketch and top-k), updated by one persistent scatter launch and one
-// accumulation launch, replayed as a CUDA graph.
-// ---------------------------------------------------------------------------
-
-namespace {
-
-constexpr uint64_t kBatchProbe = 1ull << 16;   // probe keys per volume
-
-}  // namespace
-
-struct hs_batch {
-    hs_params p;
-    uint32_t nvol = 0;
-    SketchDesc d;                       // rows, log2 W, seeds
-    std::vector<uint32_t> G;
-    std::vector<float> inv;
-    std::vector<uint64_t> n_seen, probe_base;
-    int device = 0, num_sms = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    int32_t *C = nullptr;               // nvol x rows x W
-    uint64_t *probe = nullptr;          // nvol x kBatchProbe
-    BinLayout bl{};                     // over nvol * rows rows
-    uint16_t *bins = nullptr;
-    uint32_t *cursor = nullptr;
-    uint32_t cap = 0;
-    VolumeDesc *d_vols = nullptr;
-    VolumeDesc *h_vols = nullptr;       // pinned: read by the graph's copy node
-    int threads = 1024;
-    hs_sketch *view = nullptr;          // views[0]
-    std::vector<hs_sketch *> views;     // top-k of one volume each, concurrently, own streams
-    std::vector<cudaEvent_t> vdone;     // each view's stream has finished
-    // directories of each volume's enumerated rows, kept across queries
-    std::vector<uint32_t *> vdir_off;
-    std::vector<DirRecord *> vdir_rec;
-    std::vector<uint32_t> vdir_G;
-    std::vector<uint64_t> vdir_cap;
-    cudaGraphExec_t gexec = nullptr;
-    const float *g_xyz = nullptr;
-    uint64_t g_n = 0;
-    double g_rate = -1;
-    cudaEvent_t done = nullptr;         // the last graph launch has finished with h_vols
-    cudaEvent_t fork = nullptr;         // the views' streams start after this
-    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
-    hs_stats stats;
-};
-
-namespace {
-
-void batch_drop_graph(hs_batch *b) {
-    if (b->gexec) cudaGraphExecDestroy(b->gexec);
-    b->gexec = nullptr;
-    b->g_xyz = nullptr;
-}
-
-SketchDesc batch_flat_desc(const hs_batch *b) {
-    SketchDesc dd = b->d;
-    dd.rows = b->nvol * b->d.rows;      // the layout sees one sketch of nvol * t rows
-    return dd;
-}
-
-hs_status batch_ensure_bins(hs_batch *b, const uint64_t *offsets, double rate) {
-    if (b->bins) return HS_OK;
-    const double bins_per_row = (double)(1ull << (b->d.log2w - b->bl.S));
-    uint64_t most = 0;
-    for (uint32_t v = 0; v < b->nvol; ++v) most = std::max(most, offsets[v + 1] - offsets[v]);
-    uint64_t want = (uint64_t)(1.3 * (double)most * rate / bins_per_row) + 8192;
-    uint64_t cap = std::min<uint64_t>(want, kBinBudgetBytes / (2ull * b->bl.nbins));
-    cap = std::min<uint64_t>(std::max<uint64_t>(cap, 4096), 0xFFFFFFF0ull);
-    cap = (cap + 15) & ~15ull;
-    HS_CUDA(cudaMalloc(&b->bins, (size_t)b->bl.nbins * cap * 2));
-    b->cap = (uint32_t)cap;
-    return HS_OK;
-}
-
-// scatter + accumulate of the whole batch on b->stream (captured or direct)
-hs_status batch_enqueue(hs_batch *b, const float *xyz, uint64_t n, double rate) {
-    HS_CUDA(cudaMemcpyAsync(b->d_vols, b->h_vols, b->nvol * sizeof(VolumeDesc),
-                            cudaMemcpyHostToDevice, b->stream));
-    int grid = b->num_sms * (b->threads == 512 ? 2 : 1);
-    HS_CUDA(launch_bin_scatter(xyz, n, 0, b->d, b->C, rate, b->p.sample_seed, b->probe, 0,
-                               kBatchProbe, b->bl, b->bins, b->cursor, b->cap, grid, b->stream,
-                               b->d_vols, b->nvol, kBatchProbe, b->threads));
-    HS_CUDA(launch_bin_accumulate(b->bl, b->bins, b->cursor, b->cap, b->C, b->stream));
-    return HS_OK;
-}
-
-hs_status batch_check_offsets(const hs_batch *b, const float *xyz, const uint64_t *offsets) {
-    if (!offsets) return fail(HS_ERR_ARG, "offsets is NULL");
-    if (offsets[0] != 0) return fail(HS_ERR_ARG, "offsets[0] must be 0");
-    for (uint32_t v = 0; v < b->nvol; ++v)
-        if (offsets[v + 1] < offsets[v]) return fail(HS_ERR_ARG, "offsets must not decrease");
-    if (offsets[b->nvol] > 0) {
-        if (!xyz) return fail(HS_ERR_ARG, "xyz is NULL");
-        if (!is_device_ptr(xyz)) return fail(HS_ERR_ARG, "batch particles must be device memory");
-    }
-    return HS_OK;
-}
-
-void batch_fill_vols(hs_batch *b, const uint64_t *offsets) {
-    const uint32_t bins_per_row = 1u << (b->d.log2w - b->bl.S);
-    for (uint32_t v = 0; v < b->nvol; ++v) {
-        VolumeDesc &V = b->h_vols[v];
-        V.start = offsets[v];
-        V.g0 = b->n_seen[v];
-        V.probe_base = b->probe_base[v];
-        V.inv_cell = b->inv[v];
-        V.G = b->G[v];
-        V.bin0 = v * b->d.rows * bins_per_row;
-        V.pad = 0;
-    }
-}
-
-}  // namespace
-
-extern "C" {
-
-hs_status batch_destroy(hs_batch *b);
-
-hs_status batch_create(const hs_params *params, uint32_t n_volumes, const double *boxes,
-                       void *cuda_stream, hs_batch **out) {
-    if (!out || !boxes || n_volumes == 0) return fail(HS_ERR_ARG, "NULL argument or no volumes");
-    if (!params) return fail(HS_ERR_ARG, "params is NULL");
-    hs_params p = *params;
-    p.box = boxes[0];
-    hs_status st = check_params(&p);
-    if (st != HS_OK) return st;
-    hs_batch *b = new (std::nothrow) hs_batch();
-    if (!b) return fail(HS_ERR_OOM, "host allocation failed");
-    b->p = p;
-    b->nvol = n_volumes;
-    std::memset(&b->stats, 0, sizeof(b->stats));
-    std::memset(&b->d, 0, sizeof(b->d));
-    b->d.rows = p.rows;
-    b->d.log2w = p.log2_width;
-    b->d.W = 1ull << p.log2_width;
-    for (uint32_t r = 0; r < p.rows; ++r) {
-        b->d.seed[r].a0 = splitmix64_at(p.hash_seed, 4 * r + 0);
-        b->d.seed[r].a1 = splitmix64_at(p.hash_seed, 4 * r + 1);
-        b->d.seed[r].a2 = splitmix64_at(p.hash_seed, 4 * r + 2);
-        b->d.seed[r].b = splitmix64_at(p.hash_seed, 4 * r + 3);
-    }
-    b->G.resize(n_volumes);
-    b->inv.assign(n_volumes, (float)(1.0 / p.cell));
-    b->n_seen.assign(n_volumes, 0);
-    b->probe_base.assign(n_volumes, 0);
-    for (uint32_t v = 0; v < n_volumes; ++v) {
-        double g = std::llround(boxes[v] / p.cell);
-        if (!(boxes[v] > 0) || g < 1 || g > 65535) {
-            delete b;
-            return fail(HS_ERR_ARG, "volume %u: grid round(box/cell) outside [1, 65535]", v);
-        }
-        b->G[v] = (uint32_t)g;
-    }
-    b->d.G = b->G[0];
-    b->d.inv_cell = b->inv[0];
-    b->d.Gq = b->d.G;
-    b->d.F = 1;
-    b->bl = bin_layout(batch_flat_desc(b), kBinSmemBudget);
-    if (b->bl.slot == 0 || b->bl.nbins >= 65536) {
-        delete b;
-        return fail(HS_ERR_ARG, "%u volumes x %u rows x 2^%u counters need too many bins; "
-                    "split the batch", n_volumes, p.rows, p.log2_width);
-    }
-    const size_t counters = (size_t)n_volumes * p.rows * b->d.W;
-    cudaError_t e = cudaGetDevice(&b->device);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
-    if (e == cudaSuccess) {
-        if (cuda_stream) b->stream = (cudaStream_t)cuda_stream;
-        else {
-            e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
-            b->own_stream = true;
-        }
-    }
-    if (e == cudaSuccess) e = cudaMalloc(&b->C, counters * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&b->probe, (size_t)n_volumes * kBatchProbe * 8);
-    if (e == cudaSuccess) e = cudaMalloc(&b->cursor, (size_t)b->bl.nbins * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_vols, n_volumes * sizeof(VolumeDesc));
-    if (e == cudaSuccess) e = cudaMallocHost(&b->h_vols, n_volumes * sizeof(VolumeDesc));
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreate(&b->ev_a);
-    if (e == cudaSuccess) e = cudaEventCreate(&b->ev_b);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->C, 0, counters * 4, b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->probe, 0xFF, (size_t)n_volumes * kBatchProbe * 8, b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->cursor, 0, (size_t)b->bl.nbins * 4, b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    const uint32_t nviews = std::min<uint32_t>(n_volumes, kBatchViews);
-    for (uint32_t t = 0; t < nviews && e == cudaSuccess; ++t) {
-        hs_sketch *h = new (std::nothrow) hs_sketch();
-        if (!h) {
-            e = cudaErrorMemoryAllocation;
-            break;
-        }
-        h->p = p;
-        h->d = b->d;
-        h->is_view = true;
-        h->device = b->device;
-        h->num_sms = b->num_sms;
-        h->probe_cap = kBatchProbe;
-        h->bl = BinLayout{};        // views never bin
-        std::memset(&h->stats, 0, sizeof(h->stats));
-        b->views.push_back(h);
-        b->vdone.push_back(nullptr);
-        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->vdone.back(), cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaMalloc(&h->flags, 4 * sizeof(uint32_t));
-    }
-    if (e == cudaSuccess) b->view = b->views[0];
-    if (e != cudaSuccess) {
-        hs_status code = e == cudaErrorMemoryAllocation ? HS_ERR_OOM : HS_ERR_CUDA;
-        batch_destroy(b);
-        return fail(code, "batch_create: %s", cudaGetErrorString(e));
-    }
-    *out = b;
-    return HS_OK;
-}
-
-hs_status batch_destroy(hs_batch *b) {
-    if (!b) return HS_OK;
-    if (b->stream) cudaStreamSynchronize(b->stream);
-    batch_drop_graph(b);
-    for (size_t t = 0; t < b->views.size(); ++t) {
-        hs_sketch *h = b->views[t];
-        h->C = nullptr;
-        h->probe = nullptr;
-        cudaStream_t vs = h->stream;
-        sketch_destroy(h);
-        if (vs) cudaStreamDestroy(vs);
-        if (b->vdone[t]) cudaEventDestroy(b->vdone[t]);
-    }
-    void *ps[] = {b->C, b->probe, b->cursor, b->d_vols, b->bins};
-    for (void *q : ps)
-        if (q) cudaFree(q);
-    for (auto *q : b->vdir_off)
-        if (q) cudaFree(q);
-    for (auto *q : b->vdir_rec)
-        if (q) cudaFree(q);
-    if (b->h_vols) cudaFreeHost(b->h_vols);
-    if (b->done) cudaEventDestroy(b->done);
-    if (b->fork) cudaEventDestroy(b->fork);
-    if (b->ev_a) cudaEventDestroy(b->ev_a);
-    if (b->ev_b) cudaEventDestroy(b->ev_b);
-    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
-    delete b;
-    cudaGetLastError();
-    return HS_OK;
-}
-
-hs_status batch_update(hs_batch *b, const float *xyz, const uint64_t *offsets, double sample_rate) {
-    if (!b) return fail(HS_ERR_ARG, "batch is NULL");
-    if (!(sample_rate > 0.0 && sample_rate <= 1.0))
-        return fail(HS_ERR_ARG, "sample_rate=%g outside (0, 1]", sample_rate);
-    hs_status st = batch_check_offsets(b, xyz, offsets);
-    if (st != HS_OK) return st;
-    const uint64_t n = offsets[b->nvol];
-    if (n == 0) return HS_OK;
-    st = batch_ensure_bins(b, offsets, sample_rate);
-    if (st != HS_OK) return st;
-    HS_CUDA(cudaEventSynchronize(b->done));          // the previous graph has read h_vols
-    batch_fill_vols(b, offsets);
-    if (!b->gexec || b->g_xyz != xyz || b->g_n != n || b->g_rate != sample_rate) {
-        batch_drop_graph(b);
-        cudaGraph_t graph = nullptr;
-        HS_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed));
-        st = batch_enqueue(b, xyz, n, sample_rate);
-        cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
-        if (st != HS_OK) {
-            if (graph) cudaGraphDestroy(graph);
-            return st;
-        }
-        HS_CUDA(e);
-        e = cudaGraphInstantiate(&b->gexec, graph, 0);
-        cudaGraphDestroy(graph);
-        HS_CUDA(e);
-        b->g_xyz = xyz;
-        b->g_n = n;
-        b->g_rate = sample_rate;
-    }
-    HS_CUDA(cudaEventRecord(b->ev_a, b->stream));
-    HS_CUDA(cudaGraphLaunch(b->gexec, b->stream));
-    HS_CUDA(cudaEventRecord(b->ev_b, b->stream));
-    HS_CUDA(cudaEventRecord(b->done, b->stream));
-    b->stats.kernel_launches += 2;
-    b->stats.update_launches += 1;
-    for (uint32_t v = 0; v < b->nvol; ++v) b->n_seen[v] += offsets[v + 1] - offsets[v];
-    return HS_OK;
-}
-
-// Top-k of volume v on view h (the view borrows the volume's counters, probe
-// and directories, and returns the directories it built).
-static hs_status batch_topk_one(hs_batch *b, hs_sketch *h, uint32_t v, uint32_t F, uint32_t k,
-                                uint64_t *keys, int32_t *est, uint32_t *n_out) {
-    for (uint32_t r = 0; r < F; ++r) {
-        h->dir_off[r] = b->vdir_off[v * F + r];
-        h->dir_rec[r] = b->vdir_rec[v * F + r];
-        h->dir_G[r] = b->vdir_G[v * F + r];
-        h->dir_lines_cap[r] = b->vdir_cap[v * F + r];
-    }
-    h->C = b->C + (size_t)v * b->d.rows * b->d.W;
-    h->probe = b->probe + (size_t)v * kBatchProbe;
-    h->d.G = b->G[v];
-    h->d.Gq = b->G[v];
-    h->d.F = 1;
-    h->d.inv_cell = b->inv[v];
-    h->n_cells = (uint64_t)b->G[v] * b->G[v] * b->G[v];
-    h->key_bits = 1;
-    while (h->key_bits < 64 && (1ull << h->key_bits) < h->n_cells) ++h->key_bits;
-    h->n_seen = b->n_seen[v];
-    h->probe_base = b->probe_base[v];
-    hs_status st = topk_extract(h, k, keys + (size_t)v * k, est + (size_t)v * k, &n_out[v]);
-    for (uint32_t r = 0; r < F; ++r) {
-        b->vdir_off[v * F + r] = h->dir_off[r];
-        b->vdir_rec[v * F + r] = h->dir_rec[r];
-        b->vdir_G[v * F + r] = h->dir_G[r];
-        b->vdir_cap[v * F + r] = h->dir_lines_cap[r];
-        h->dir_off[r] = nullptr;
-        h->dir_rec[r] = nullptr;
-        h->dir_G[r] = 0;
-        h->dir_lines_cap[r] = 0;
-    }
-    return st;
-}
-
-hs_status batch_topk(hs_batch *b, uint32_t k, uint64_t *keys, int32_t *est, uint32_t *n_out) {
-    if (!b) return fail(HS_ERR_ARG, "batch is NULL");
-    if (k == 0 || !keys || !est || !n_out) return fail(HS_ERR_ARG, "k == 0 or NULL output");
-    const uint32_t F = enum_rows(b->view);
-    if (b->vdir_off.size() != (size_t)b->nvol * F) {
-        b->vdir_off.assign((size_t)b->nvol * F, nullptr);
-        b->vdir_rec.assign((size_t)b->nvol * F, nullptr);
-        b->vdir_G.assign((size_t)b->nvol * F, 0);
-        b->vdir_cap.assign((size_t)b->nvol * F, 0);
-    }
-    // the views start after the batch's pending work; the batch resumes after theirs
-    HS_CUDA(cudaEventRecord(b->fork, b->stream));
-    for (hs_sketch *h : b->views) HS_CUDA(cudaStreamWaitEvent(h->stream, b->fork, 0));
-    // each host thread drives one view over volumes taken from a shared counter
-    std::atomic<uint32_t> next{0};
-    std::vector<hs_status> status(b->views.size(), HS_OK);
-    std::vector<std::string> msg(b->views.size());
-    auto work = [&](size_t t) {
-        cudaSetDevice(b->device);
-        for (uint32_t v = next.fetch_add(1); v < b->nvol; v = next.fetch_add(1)) {
-            hs_status st = batch_topk_one(b, b->views[t], v, F, k, keys, est, n_out);
-            if (st != HS_OK) {
-                status[t] = st;
-                msg[t] = hs_last_error();
-                next.store(b->nvol);
-                break;
-            }
-        }
-    };
-    std::vector<std::thread> pool;
-    for (size_t t = 1; t < b->views.size(); ++t) pool.emplace_back(work, t);
-    work(0);
-    for (auto &th : pool) th.join();
-    for (size_t t = 0; t < b->views.size(); ++t) {
-        HS_CUDA(cudaEventRecord(b->vdone[t], b->views[t]->stream));
-        HS_CUDA(cudaStreamWaitEvent(b->stream, b->vdone[t], 0));
-    }
-    for (size_t t = 0; t < b->views.size(); ++t)
-        if (status[t] != HS_OK) return fail(status[t], "%s", msg[t].c_str());
-    return HS_OK;
-}
-
-hs_status batch_counters(hs_batch *b, uint32_t volume, int32_t *out) {
-    if (!b || !out || volume >= (b ? b->nvol : 0)) return fail(HS_ERR_ARG, "bad argument");
-    const size_t per = (size_t)b->d.rows * b->d.W;
-    HS_CUDA(cudaMemcpyAsync(out, b->C + volume * per, per * 4, cudaMemcpyDefault, b->stream));
-    HS_CUDA(cudaStreamSynchronize(b->stream));
-    return HS_OK;
-}
-
-hs_status batch_reset(hs_batch *b) {
-    if (!b) return fail(HS_ERR_ARG, "batch is NULL");
-    HS_CUDA(cudaMemsetAsync(b->C, 0, (size_t)b->nvol * b->d.rows * b->d.W * 4, b->stream));
-    HS_CUDA(cudaMemsetAsync(b->probe, 0xFF, (size_t)b->nvol * kBatchProbe * 8, b->stream));
-    HS_CUDA(cudaMemsetAsync(b->cursor, 0, (size_t)b->bl.nbins * 4, b->stream));
-    std::fill(b->n_seen.begin(), b->n_seen.end(), 0);
-    std::fill(b->probe_base.begin(), b->probe_base.end(), 0);
-    return HS_OK;
-}
-
-hs_status batch_volume_info(const hs_batch *b, uint32_t volume, hs_info *out) {
-    if (!b || !out || volume >= b->nvol) return fail(HS_ERR_ARG, "bad argument");
-    out->rows = b->d.rows;
-    out->log2_width = b->d.log2w;
-    out->grid = b->G[volume];
-    out->inv_cell = b->inv[volume];
-    out->width = b->d.W;
-    out->n_cells = (uint64_t)b->G[volume] * b->G[volume] * b->G[volume];
-    out->n_seen = b->n_seen[volume];
-    return HS_OK;
-}
-
-hs_status batch_stats(hs_batch *b, hs_stats *out, int reset) {
-    if (!b || !out) return fail(HS_ERR_ARG, "NULL argument");
-    HS_CUDA(cudaStreamSynchronize(b->stream));
-    float ms = 0;
-    if (b->stats.update_launches && cudaEventElapsedTime(&ms, b->ev_a, b->ev_b) == cudaSuccess)
-        b->stats.update_ms = ms;                     // the last update
-    cudaGetLastError();
-    *out = b->stats;
-    out->search_launches = 0;
-    out->search_ms = 0;
-    out->topk_ms = 0;
-    out->topk_calls = 0;
-    for (hs_sketch *h : b->views) {
-        hs_stats vs{};
-        sketch_stats(h, &vs, reset);
-        out->kernel_launches += vs.kernel_launches;
-        out->search_launches += vs.search_launches;
-        out->search_ms += vs.search_ms;
-        out->topk_ms += vs.topk_ms;     // summed over concurrent views
-        out->topk_calls += vs.topk_calls;
-    }
-    if (reset) std::memset(&b->stats, 0, sizeof(b->stats));
-    return HS_OK;
-}
-
-hs_status batch_autotune(hs_batch *b, const float *xyz, const uint64_t *offsets,
-                         double sample_rate, hs_tune *out) {
-    if (!b || !out) return fail(HS_ERR_ARG, "NULL argument");
-    if (!(sample_rate > 0.0 && sample_rate <= 1.0)) return fail(HS_ERR_ARG, "bad sample_rate");
-    hs_status st = batch_check_offsets(b, xyz, offsets);
-    if (st != HS_OK) return st;
-    const uint64_t n = offsets[b->nvol];
-    if (n == 0) return fail(HS_ERR_ARG, "no particles to tune on");
-    st = batch_ensure_bins(b, offsets, sample_rate);
-    if (st != HS_OK) return st;
-    batch_drop_graph(b);
-    const BinLayout base = b->bl;
-    const int threads_opt[2] = {1024, 512};
-    const uint32_t slot_opt[2] = {32, 16};
-    float best = 1e30f;
-    int best_t = b->threads;
-    BinLayout best_l = base;
-    int tried = 0;
-    for (int ti = 0; ti < 2; ++ti)
-        for (int si = 0; si < 2; ++si) {
-            BinLayout L = base;
-            L.slot = slot_opt[si];
-            size_t queue = (size_t)(1024 / 32) * 128 * 8;
-            L.smem = ((L.nbins * 4 + 15) & ~15ull) + ((L.nbins * L.slot * 2 + 15) & ~15ull) + queue +
-                     ((L.nbins + 31) / 32) * 4;
-            if (L.smem > kBinSmemBudget) continue;
-            if (threads_opt[ti] == 512 && L.nbins > 6u * 512) continue;
-            b->bl = L;
-            b->threads = threads_opt[ti];
-            float ms_best = 1e30f;
-            for (int rep = 0; rep < 2; ++rep) {
-                batch_fill_vols(b, offsets);
-                HS_CUDA(cudaEventRecord(b->ev_a, b->stream));
-                st = batch_enqueue(b, xyz, n, sample_rate);
-                if (st != HS_OK) return st;
-                HS_CUDA(cudaEventRecord(b->ev_b, b->stream));
-                HS_CUDA(cudaStreamSynchronize(b->stream));
-                float ms = 0;
-                HS_CUDA(cudaEventElapsedTime(&ms, b->ev_a, b->ev_b));
-                ms_best = std::min(ms_best, ms);
-            }
-            ++tried;
-            if (ms_best < best) {
-                best = ms_best;
-                best_t = threads_opt[ti];
-                best_l = L;
-            }
-        }
-    b->bl = best_l;
-    b->threads = best_t;
-    st = batch_reset(b);                              // tuning runs touched the counters
-    if (st != HS_OK) return st;
-    HS_CUDA(cudaStreamSynchronize(b->stream));
-    out->threads = (uint32_t)best_t;
-    out->slot = best_l.slot;
-    out->configs_tried = (uint32_t)tried;
-    out->best_ms = best;
-    return HS_OK;
-}
-
-}  // extern "C"
-
-// ---------------------------------------------------------------------------
-// Learned router: MLP objects, exact counting, and the learned sketch.
-// ---------------------------------------------------------------------------
-
-struct hs_mlp {
-    float *P = nullptr, *M = nullptr, *V = nullptr, *grad = nullptr, *loss = nullptr;
-    int step = 0;
-    cudaStream_t stream = nullptr;
-    int device = 0;
-};
-
-struct hs_exact {
-    SketchDesc d{};
-    cudaStream_t stream = nullptr;
-    int device = 0, num_sms = 0;
-    uint64_t slots = 0;
-    uint32_t key_bits = 1;
-    unsigned long long *keys = nullptr;   // all ones = empty
-    int32_t *counts = nullptr;
-    uint32_t *overflow = nullptr;
-    unsigned long long *ctr = nullptr;    // [0] listed entries, [1] taken entries
-    SelectState *sel = nullptr;
-    unsigned long long *hist = nullptr;
-    uint64_t *tmp_key = nullptr, *out_key = nullptr;
-    int32_t *tmp_est = nullptr, *out_est = nullptr;
-    uint32_t *tmp_rank = nullptr;
-    uint64_t out_cap = 0;
-};
-
-struct hs_learned {
-    hs_sketch *sk = nullptr;       // the sketch of the cells that are not routed
-    uint32_t R = 10, Gc = 0;
-    uint64_t ncoarse = 0, words = 0;
-    uint32_t coarse_key_bits = 1;
-    uint64_t feature_seed = 0;
-    double feature_rate = 1.0 / 64;
-    uint64_t n_sampled = 0;        // particles passed to learned_sample since the last route
-    int32_t *coarse = nullptr;     // Gc^3 sample counts
-    uint64_t *clist = nullptr;     // coarse cells with a sample
-    uint64_t clist_cap = 0, n_list = 0, n_routed = 0;
-    uint16_t *feats = nullptr;
-    float *logits = nullptr;
-    int32_t *lrank = nullptr;      // routing rank of each listed cell
-    uint32_t *routed = nullptr;    // Gc^3 bits
-    uint32_t *prefix = nullptr;    // routed cells before each bitmap word
-    uint32_t *scan_scratch = nullptr;
-    uint64_t max_blocks = 0;       // routing budget: dense blocks of R^3 counters
-    int32_t *blocks = nullptr;
-    uint64_t *rlist = nullptr;     // coarse key of each block
-    unsigned long long *ctr = nullptr;   // [0] list length, [1] positive logits, [2] table entries
-    uint16_t *ftab = nullptr;      // bf16(log10(1 + n)) for n < kFeatTab
-};
-
-namespace {
-
-constexpr uint32_t kFeatTab = 65536;
-
-// float -> bf16 bits, round to nearest, ties to even (finite inputs)
-uint16_t host_bf16(float f) {
-    uint32_t u;
-    std::memcpy(&u, &f, 4);
-    u += 0x7FFFu + ((u >> 16) & 1u);
-    return (uint16_t)(u >> 16);
-}
-
-bool host_is_device(const void *p) { return is_device_ptr(p); }
-
-// device copy of a host-or-device input (tmp is freed by the caller)
-template <typename T>
-hs_status device_input(const T *src, uint64_t count, cudaStream_t s, const T **dst, T **tmp) {
-    *tmp = nullptr;
-    if (host_is_device(src)) {
-        *dst = src;
-        return HS_OK;
-    }
-    HS_CUDA(cudaMalloc(tmp, std::max<uint64_t>(count, 1) * sizeof(T)));
-    HS_CUDA(cudaMemcpyAsync(*tmp, src, count * sizeof(T), cudaMemcpyHostToDevice, s));
-    *dst = *tmp;
-    return HS_OK;
-}
-
-void learned_free(hs_learned *L) {
-    void *ps[] = {L->coarse, L->clist,  L->feats,        L->logits, L->lrank, L->routed,
-                  L->prefix, L->scan_scratch, L->blocks, L->rlist, L->ctr,   L->ftab};
-    for (void *q : ps)
-        if (q) cudaFree(q);
-}
-
-}  // namespace
-
-extern "C" {
-
-hs_status mlp_destroy(hs_mlp *m) {
-    if (!m) return HS_OK;
-    void *ps[] = {m->P, m->M, m->V, m->grad, m->loss};
-    for (void *q : ps)
-        if (q) cudaFree(q);
-    delete m;
-    return HS_OK;
-}
-
-hs_status mlp_create(uint64_t seed, void *cuda_stream, hs_mlp **out) {
-    if (!out) return fail(HS_ERR_ARG, "out is NULL");
-    hs_mlp *m = new (std::nothrow) hs_mlp();
-    if (!m) return fail(HS_ERR_OOM, "host allocation failed");
-    m->stream = (cudaStream_t)cuda_stream;
-    cudaError_t e = cudaGetDevice(&m->device);
-    for (float **q : {&m->P, &m->M, &m->V, &m->grad})
-        if (e == cudaSuccess) e = cudaMalloc(q, kMlpParams * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&m->loss, 2 * 4);
-    if (e != cudaSuccess) {
-        mlp_destroy(m);
-        return fail(HS_ERR_OOM, "mlp_create: %s", cudaGetErrorString(e));
-    }
-    // uniform(-sqrt(6/fan_in), +sqrt(6/fan_in)) weights from splitmix64, zero biases
-    std::vector<float> P(kMlpParams, 0.0f);
-    uint64_t g = 0;
-    auto uni = [&](double a) {
-        uint64_t x = splitmix64_at(seed, g++);
-        return (float)(((double)(x >> 11) * 0x1p-53 * 2.0 - 1.0) * a);
-    };
-    size_t o = 0;
-    for (int i = 0; i < kMlpH * kMlpIn; ++i) P[o++] = uni(std::sqrt(6.0 / kMlpIn));
-    o += kMlpH;
-    for (int i = 0; i < kMlpH * kMlpH; ++i) P[o++] = uni(std::sqrt(6.0 / kMlpH));
-    o += kMlpH;
-    for (int i = 0; i < kMlpH; ++i) P[o++] = uni(std::sqrt(6.0 / kMlpH));
-    e = cudaMemcpyAsync(m->P, P.data(), kMlpParams * 4, cudaMemcpyHostToDevice, m->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(m->M, 0, kMlpParams * 4, m->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(m->V, 0, kMlpParams * 4, m->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
-    if (e != cudaSuccess) {
-        mlp_destroy(m);
-        return fail(HS_ERR_CUDA, "mlp_create: %s", cudaGetErrorString(e));
-    }
-    *out = m;
-    return HS_OK;
-}
-
-hs_status mlp_set_params(hs_mlp *m, const float *params) {
-    if (!m || !params) return fail(HS_ERR_ARG, "NULL argument");
-    HS_CUDA(cudaMemcpyAsync(m->P, params, kMlpParams * 4, cudaMemcpyDefault, m->stream));
-    HS_CUDA(cudaMemsetAsync(m->M, 0, kMlpParams * 4, m->stream));
-    HS_CUDA(cudaMemsetAsync(m->V, 0, kMlpParams * 4, m->stream));
-    HS_CUDA(cudaStreamSynchronize(m->stream));
-    m->step = 0;
-    return HS_OK;
-}
-
-hs_status mlp_get_params(hs_mlp *m, float *params) {
-    if (!m || !params) return fail(HS_ERR_ARG, "NULL argument");
-    HS_CUDA(cudaMemcpyAsync(params, m->P, kMlpParams * 4, cudaMemcpyDefault, m->stream));
-    HS_CUDA(cudaStreamSynchronize(m->stream));
-    return HS_OK;
-}
-
-hs_status mlp_forward(hs_mlp *m, const uint16_t *feats, uint64_t n, float *logits) {
-    if (!m || (n && (!feats || !logits))) return fail(HS_ERR_ARG, "NULL argument");
-    if (n == 0) return HS_OK;
-    const uint16_t *df;
-    uint16_t *tf = nullptr;
-    hs_status st = device_input(feats, n * kMlpIn, m->stream, &df, &tf);
-    if (st != HS_OK) return st;
-    const bool ld = host_is_device(logits);
-    float *dl = logits;
-    if (!ld && cudaMalloc(&dl, n * 4) != cudaSuccess) {
-        if (tf) cudaFree(tf);
-        return fail(HS_ERR_OOM, "mlp_forward: no memory for logits");
-    }
-    cudaError_t e = launch_mlp_forward(m->P, df, n, dl, m->stream);
-    if (e == cudaSuccess && !ld) e = cudaMemcpyAsync(logits, dl, n * 4, cudaMemcpyDeviceToHost, m->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
-    if (tf) cudaFree(tf);
-    if (!ld) cudaFree(dl);
-    if (e != cudaSuccess) return fail(HS_ERR_CUDA, "mlp_forward: %s", cudaGetErrorString(e));
-    return HS_OK;
-}
-
-static hs_status mlp_grad_common(hs_mlp *m, const uint16_t *feats, const float *y, const float *w,
-                                 uint64_t n) {
-    const uint16_t *df;
-    const float *dy, *dw;
-    uint16_t *tf = nullptr;
-    float *ty = nullptr, *tw = nullptr;
-    hs_status st = device_input(feats, n * kMlpIn, m->stream, &df, &tf);
-    if (st == HS_OK) st = device_input(y, n, m->stream, &dy, &ty);
-    if (st == HS_OK) st = device_input(w, n, m->stream, &dw, &tw);
-    cudaError_t e = st == HS_OK ? launch_mlp_grad(m->P, df, dy, dw, n, m->grad, m->loss, m->stream)
-                                : cudaSuccess;
-    if (tf || ty || tw) cudaStreamSynchronize(m->stream);
-    if (tf) cudaFree(tf);
-    if (ty) cudaFree(ty);
-    if (tw) cudaFree(tw);
-    if (st != HS_OK) return st;
-    HS_CUDA(e);
-    return HS_OK;
-}
-
-hs_status mlp_gradient(hs_mlp *m, const uint16_t *feats, const float *y, const float *w, uint64_t n,
-                       float *grad, float *loss) {
-    if (!m || !feats || !y || !w || !grad || !loss || n == 0) return fail(HS_ERR_ARG, "bad argument");
-    hs_status st = mlp_grad_common(m, feats, y, w, n);
-    if (st != HS_OK) return st;
-    HS_CUDA(cudaMemcpyAsync(grad, m->grad, kMlpParams * 4, cudaMemcpyDefault, m->stream));
-    HS_CUDA(cudaMemcpyAsync(loss, m->loss, 4, cudaMemcpyDefault, m->stream));
-    HS_CUDA(cudaStreamSynchronize(m->stream));
-    return HS_OK;
-}
-
-hs_status mlp_train_step(hs_mlp *m, const uint16_t *feats, const float *y, const float *w,
-                         uint64_t n, float lr, float *loss) {
-    if (!m || !feats || !y || !w || n == 0 || !(lr > 0)) return fail(HS_ERR_ARG, "bad argument");
-    hs_status st = mlp_grad_common(m, feats, y, w, n);
-    if (st != HS_OK) return st;
-    m->step += 1;
-    HS_CUDA(launch_adam(m->P, m->M, m->V, m->grad, m->loss + 1, lr, m->step, m->stream));
-    if (loss) {
-        float l[2];
-        HS_CUDA(cudaMemcpyAsync(l, m->loss, 8, cudaMemcpyDeviceToHost, m->stream));
-        HS_CUDA(cudaStreamSynchronize(m->stream));
-        *loss = l[1] > 0 ? l[0] / l[1] : 0.0f;
-    }
-    return HS_OK;
-}
-
-hs_status exact_destroy(hs_exact *E) {
-    if (!E) return HS_OK;
-    void *ps[] = {E->keys, E->counts, E->overflow, E->ctr, E->sel, E->hist,
-                  E->tmp_key, E->tmp_est, E->out_key, E->out_est, E->tmp_rank};
-    for (void *q : ps)
-        if (q) cudaFree(q);
-    delete E;
-    return HS_OK;
-}
-
-hs_status exact_create(double box, double cell, uint32_t log2_slots, void *cuda_stream,
-                       hs_exact **out) {
-    if (!out || log2_slots < 4 || log2_slots > 34) return fail(HS_ERR_ARG, "bad argument");
-    hs_params p{1, 1, box, cell, 0, 0, 0, 0};
-    hs_status st = check_params(&p);
-    if (st != HS_OK) return st;
-    hs_exact *E = new (std::nothrow) hs_exact();
-    if (!E) return fail(HS_ERR_OOM, "host allocation failed");
-    E->stream = (cudaStream_t)cuda_stream;
-    E->d.G = (uint32_t)std::llround(box / cell);
-    E->d.inv_cell = (float)(1.0 / cell);
-    E->slots = 1ull << log2_slots;
-    const uint64_t cells = (uint64_t)E->d.G * E->d.G * E->d.G;
-    while (E->key_bits < 64 && (1ull << E->key_bits) < cells) ++E->key_bits;
-    cudaError_t e = cudaGetDevice(&E->device);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&E->num_sms, cudaDevAttrMultiProcessorCount, E->device);
-    if (e == cudaSuccess) e = cudaMalloc(&E->keys, E->slots * 8);
-    if (e == cudaSuccess) e = cudaMalloc(&E->counts, E->slots * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&E->overflow, 4);
-    if (e == cudaSuccess) e = cudaMalloc(&E->ctr, 2 * 8);
-    if (e == cudaSuccess) e = cudaMalloc(&E->sel, sizeof(SelectState));
-    if (e == cudaSuccess) e = cudaMalloc(&E->hist, 256 * sizeof(unsigned long long));
-    if (e != cudaSuccess) {
-        exact_destroy(E);
-        return fail(HS_ERR_OOM, "exact_create: %s", cudaGetErrorString(e));
-    }
-    st = exact_reset(E);
-    if (st != HS_OK) {
-        exact_destroy(E);
-        return st;
-    }
-    *out = E;
-    return HS_OK;
-}
-
-hs_status exact_reset(hs_exact *E) {
-    if (!E) return fail(HS_ERR_ARG, "NULL handle");
-    HS_CUDA(cudaMemsetAsync(E->keys, 0xFF, E->slots * 8, E->stream));
-    HS_CUDA(cudaMemsetAsync(E->counts, 0, E->slots * 4, E->stream));
-    HS_CUDA(cudaMemsetAsync(E->overflow, 0, 4, E->stream));
-    HS_CUDA(cudaStreamSynchronize(E->stream));
-    return HS_OK;
-}
-
-hs_status exact_add(hs_exact *E, const float *xyz, uint64_t n) {
-    if (!E || (n && !xyz)) return fail(HS_ERR_ARG, "bad argument");
-    if (n == 0) return HS_OK;
-    if (!is_device_ptr(xyz)) return fail(HS_ERR_ARG, "xyz must be device memory");
-    HS_CUDA(launch_exact_count(xyz, n, E->d, E->keys, E->counts, E->slots, E->overflow, E->stream));
-    return HS_OK;
-}
-
-static hs_status exact_check(hs_exact *E) {
-    uint32_t of = 0;
-    HS_CUDA(cudaMemcpyAsync(&of, E->overflow, 4, cudaMemcpyDeviceToHost, E->stream));
-    HS_CUDA(cudaStreamSynchronize(E->stream));
-    if (of) return fail(HS_ERR_TABLE_FULL, "exact table: a key found no free slot in %d probes",
-                        kTableProbes);
-    return HS_OK;
-}
-
-hs_status exact_list(hs_exact *E, uint64_t *keys, int32_t *counts, uint64_t cap, uint64_t *n_out) {
-    if (!E || !n_out || (cap && (!keys || !counts))) return fail(HS_ERR_ARG, "bad argument");
-    hs_status st = exact_check(E);
-    if (st != HS_OK) return st;
-    cudaStream_t s = E->stream;
-    const bool dev = cap && is_device_ptr(keys) && is_device_ptr(counts);
-    uint64_t *dk = dev ? keys : nullptr;
-    int32_t *dc = dev ? counts : nullptr;
-    cudaError_t e = cudaSuccess;
-    if (cap && !dev) {
-        e = cudaMalloc(&dk, cap * 8);
-        if (e == cudaSuccess) e = cudaMalloc(&dc, cap * 4);
-    }
-    if (e == cudaSuccess) e = cudaMemsetAsync(E->ctr, 0, 8, s);
-    if (e == cudaSuccess) e = launch_table_list(E->keys, E->counts, E->slots, dk, dc, E->ctr, cap, s);
-    unsigned long long nn = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&nn, E->ctr, 8, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    const uint64_t m = std::min<uint64_t>(nn, cap);
-    if (e == cudaSuccess && m && !dev) {
-        e = cudaMemcpy(keys, dk, m * 8, cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess) e = cudaMemcpy(counts, dc, m * 4, cudaMemcpyDeviceToHost);
-    }
-    if (!dev) {
-        if (dk) cudaFree(dk);
-        if (dc) cudaFree(dc);
-    }
-    if (e != cudaSuccess) return fail(HS_ERR_CUDA, "exact_list: %s", cudaGetErrorString(e));
-    *n_out = nn;
-    return HS_OK;
-}
-
-hs_status exact_topk(hs_exact *E, uint32_t k, uint64_t *keys, int32_t *counts, uint32_t *n_out) {
-    if (!E || !n_out || (k && (!keys || !counts))) return fail(HS_ERR_ARG, "bad argument");
-    uint64_t D = 0;
-    hs_status st = exact_list(E, nullptr, nullptr, 0, &D);
-    if (st != HS_OK) return st;
-    const uint64_t kk = std::min<uint64_t>(k, D);
-    *n_out = 0;
-    if (kk == 0) return HS_OK;
-    if (E->out_cap < kk) {
-        void *ps[] = {E->tmp_key, E->tmp_est, E->out_key, E->out_est, E->tmp_rank};
-        for (void *q : ps)
-            if (q) cudaFree(q);
-        E->tmp_key = E->out_key = nullptr;
-        E->tmp_est = E->out_est = nullptr;
-        E->tmp_rank = nullptr;
-        E->out_cap = 0;
-        HS_CUDA(cudaMalloc(&E->tmp_key, kk * 8));
-        HS_CUDA(cudaMalloc(&E->tmp_est, kk * 4));
-        HS_CUDA(cudaMalloc(&E->tmp_rank, kk * 4));
-        HS_CUDA(cudaMalloc(&E->out_key, kk * 8));
-        HS_CUDA(cudaMalloc(&E->out_est, kk * 4));
-        E->out_cap = kk;
-    }
-    // Rank every slot: empty slots carry count 0 and so rank below the kk-th
-    // occupied one (its count is >= 1 because kk <= D).
-    int launches = 0;
-    const uint64_t *tk = reinterpret_cast<const uint64_t *>(E->keys);
-    HS_CUDA(launch_select_kth(tk, E->counts, E->slots, kk, E->key_bits, E->sel, E->hist,
-                              E->num_sms * 4, E->stream, &launches));
-    HS_CUDA(launch_take_sorted(tk, E->counts, E->slots, E->sel, 0, E->tmp_key, E->tmp_est,
-                               &E->ctr[1], E->tmp_rank, kk, E->out_key, E->out_est, E->num_sms * 4, E->stream,
-                               &launches));
-    HS_CUDA(cudaMemcpyAsync(keys, E->out_key, kk * 8, cudaMemcpyDefault, E->stream));
-    HS_CUDA(cudaMemcpyAsync(counts, E->out_est, kk * 4, cudaMemcpyDefault, E->stream));
-    HS_CUDA(cudaStreamSynchronize(E->stream));
-    *n_out = (uint32_t)kk;
-    return HS_OK;
-}
-
-hs_status exact_query(hs_exact *E, const uint64_t *keys, uint64_t m, int32_t *counts) {
-    if (!E || (m && (!keys || !counts))) return fail(HS_ERR_ARG, "bad argument");
-    if (m == 0) return HS_OK;
-    hs_status st = exact_check(E);
-    if (st != HS_OK) return st;
-    const uint64_t *dk;
-    uint64_t *tk = nullptr;
-    st = device_input(keys, m, E->stream, &dk, &tk);
-    if (st != HS_OK) return st;
-    const bool dev_out = is_device_ptr(counts);
-    int32_t *dc = counts;
-    cudaError_t e = cudaSuccess;
-    if (!dev_out) e = cudaMalloc(&dc, m * 4);
-    if (e == cudaSuccess) e = launch_exact_query(E->keys, E->counts, E->slots, dk, m, dc, E->stream);
-    if (e == cudaSuccess && !dev_out)
-        e = cudaMemcpyAsync(counts, dc, m * 4, cudaMemcpyDeviceToHost, E->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(E->stream);
-    if (tk) cudaFree(tk);
-    if (!dev_out && dc) cudaFree(dc);
-    if (e != cudaSuccess) return fail(HS_ERR_CUDA, "exact_query: %s", cudaGetErrorString(e));
-    return HS_OK;
-}
-
-hs_status exact_counts(const float *xyz, uint64_t n, double box, double cell, uint32_t log2_slots,
-                       void *cuda_stream, uint64_t *keys, int32_t *counts, uint64_t cap,
-                       uint64_t *n_out) {
-    if (!n_out || (n && !xyz)) return fail(HS_ERR_ARG, "bad argument");
-    hs_exact *E = nullptr;
-    hs_status st = exact_create(box, cell, log2_slots, cuda_stream, &E);
-    if (st == HS_OK) st = exact_add(E, xyz, n);
-    if (st == HS_OK) st = exact_list(E, keys, counts, keys ? cap : 0, n_out);
-    exact_destroy(E);
-    return st;
-}
-
-hs_status learned_destroy(hs_learned *L) {
-    if (!L) return HS_OK;
-    if (L->sk) sketch_destroy(L->sk);
-    learned_free(L);
-    delete L;
-    return HS_OK;
-}
-
-hs_status learned_create(const hs_params *params, uint32_t coarse_factor, uint32_t table_log2,
-                         uint64_t feature_seed, double feature_rate, void *cuda_stream,
-                         hs_learned **out) {
-    if (!out || !params) return fail(HS_ERR_ARG, "NULL argument");
-    if (coarse_factor < 1 || coarse_factor > 64 || table_log2 < 4 || table_log2 > 32 ||
-        !(feature_rate > 0 && feature_rate <= 1))
-        return fail(HS_ERR_ARG, "bad coarse factor, table size or feature rate");
-    const uint64_t R3 = (uint64_t)coarse_factor * coarse_factor * coarse_factor;
-    const uint64_t max_blocks = (3ull << table_log2) / R3;   // 12-byte slots -> 4-byte counters
-    if (max_blocks == 0) return fail(HS_ERR_ARG, "the table holds no block of R^3 counters");
-    hs_sketch *sk = nullptr;
-    hs_status st = sketch_create(params, cuda_stream, &sk);
-    if (st != HS_OK) return st;
-    if (sk->d.G % coarse_factor != 0 || sk->d.G > 65535 || sk->bl.slot == 0) {
-        sketch_destroy(sk);
-        return fail(HS_ERR_ARG, "the mesh must be a multiple of the coarse factor, below 2^16, "
-                    "and the sketch must allow the binned update");
-    }
-    hs_learned *L = new (std::nothrow) hs_learned();
-    if (!L) {
-        sketch_destroy(sk);
-        return fail(HS_ERR_OOM, "host allocation failed");
-    }
-    L->sk = sk;
-    L->R = coarse_factor;
-    L->Gc = sk->d.G / coarse_factor;
-    L->ncoarse = (uint64_t)L->Gc * L->Gc * L->Gc;
-    L->words = (L->ncoarse + 31) / 32;
-    while (L->coarse_key_bits < 64 && (1ull << L->coarse_key_bits) < L->ncoarse) ++L->coarse_key_bits;
-    L->feature_seed = feature_seed;
-    L->feature_rate = feature_rate;
-    L->max_blocks = max_blocks;
-    cudaStream_t s = sk->stream;
-    cudaError_t e = cudaMalloc(&L->coarse, L->ncoarse * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&L->routed, L->words * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&L->prefix, L->words * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&L->scan_scratch, (L->words / 1024 + 4096) * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&L->blocks, max_blocks * R3 * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&L->rlist, max_blocks * 8);
-    if (e == cudaSuccess) e = cudaMalloc(&L->ctr, 4 * 8);
-    if (e == cudaSuccess) e = cudaMalloc(&L->ftab, kFeatTab * 2);
-    if (e == cudaSuccess) {
-        std::vector<uint16_t> t(kFeatTab);
-        for (uint32_t c = 0; c < kFeatTab; ++c)
-            t[c] = host_bf16((float)std::log10(1.0 + (double)c));   // double -> float -> bf16
-        e = cudaMemcpy(L->ftab, t.data(), kFeatTab * 2, cudaMemcpyHostToDevice);
-    }
-    if (e == cudaSuccess) e = cudaMemsetAsync(L->routed, 0, L->words * 4, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(L->prefix, 0, L->words * 4, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(L->blocks, 0, max_blocks * R3 * 4, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) {
-        learned_destroy(L);
-        return fail(HS_ERR_OOM, "learned_create: %s", cudaGetErrorString(e));
-    }
-    sk->route.filter = RouteFilter{L->routed, (uint32_t)((0x100000000ull + coarse_factor - 1) / coarse_factor),
-                                   L->Gc, coarse_factor};
-    sk->route.prefix = L->prefix;
-    sk->route.blocks = L->blocks;
-    sk->min_cap = max_blocks * R3;
-    *out = L;
-    return HS_OK;
-}
-
-hs_status learned_capacity(hs_learned *L, uint64_t *max_routed, uint64_t *table_bytes) {
-    if (!L) return fail(HS_ERR_ARG, "NULL handle");
-    if (max_routed) *max_routed = L->max_blocks;
-    if (table_bytes) *table_bytes = L->max_blocks * L->R * L->R * L->R * 4;
-    return HS_OK;
-}
-
-hs_status learned_sample(hs_learned *L, const float *xyz, uint64_t n) {
-    if (!L || (n && !xyz)) return fail(HS_ERR_ARG, "NULL argument");
-    hs_sketch *sk = L->sk;
-    cudaStream_t s = sk->stream;
-    if (L->n_sampled == 0) HS_CUDA(cudaMemsetAsync(L->coarse, 0, L->ncoarse * 4, s));
-    if (n == 0) return HS_OK;
-    if (is_device_ptr(xyz)) {
-        HS_CUDA(launch_coarse_hist(xyz, n, L->n_sampled, sk->d, L->R, L->Gc, L->feature_seed,
-                                   L->feature_rate, L->coarse, s));
-        sk->stats.kernel_launches += 1;
-    } else {   // through the sketch's staging buffers, as sketch_update does
-        hs_status st = ensure_staging(sk);
-        if (st != HS_OK) return st;
-        int i = 0;
-        for (uint64_t off = 0; off < n; off += kStageParticles, ++i) {
-            const uint64_t cnt = std::min(kStageParticles, n - off);
-            const int b = i % kStageBuffers;
-            HS_CUDA(cudaStreamWaitEvent(sk->copy_stream, sk->ev_free[b], 0));
-            HS_CUDA(cudaMemcpyAsync(sk->stage[b], xyz + 3 * off, cnt * 12, cudaMemcpyHostToDevice,
-                                    sk->copy_stream));
-            HS_CUDA(cudaEventRecord(sk->ev_copied[b], sk->copy_stream));
-            HS_CUDA(cudaStreamWaitEvent(s, sk->ev_copied[b], 0));
-            HS_CUDA(launch_coarse_hist(sk->stage[b], cnt, L->n_sampled + off, sk->d, L->R, L->Gc,
-                                       L->feature_seed, L->feature_rate, L->coarse, s));
-            HS_CUDA(cudaEventRecord(sk->ev_free[b], s));
-            sk->stats.kernel_launches += 1;
-        }
-    }
-    L->n_sampled += n;
-    return HS_OK;
-}
-
-hs_status learned_route(hs_learned *L, hs_mlp *mlp, uint64_t *n_routed) {
-    if (!L || !mlp) return fail(HS_ERR_ARG, "NULL argument");
-    hs_sketch *sk = L->sk;
-    cudaStream_t s = sk->stream;
-    int launches = 0;
-    if (L->n_sampled == 0) HS_CUDA(cudaMemsetAsync(L->coarse, 0, L->ncoarse * 4, s));
-    L->n_sampled = 0;                     // the next learned_sample starts a new histogram
-    HS_CUDA(cudaMemsetAsync(L->ctr, 0, 4 * 8, s));
-    // list the coarse cells with a sample (size known only on the device: count first)
-    HS_CUDA(launch_coarse_list(L->coarse, L->ncoarse, nullptr, &L->ctr[0], 0, s));
-    unsigned long long nl = 0;
-    HS_CUDA(cudaMemcpyAsync(&nl, &L->ctr[0], 8, cudaMemcpyDeviceToHost, s));
-    HS_CUDA(cudaStreamSynchronize(s));
-    if (nl > L->clist_cap) {
-        void *old[] = {L->clist, L->feats, L->logits, L->lrank};
-        for (void *q : old)
-            if (q) cudaFree(q);
-        L->clist = nullptr;
-        L->feats = nullptr;
-        L->logits = nullptr;
-        L->lrank = nullptr;
-        L->clist_cap = std::max<uint64_t>(nl, 1024);
-        HS_CUDA(cudaMalloc(&L->clist, L->clist_cap * 8));
-        HS_CUDA(cudaMalloc(&L->feats, L->clist_cap * kMlpIn * 2));
-        HS_CUDA(cudaMalloc(&L->logits, L->clist_cap * 4));
-        HS_CUDA(cudaMalloc(&L->lrank, L->clist_cap * 4));
-    }
-    HS_CUDA(cudaMemsetAsync(&L->ctr[0], 0, 8, s));
-    HS_CUDA(launch_coarse_list(L->coarse, L->ncoarse, L->clist, &L->ctr[0], L->clist_cap, s));
-    HS_CUDA(launch_features(L->coarse, L->Gc, L->clist, nl, L->ftab, kFeatTab, L->feats, s));
-    HS_CUDA(launch_mlp_forward(mlp->P, L->feats, nl, L->logits, s));
-    HS_CUDA(launch_logit_rank(L->logits, nl, L->lrank, &L->ctr[1], s));
-    unsigned long long npos = 0;
-    HS_CUDA(cudaMemcpyAsync(&npos, &L->ctr[1], 8, cudaMemcpyDeviceToHost, s));
-    HS_CUDA(cudaStreamSynchronize(s));
-    launches += 5;
-    // over budget: keep the max_blocks cells of largest logit (ties: smaller key)
-    const int use_sel = npos > L->max_blocks;
-    if (use_sel) {
-        hs_status st = ensure_topk_scratch(sk, 1);
-        if (st != HS_OK) return st;
-        HS_CUDA(launch_select_kth(L->clist, L->lrank, nl, L->max_blocks, L->coarse_key_bits,
-                                  sk->sel, sk->hist, sk->num_sms * 4, s, &launches));
-    }
-    HS_CUDA(cudaMemsetAsync(L->routed, 0, L->words * 4, s));
-    HS_CUDA(launch_route(L->clist, L->lrank, nl, use_sel ? sk->sel : nullptr, use_sel, L->routed, s));
-    HS_CUDA(launch_word_popc(L->routed, L->words, L->prefix, s));
-    HS_CUDA(launch_exclusive_scan(L->prefix, L->prefix, L->words, L->scan_scratch, s, &launches));
-    HS_CUDA(launch_route_list(L->clist, nl, L->routed, L->prefix, L->rlist, s));
-    const uint64_t nr = use_sel ? L->max_blocks : npos;
-    const uint64_t R3 = (uint64_t)L->R * L->R * L->R;
-    HS_CUDA(cudaMemsetAsync(L->blocks, 0, L->max_blocks * R3 * 4, s));
-    HS_CUDA(cudaStreamSynchronize(s));
-    launches += 3;
-    sk->stats.kernel_launches += launches;
-    L->n_list = nl;
-    L->n_routed = nr;
-    sk->routing = true;
-    if (n_routed) *n_routed = nr;
-    return HS_OK;
-}
-
-hs_status learned_prepare(hs_learned *L, const float *xyz, uint64_t n, hs_mlp *mlp,
-                          uint64_t *n_routed) {
-    if (!L || !mlp || (n && !xyz)) return fail(HS_ERR_ARG, "NULL argument");
-    L->n_sampled = 0;
-    hs_status st = learned_sample(L, xyz, n);
-    if (st != HS_OK) return st;
-    return learned_route(L, mlp, n_routed);
-}
-
-hs_status learned_update(hs_learned *L, const float *xyz, uint64_t n, double sample_rate) {
-    if (!L) return fail(HS_ERR_ARG, "NULL handle");
-    if (!L->sk->routing) return fail(HS_ERR_STATE, "call learned_prepare first");
-    return sketch_update(L->sk, xyz, n, sample_rate);
-}
-
-hs_status learned_topk(hs_learned *L, uint32_t k, uint64_t *keys, int32_t *est, uint32_t *n_out) {
-    if (!L || k == 0 || !keys || !est || !n_out) return fail(HS_ERR_ARG, "bad argument");
-    hs_sketch *h = L->sk;
-    uint32_t n1 = 0;
-    hs_status st = topk_extract(h, k, keys, est, &n1);   // leaves the ranking in h->out_*
-    if (st != HS_OK) return st;
-    // candidates: the sketch's ranking, then every non-zero exact counter
-    HS_CUDA(cudaMemcpyAsync(h->cand_key, h->out_key, n1 * 8, cudaMemcpyDeviceToDevice, h->stream));
-    HS_CUDA(cudaMemcpyAsync(h->cand_est, h->out_est, n1 * 4, cudaMemcpyDeviceToDevice, h->stream));
-    HS_CUDA(cudaMemsetAsync(&L->ctr[2], 0, 8, h->stream));
-    HS_CUDA(launch_block_list(L->blocks, L->rlist, L->n_routed, L->R, L->Gc, h->d.G,
-                              h->cand_key + n1, h->cand_est + n1, &L->ctr[2], h->cap - n1,
-                              h->stream));
-    unsigned long long nt = 0;
-    HS_CUDA(cudaMemcpyAsync(&nt, &L->ctr[2], 8, cudaMemcpyDeviceToHost, h->stream));
-    HS_CUDA(cudaStreamSynchronize(h->stream));
-    h->stats.kernel_launches += 1;
-    if (nt > h->cap - n1) return fail(HS_ERR_STATE, "too many exact counts for the candidates");
-    const uint64_t m = n1 + nt;
-    const uint64_t kk = std::min<uint64_t>(k, m);
-    if (m == 0) {
-        *n_out = 0;
-        return HS_OK;
-    }
-    st = finalize(h, m, kk);
-    if (st != HS_OK) return st;
-    HS_CUDA(cudaMemcpyAsync(keys, h->out_key, kk * 8, cudaMemcpyDeviceToHost, h->stream));
-    HS_CUDA(cudaMemcpyAsync(est, h->out_est, kk * 4, cudaMemcpyDeviceToHost, h->stream));
-    HS_CUDA(cudaStreamSynchronize(h->stream));
-    *n_out = (uint32_t)kk;
-    return HS_OK;
-}
-
-hs_status learned_table(hs_learned *L, uint64_t *keys, int32_t *counts, uint64_t cap,
-                        uint64_t *n_out) {
-    if (!L || !n_out || (cap && (!keys || !counts))) return fail(HS_ERR_ARG, "bad argument");
-    cudaStream_t s = L->sk->stream;
-    hs_status st = drain(L->sk);
-    if (st != HS_OK) return st;
-    uint64_t *dk = nullptr;
-    int32_t *dc = nullptr;
-    if (cap) {
-        HS_CUDA(cudaMalloc(&dk, cap * 8));
-        HS_CUDA(cudaMalloc(&dc, cap * 4));
-    }
-    HS_CUDA(cudaMemsetAsync(&L->ctr[2], 0, 8, s));
-    HS_CUDA(launch_block_list(L->blocks, L->rlist, L->n_routed, L->R, L->Gc, L->sk->d.G, dk, dc,
-                              &L->ctr[2], cap, s));
-    unsigned long long nt = 0;
-    HS_CUDA(cudaMemcpyAsync(&nt, &L->ctr[2], 8, cudaMemcpyDeviceToHost, s));
-    HS_CUDA(cudaStreamSynchronize(s));
-    uint64_t m = std::min<uint64_t>(nt, cap);
-    cudaError_t e = cudaSuccess;
-    if (m) {
-        e = cudaMemcpy(keys, dk, m * 8, cudaMemcpyDefault);
-        if (e == cudaSuccess) e = cudaMemcpy(counts, dc, m * 4, cudaMemcpyDefault);
-    }
-    if (dk) cudaFree(dk);
-    if (dc) cudaFree(dc);
-    if (e != cudaSuccess) return fail(HS_ERR_CUDA, "learned_table: %s", cudaGetErrorString(e));
-    *n_out = nt;
-    return HS_OK;
-}
-
-hs_status learned_routed(hs_learned *L, uint64_t *coarse_keys, uint64_t cap, uint64_t *n_out) {
-    if (!L || !n_out || (cap && !coarse_keys)) return fail(HS_ERR_ARG, "bad argument");
-    uint64_t m = std::min<uint64_t>(L->n_routed, cap);
-    if (m) HS_CUDA(cudaMemcpy(coarse_keys, L->rlist, m * 8, cudaMemcpyDefault));
-    *n_out = L->n_routed;
-    return HS_OK;
-}
-
-hs_status learned_logits(hs_learned *L, uint64_t *coarse_keys, float *logits, uint64_t cap,
-                         uint64_t *n_out) {
-    if (!L || !n_out) return fail(HS_ERR_ARG, "bad argument");
-    uint64_t m = std::min<uint64_t>(L->n_list, cap);
-    if (m) {
-        HS_CUDA(cudaMemcpy(coarse_keys, L->clist, m * 8, cudaMemcpyDefault));
-        HS_CUDA(cudaMemcpy(logits, L->logits, m * 4, cudaMemcpyDefault));
-    }
-    *n_out = L->n_list;
-    return HS_OK;
-}
-
-hs_status learned_coarse_counts(hs_learned *L, int32_t *out) {
-    if (!L || !out) return fail(HS_ERR_ARG, "bad argument");
-    HS_CUDA(cudaMemcpyAsync(out, L->coarse, L->ncoarse * 4, cudaMemcpyDefault, L->sk->stream));
-    HS_CUDA(cudaStreamSynchronize(L->sk->stream));
-    return HS_OK;
-}
-
-hs_status learned_features(hs_learned *L, uint16_t *feats, uint64_t cap, uint64_t *n_out) {
-    if (!L || !n_out) return fail(HS_ERR_ARG, "bad argument");
-    uint64_t m = std::min<uint64_t>(L->n_list, cap);
-    if (m) HS_CUDA(cudaMemcpy(feats, L->feats, m * kMlpIn * 2, cudaMemcpyDefault));
-    *n_out = L->n_list;
-    return HS_OK;
-}
-
-hs_status learned_sketch(hs_learned *L, hs_sketch **out) {
-    if (!L || !out) return fail(HS_ERR_ARG, "bad argument");
-    *out = L->sk;
-    return HS_OK;
-}
-
-hs_status learned_reset(hs_learned *L) {
-    if (!L) return fail(HS_ERR_ARG, "NULL handle");
-    hs_status st = sketch_reset(L->sk);
-    if (st != HS_OK) return st;
-    const uint64_t R3 = (uint64_t)L->R * L->R * L->R;
-    HS_CUDA(cudaMemsetAsync(L->blocks, 0, L->max_blocks * R3 * 4, L->sk->stream));
     return HS_OK;
 }
 

@@ -1,0 +1,490 @@
+// capi_batch.cu - batches of independent sub-volumes (batch_* of the C ABI).
+#include <atomic>
+#include <thread>
+
+#include "capi_internal.h"
+
+// ---------------------------------------------------------------------------
+// Batches of independent sub-volumes (each with its own mesh, stream index,
+// sketch and top-k), updated by one persistent scatter launch and one
+// accumulation launch, replayed as a CUDA graph.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr uint64_t kBatchProbe = 1ull << 16;   // probe keys per volume
+
+}  // namespace
+
+struct hs_batch {
+    hs_params p;
+    uint32_t nvol = 0;
+    SketchDesc d;                       // rows, log2 W, seeds
+    std::vector<uint32_t> G;
+    std::vector<float> inv;
+    std::vector<uint64_t> n_seen, probe_base;
+    int device = 0, num_sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int32_t *C = nullptr;               // nvol x rows x W
+    uint64_t *probe = nullptr;          // nvol x kBatchProbe
+    BinLayout bl{};                     // over nvol * rows rows
+    uint16_t *bins = nullptr;
+    uint32_t *cursor = nullptr;
+    uint32_t cap = 0;
+    VolumeDesc *d_vols = nullptr;
+    VolumeDesc *h_vols = nullptr;       // pinned: read by the graph's copy node
+    int threads = 1024;
+    hs_sketch *view = nullptr;          // views[0]
+    std::vector<hs_sketch *> views;     // top-k of one volume each, concurrently, own streams
+    std::vector<cudaEvent_t> vdone;     // each view's stream has finished
+    // directories of each volume's enumerated rows, kept across queries
+    std::vector<uint32_t *> vdir_off;
+    std::vector<DirRecord *> vdir_rec;
+    std::vector<uint32_t> vdir_G;
+    std::vector<uint64_t> vdir_cap;
+    cudaGraphExec_t gexec = nullptr;
+    const float *g_xyz = nullptr;
+    uint64_t g_n = 0;
+    double g_rate = -1;
+    cudaEvent_t done = nullptr;         // the last graph launch has finished with h_vols
+    cudaEvent_t fork = nullptr;         // the views' streams start after this
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+    hs_stats stats;
+};
+
+namespace {
+
+void batch_drop_graph(hs_batch *b) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    b->g_xyz = nullptr;
+}
+
+SketchDesc batch_flat_desc(const hs_batch *b) {
+    SketchDesc dd = b->d;
+    dd.rows = b->nvol * b->d.rows;      // the layout sees one sketch of nvol * t rows
+    return dd;
+}
+
+hs_status batch_ensure_bins(hs_batch *b, const uint64_t *offsets, double rate) {
+    if (b->bins) return HS_OK;
+    const double bins_per_row = (double)(1ull << (b->d.log2w - b->bl.S));
+    uint64_t most = 0;
+    for (uint32_t v = 0; v < b->nvol; ++v) most = std::max(most, offsets[v + 1] - offsets[v]);
+    uint64_t want = (uint64_t)(1.3 * (double)most * rate / bins_per_row) + 8192;
+    uint64_t cap = std::min<uint64_t>(want, kBinBudgetBytes / (2ull * b->bl.nbins));
+    cap = std::min<uint64_t>(std::max<uint64_t>(cap, 4096), 0xFFFFFFF0ull);
+    cap = (cap + 15) & ~15ull;
+    HS_CUDA(cudaMalloc(&b->bins, (size_t)b->bl.nbins * cap * 2));
+    b->cap = (uint32_t)cap;
+    return HS_OK;
+}
+
+// scatter + accumulate of the whole batch on b->stream (captured or direct)
+hs_status batch_enqueue(hs_batch *b, const float *xyz, uint64_t n, double rate) {
+    HS_CUDA(cudaMemcpyAsync(b->d_vols, b->h_vols, b->nvol * sizeof(VolumeDesc),
+                            cudaMemcpyHostToDevice, b->stream));
+    int grid = b->num_sms * (b->threads == 512 ? 2 : 1);
+    HS_CUDA(launch_bin_scatter(xyz, n, 0, b->d, b->C, rate, b->p.sample_seed, b->probe, 0,
+                               kBatchProbe, b->bl, b->bins, b->cursor, b->cap, grid, b->stream,
+                               b->d_vols, b->nvol, kBatchProbe, b->threads));
+    HS_CUDA(launch_bin_accumulate(b->bl, b->bins, b->cursor, b->cap, b->C, b->stream));
+    return HS_OK;
+}
+
+hs_status batch_check_offsets(const hs_batch *b, const float *xyz, const uint64_t *offsets) {
+    if (!offsets) return fail(HS_ERR_ARG, "offsets is NULL");
+    if (offsets[0] != 0) return fail(HS_ERR_ARG, "offsets[0] must be 0");
+    for (uint32_t v = 0; v < b->nvol; ++v)
+        if (offsets[v + 1] < offsets[v]) return fail(HS_ERR_ARG, "offsets must not decrease");
+    if (offsets[b->nvol] > 0) {
+        if (!xyz) return fail(HS_ERR_ARG, "xyz is NULL");
+        if (!is_device_ptr(xyz)) return fail(HS_ERR_ARG, "batch particles must be device memory");
+    }
+    return HS_OK;
+}
+
+void batch_fill_vols(hs_batch *b, const uint64_t *offsets) {
+    const uint32_t bins_per_row = 1u << (b->d.log2w - b->bl.S);
+    for (uint32_t v = 0; v < b->nvol; ++v) {
+        VolumeDesc &V = b->h_vols[v];
+        V.start = offsets[v];
+        V.g0 = b->n_seen[v];
+        V.probe_base = b->probe_base[v];
+        V.inv_cell = b->inv[v];
+        V.G = b->G[v];
+        V.bin0 = v * b->d.rows * bins_per_row;
+        V.pad = 0;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+hs_status batch_destroy(hs_batch *b);
+
+hs_status batch_create(const hs_params *params, uint32_t n_volumes, const double *boxes,
+                       void *cuda_stream, hs_batch **out) {
+    if (!out || !boxes || n_volumes == 0) return fail(HS_ERR_ARG, "NULL argument or no volumes");
+    if (!params) return fail(HS_ERR_ARG, "params is NULL");
+    hs_params p = *params;
+    p.box = boxes[0];
+    hs_status st = check_params(&p);
+    if (st != HS_OK) return st;
+    hs_batch *b = new (std::nothrow) hs_batch();
+    if (!b) return fail(HS_ERR_OOM, "host allocation failed");
+    b->p = p;
+    b->nvol = n_volumes;
+    std::memset(&b->stats, 0, sizeof(b->stats));
+    std::memset(&b->d, 0, sizeof(b->d));
+    b->d.rows = p.rows;
+    b->d.log2w = p.log2_width;
+    b->d.W = 1ull << p.log2_width;
+    for (uint32_t r = 0; r < p.rows; ++r) {
+        b->d.seed[r].a0 = splitmix64_at(p.hash_seed, 4 * r + 0);
+        b->d.seed[r].a1 = splitmix64_at(p.hash_seed, 4 * r + 1);
+        b->d.seed[r].a2 = splitmix64_at(p.hash_seed, 4 * r + 2);
+        b->d.seed[r].b = splitmix64_at(p.hash_seed, 4 * r + 3);
+    }
+    b->G.resize(n_volumes);
+    b->inv.assign(n_volumes, (float)(1.0 / p.cell));
+    b->n_seen.assign(n_volumes, 0);
+    b->probe_base.assign(n_volumes, 0);
+    for (uint32_t v = 0; v < n_volumes; ++v) {
+        double g = std::llround(boxes[v] / p.cell);
+        if (!(boxes[v] > 0) || g < 1 || g > 65535) {
+            delete b;
+            return fail(HS_ERR_ARG, "volume %u: grid round(box/cell) outside [1, 65535]", v);
+        }
+        b->G[v] = (uint32_t)g;
+    }
+    b->d.G = b->G[0];
+    b->d.inv_cell = b->inv[0];
+    b->d.Gq = b->d.G;
+    b->d.F = 1;
+    b->bl = bin_layout(batch_flat_desc(b), kBinSmemBudget);
+    if (b->bl.slot == 0 || b->bl.nbins >= 65536) {
+        delete b;
+        return fail(HS_ERR_ARG, "%u volumes x %u rows x 2^%u counters need too many bins; "
+                    "split the batch", n_volumes, p.rows, p.log2_width);
+    }
+    const size_t counters = (size_t)n_volumes * p.rows * b->d.W;
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (e == cudaSuccess) {
+        if (cuda_stream) b->stream = (cudaStream_t)cuda_stream;
+        else {
+            e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+            b->own_stream = true;
+        }
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&b->C, counters * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&b->probe, (size_t)n_volumes * kBatchProbe * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&b->cursor, (size_t)b->bl.nbins * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_vols, n_volumes * sizeof(VolumeDesc));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_vols, n_volumes * sizeof(VolumeDesc));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev_a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev_b);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->C, 0, counters * 4, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->probe, 0xFF, (size_t)n_volumes * kBatchProbe * 8, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->cursor, 0, (size_t)b->bl.nbins * 4, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    const uint32_t nviews = std::min<uint32_t>(n_volumes, kBatchViews);
+    for (uint32_t t = 0; t < nviews && e == cudaSuccess; ++t) {
+        hs_sketch *h = new (std::nothrow) hs_sketch();
+        if (!h) {
+            e = cudaErrorMemoryAllocation;
+            break;
+        }
+        h->p = p;
+        h->d = b->d;
+        h->is_view = true;
+        h->device = b->device;
+        h->num_sms = b->num_sms;
+        h->probe_cap = kBatchProbe;
+        h->bl = BinLayout{};        // views never bin
+        std::memset(&h->stats, 0, sizeof(h->stats));
+        b->views.push_back(h);
+        b->vdone.push_back(nullptr);
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->vdone.back(), cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMalloc(&h->flags, 4 * sizeof(uint32_t));
+    }
+    if (e == cudaSuccess) b->view = b->views[0];
+    if (e != cudaSuccess) {
+        hs_status code = e == cudaErrorMemoryAllocation ? HS_ERR_OOM : HS_ERR_CUDA;
+        batch_destroy(b);
+        return fail(code, "batch_create: %s", cudaGetErrorString(e));
+    }
+    *out = b;
+    return HS_OK;
+}
+
+hs_status batch_destroy(hs_batch *b) {
+    if (!b) return HS_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_drop_graph(b);
+    for (size_t t = 0; t < b->views.size(); ++t) {
+        hs_sketch *h = b->views[t];
+        h->C = nullptr;
+        h->probe = nullptr;
+        cudaStream_t vs = h->stream;
+        sketch_destroy(h);
+        if (vs) cudaStreamDestroy(vs);
+        if (b->vdone[t]) cudaEventDestroy(b->vdone[t]);
+    }
+    void *ps[] = {b->C, b->probe, b->cursor, b->d_vols, b->bins};
+    for (void *q : ps)
+        if (q) cudaFree(q);
+    for (auto *q : b->vdir_off)
+        if (q) cudaFree(q);
+    for (auto *q : b->vdir_rec)
+        if (q) cudaFree(q);
+    if (b->h_vols) cudaFreeHost(b->h_vols);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->ev_a) cudaEventDestroy(b->ev_a);
+    if (b->ev_b) cudaEventDestroy(b->ev_b);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    cudaGetLastError();
+    return HS_OK;
+}
+
+hs_status batch_update(hs_batch *b, const float *xyz, const uint64_t *offsets, double sample_rate) {
+    if (!b) return fail(HS_ERR_ARG, "batch is NULL");
+    if (!(sample_rate > 0.0 && sample_rate <= 1.0))
+        return fail(HS_ERR_ARG, "sample_rate=%g outside (0, 1]", sample_rate);
+    hs_status st = batch_check_offsets(b, xyz, offsets);
+    if (st != HS_OK) return st;
+    const uint64_t n = offsets[b->nvol];
+    if (n == 0) return HS_OK;
+    st = batch_ensure_bins(b, offsets, sample_rate);
+    if (st != HS_OK) return st;
+    HS_CUDA(cudaEventSynchronize(b->done));          // the previous graph has read h_vols
+    batch_fill_vols(b, offsets);
+    if (!b->gexec || b->g_xyz != xyz || b->g_n != n || b->g_rate != sample_rate) {
+        batch_drop_graph(b);
+        cudaGraph_t graph = nullptr;
+        HS_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed));
+        st = batch_enqueue(b, xyz, n, sample_rate);
+        cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+        if (st != HS_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        HS_CUDA(e);
+        e = cudaGraphInstantiate(&b->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        HS_CUDA(e);
+        b->g_xyz = xyz;
+        b->g_n = n;
+        b->g_rate = sample_rate;
+    }
+    HS_CUDA(cudaEventRecord(b->ev_a, b->stream));
+    HS_CUDA(cudaGraphLaunch(b->gexec, b->stream));
+    HS_CUDA(cudaEventRecord(b->ev_b, b->stream));
+    HS_CUDA(cudaEventRecord(b->done, b->stream));
+    b->stats.kernel_launches += 2;
+    b->stats.update_launches += 1;
+    for (uint32_t v = 0; v < b->nvol; ++v) b->n_seen[v] += offsets[v + 1] - offsets[v];
+    return HS_OK;
+}
+
+// Top-k of volume v on view h (the view borrows the volume's counters, probe
+// and directories, and returns the directories it built).
+static hs_status batch_topk_one(hs_batch *b, hs_sketch *h, uint32_t v, uint32_t F, uint32_t k,
+                                uint64_t *keys, int32_t *est, uint32_t *n_out) {
+    for (uint32_t r = 0; r < F; ++r) {
+        h->dir_off[r] = b->vdir_off[v * F + r];
+        h->dir_rec[r] = b->vdir_rec[v * F + r];
+        h->dir_G[r] = b->vdir_G[v * F + r];
+        h->dir_lines_cap[r] = b->vdir_cap[v * F + r];
+    }
+    h->C = b->C + (size_t)v * b->d.rows * b->d.W;
+    h->probe = b->probe + (size_t)v * kBatchProbe;
+    h->d.G = b->G[v];
+    h->d.Gq = b->G[v];
+    h->d.F = 1;
+    h->d.inv_cell = b->inv[v];
+    h->n_cells = (uint64_t)b->G[v] * b->G[v] * b->G[v];
+    h->key_bits = 1;
+    while (h->key_bits < 64 && (1ull << h->key_bits) < h->n_cells) ++h->key_bits;
+    h->n_seen = b->n_seen[v];
+    h->probe_base = b->probe_base[v];
+    hs_status st = topk_extract(h, k, keys + (size_t)v * k, est + (size_t)v * k, &n_out[v]);
+    for (uint32_t r = 0; r < F; ++r) {
+        b->vdir_off[v * F + r] = h->dir_off[r];
+        b->vdir_rec[v * F + r] = h->dir_rec[r];
+        b->vdir_G[v * F + r] = h->dir_G[r];
+        b->vdir_cap[v * F + r] = h->dir_lines_cap[r];
+        h->dir_off[r] = nullptr;
+        h->dir_rec[r] = nullptr;
+        h->dir_G[r] = 0;
+        h->dir_lines_cap[r] = 0;
+    }
+    return st;
+}
+
+hs_status batch_topk(hs_batch *b, uint32_t k, uint64_t *keys, int32_t *est, uint32_t *n_out) {
+    if (!b) return fail(HS_ERR_ARG, "batch is NULL");
+    if (k == 0 || !keys || !est || !n_out) return fail(HS_ERR_ARG, "k == 0 or NULL output");
+    const uint32_t F = enum_rows(b->view);
+    if (b->vdir_off.size() != (size_t)b->nvol * F) {
+        b->vdir_off.assign((size_t)b->nvol * F, nullptr);
+        b->vdir_rec.assign((size_t)b->nvol * F, nullptr);
+        b->vdir_G.assign((size_t)b->nvol * F, 0);
+        b->vdir_cap.assign((size_t)b->nvol * F, 0);
+    }
+    // the views start after the batch's pending work; the batch resumes after theirs
+    HS_CUDA(cudaEventRecord(b->fork, b->stream));
+    for (hs_sketch *h : b->views) HS_CUDA(cudaStreamWaitEvent(h->stream, b->fork, 0));
+    // each host thread drives one view over volumes taken from a shared counter
+    std::atomic<uint32_t> next{0};
+    std::vector<hs_status> status(b->views.size(), HS_OK);
+    std::vector<std::string> msg(b->views.size());
+    auto work = [&](size_t t) {
+        cudaSetDevice(b->device);
+        for (uint32_t v = next.fetch_add(1); v < b->nvol; v = next.fetch_add(1)) {
+            hs_status st = batch_topk_one(b, b->views[t], v, F, k, keys, est, n_out);
+            if (st != HS_OK) {
+                status[t] = st;
+                msg[t] = hs_last_error();
+                next.store(b->nvol);
+                break;
+            }
+        }
+    };
+    std::vector<std::thread> pool;
+    for (size_t t = 1; t < b->views.size(); ++t) pool.emplace_back(work, t);
+    work(0);
+    for (auto &th : pool) th.join();
+    for (size_t t = 0; t < b->views.size(); ++t) {
+        HS_CUDA(cudaEventRecord(b->vdone[t], b->views[t]->stream));
+        HS_CUDA(cudaStreamWaitEvent(b->stream, b->vdone[t], 0));
+    }
+    for (size_t t = 0; t < b->views.size(); ++t)
+        if (status[t] != HS_OK) return fail(status[t], "%s", msg[t].c_str());
+    return HS_OK;
+}
+
+hs_status batch_counters(hs_batch *b, uint32_t volume, int32_t *out) {
+    if (!b || !out || volume >= (b ? b->nvol : 0)) return fail(HS_ERR_ARG, "bad argument");
+    const size_t per = (size_t)b->d.rows * b->d.W;
+    HS_CUDA(cudaMemcpyAsync(out, b->C + volume * per, per * 4, cudaMemcpyDefault, b->stream));
+    HS_CUDA(cudaStreamSynchronize(b->stream));
+    return HS_OK;
+}
+
+hs_status batch_reset(hs_batch *b) {
+    if (!b) return fail(HS_ERR_ARG, "batch is NULL");
+    HS_CUDA(cudaMemsetAsync(b->C, 0, (size_t)b->nvol * b->d.rows * b->d.W * 4, b->stream));
+    HS_CUDA(cudaMemsetAsync(b->probe, 0xFF, (size_t)b->nvol * kBatchProbe * 8, b->stream));
+    HS_CUDA(cudaMemsetAsync(b->cursor, 0, (size_t)b->bl.nbins * 4, b->stream));
+    std::fill(b->n_seen.begin(), b->n_seen.end(), 0);
+    std::fill(b->probe_base.begin(), b->probe_base.end(), 0);
+    return HS_OK;
+}
+
+hs_status batch_volume_info(const hs_batch *b, uint32_t volume, hs_info *out) {
+    if (!b || !out || volume >= b->nvol) return fail(HS_ERR_ARG, "bad argument");
+    out->rows = b->d.rows;
+    out->log2_width = b->d.log2w;
+    out->grid = b->G[volume];
+    out->inv_cell = b->inv[volume];
+    out->width = b->d.W;
+    out->n_cells = (uint64_t)b->G[volume] * b->G[volume] * b->G[volume];
+    out->n_seen = b->n_seen[volume];
+    return HS_OK;
+}
+
+hs_status batch_stats(hs_batch *b, hs_stats *out, int reset) {
+    if (!b || !out) return fail(HS_ERR_ARG, "NULL argument");
+    HS_CUDA(cudaStreamSynchronize(b->stream));
+    float ms = 0;
+    if (b->stats.update_launches && cudaEventElapsedTime(&ms, b->ev_a, b->ev_b) == cudaSuccess)
+        b->stats.update_ms = ms;                     // the last update
+    cudaGetLastError();
+    *out = b->stats;
+    out->search_launches = 0;
+    out->search_ms = 0;
+    out->topk_ms = 0;
+    out->topk_calls = 0;
+    for (hs_sketch *h : b->views) {
+        hs_stats vs{};
+        sketch_stats(h, &vs, reset);
+        out->kernel_launches += vs.kernel_launches;
+        out->search_launches += vs.search_launches;
+        out->search_ms += vs.search_ms;
+        out->topk_ms += vs.topk_ms;     // summed over concurrent views
+        out->topk_calls += vs.topk_calls;
+    }
+    if (reset) std::memset(&b->stats, 0, sizeof(b->stats));
+    return HS_OK;
+}
+
+hs_status batch_autotune(hs_batch *b, const float *xyz, const uint64_t *offsets,
+                         double sample_rate, hs_tune *out) {
+    if (!b || !out) return fail(HS_ERR_ARG, "NULL argument");
+    if (!(sample_rate > 0.0 && sample_rate <= 1.0)) return fail(HS_ERR_ARG, "bad sample_rate");
+    hs_status st = batch_check_offsets(b, xyz, offsets);
+    if (st != HS_OK) return st;
+    const uint64_t n = offsets[b->nvol];
+    if (n == 0) return fail(HS_ERR_ARG, "no particles to tune on");
+    st = batch_ensure_bins(b, offsets, sample_rate);
+    if (st != HS_OK) return st;
+    batch_drop_graph(b);
+    const BinLayout base = b->bl;
+    const int threads_opt[2] = {1024, 512};
+    const uint32_t slot_opt[2] = {32, 16};
+    float best = 1e30f;
+    int best_t = b->threads;
+    BinLayout best_l = base;
+    int tried = 0;
+    for (int ti = 0; ti < 2; ++ti)
+        for (int si = 0; si < 2; ++si) {
+            BinLayout L = base;
+            L.slot = slot_opt[si];
+            size_t queue = (size_t)(1024 / 32) * 128 * 8;
+            L.smem = ((L.nbins * 4 + 15) & ~15ull) + ((L.nbins * L.slot * 2 + 15) & ~15ull) + queue +
+                     ((L.nbins + 31) / 32) * 4;
+            if (L.smem > kBinSmemBudget) continue;
+            if (threads_opt[ti] == 512 && L.nbins > 6u * 512) continue;
+            b->bl = L;
+            b->threads = threads_opt[ti];
+            float ms_best = 1e30f;
+            for (int rep = 0; rep < 2; ++rep) {
+                batch_fill_vols(b, offsets);
+                HS_CUDA(cudaEventRecord(b->ev_a, b->stream));
+                st = batch_enqueue(b, xyz, n, sample_rate);
+                if (st != HS_OK) return st;
+                HS_CUDA(cudaEventRecord(b->ev_b, b->stream));
+                HS_CUDA(cudaStreamSynchronize(b->stream));
+                float ms = 0;
+                HS_CUDA(cudaEventElapsedTime(&ms, b->ev_a, b->ev_b));
+                ms_best = std::min(ms_best, ms);
+            }
+            ++tried;
+            if (ms_best < best) {
+                best = ms_best;
+                best_t = threads_opt[ti];
+                best_l = L;
+            }
+        }
+    b->bl = best_l;
+    b->threads = best_t;
+    st = batch_reset(b);                              // tuning runs touched the counters
+    if (st != HS_OK) return st;
+    HS_CUDA(cudaStreamSynchronize(b->stream));
+    out->threads = (uint32_t)best_t;
+    out->slot = best_l.slot;
+    out->configs_tried = (uint32_t)tried;
+    out->best_ms = best;
+    return HS_OK;
+}
+
+}  // extern "C"
