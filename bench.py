@@ -208,7 +208,12 @@ def run_batched(steps: int, warmup: int):
     upd = float(np.mean([a.elapsed_time(c) for a, c in ups]))
     st = b.stats(reset=True)
     b.close()
+    hbm, _ = peaks()
     return {"workload": "subvolumes-64", "volumes": len(specs), "particles": total,
+            "roofline": {"kernel": "k_bin_scatter<batch> + k_bin_accumulate", "bound": "hbm",
+                         "achieved": 12.0 * total / (upd * 1e-3) / 1e9, "peak": hbm,
+                         "unit": "GB/s", "frac": 12.0 * total / (upd * 1e-3) / 1e9 / hbm,
+                         "note": "12 B per particle over the update's time"},
             "particles_per_s": total / (ms * 1e-3), "ms_per_step": ms, "update_ms": upd,
             "update_stream_gbs": 12.0 * total / (upd * 1e-3) / 1e9,
             "topk_ms_per_step": ms - upd, "k": 500, "sketch": "5 x 2^18 int32 per volume",
@@ -375,6 +380,12 @@ def run_learned(dev, n: int, main_keys: np.ndarray, train_boxes: int, stream):
         "plain_160MiB_ms": {"update": up_ms, "topk": tk_ms},
         "learned_ms": {"prepare": prep_ms, "update": lup_ms, "topk": ltk_ms},
         "learned_particles_per_s": n / ((prep_ms + lup_ms + ltk_ms) * 1e-3),
+        "roofline": {"kernel": "k_bin_scatter<routed> + k_bin_accumulate", "bound": "hbm",
+                     "achieved": 12.0 * n / (lup_ms * 1e-3) / 1e9, "peak": peaks()[0],
+                     "unit": "GB/s", "frac": 12.0 * n / (lup_ms * 1e-3) / 1e9 / peaks()[0],
+                     "note": "12 B per particle over the learned update's time; the sample "
+                             "pass reads the same 12 B in "
+                             f"{prep_ms:.1f} ms with features, MLP and routing"},
         "exact_table": f"2^{C['exact_log2_slots']} slots"})
     L.close()
     E.close()
@@ -793,7 +804,11 @@ def run_ours(args):
                 sk.stats(reset=True)
 
         pms, pst = ptimed(rec, args.steps, args.warmup)
+        pgbs = 8.0 * n / (pst["update_ms"] / args.steps * 1e-3) / 1e9
         packed = {"records": "64-bit, three 21-bit coordinates", "value": n * world / (pms * 1e-3),
+                  "roofline": {"kernel": "k_bin_scatter<packed> + k_bin_accumulate",
+                               "bound": "hbm", "achieved": pgbs, "peak": hbm, "unit": "GB/s",
+                               "frac": pgbs / hbm, "note": "8 B per record over the update"},
                   "unit": "particles/s", "ms_per_step": pms,
                   "update_ms": pst["update_ms"] / args.steps,
                   "stream_gbs": 8.0 * n / (pst["update_ms"] / args.steps * 1e-3) / 1e9,
