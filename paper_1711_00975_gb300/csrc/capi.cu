@@ -185,20 +185,21 @@ hs_status ensure_dir_scratch(hs_sketch *h) {
     return HS_OK;
 }
 
-// build the directory of row r (once per mesh size; the buffers are reused
-// when a batch view moves to a smaller mesh); false when memory is short
+// build the directory of row r (once per mesh; the buffers are reused when a
+// batch view moves to a mesh whose directory fits them); false when memory is
+// short
 bool ensure_dir(hs_sketch *h, int r) {
     uint64_t lines = (uint64_t)h->d.G * h->d.G;
     if (h->dir_off[r] && h->dir_G[r] == h->d.G) return true;
-    uint64_t nslots = 1ull << h->dir_D;
-    if (h->dir_off[r] && h->dir_lines_cap[r] < lines) {
+    if (h->dir_off[r] && (h->dir_lines_cap[r] < lines ||
+                          dir_bytes(h->dir_G[r], h->dir_D) < dir_bytes(h->d.G, h->dir_D))) {
         cudaFree(h->dir_off[r]);
         cudaFree(h->dir_rec[r]);
         h->dir_off[r] = nullptr;
         h->dir_rec[r] = nullptr;
     }
     if (!h->dir_off[r]) {
-        if (cudaMalloc(&h->dir_off[r], (nslots + 1) * 4) != cudaSuccess ||
+        if (cudaMalloc(&h->dir_off[r], dir_bytes(h->d.G, h->dir_D)) != cudaSuccess ||
             cudaMalloc(&h->dir_rec[r], lines * sizeof(DirRecord)) != cudaSuccess) {
             cudaGetLastError();
             if (h->dir_off[r]) cudaFree(h->dir_off[r]);

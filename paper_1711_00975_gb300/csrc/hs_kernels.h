@@ -151,6 +151,26 @@ cudaError_t launch_probe_distinct(const uint64_t *probe, uint64_t m, uint64_t *s
 // one mesh line of a row's directory: cy | cz << 16 (directories exist for
 // G < 2^16 only); the line's value L is recomputed from it when queried
 typedef uint32_t DirRecord;
+// A row's directory lives in one allocation of dir_bytes(G, D): (2^D + 1)
+// uint32 slot offsets, then (16-byte aligned) 2^D inline slots of up to 4
+// records.  The inline slots save a dependent DRAM read when the directory is
+// too large for L2 (G^2 >= 2^23 lines) and slots hold about 2 lines or fewer
+// (G^2 <= 2^(D+1)); otherwise only the offsets are kept.
+inline bool dir_has_inline(uint32_t G, uint32_t D) {
+    const uint64_t lines = (uint64_t)G * G;
+    return lines >= (1ull << 23) && lines <= (2ull << D);
+}
+inline size_t dir_offsets_bytes(uint32_t D) { return (((size_t)1 << D) * 4 + 4 + 15) & ~(size_t)15; }
+inline size_t dir_bytes(uint32_t G, uint32_t D) {
+    return dir_offsets_bytes(D) + (dir_has_inline(G, D) ? ((size_t)16 << D) : 0);
+}
+inline const uint4 *dir_inline(const uint32_t *offsets, uint32_t D) {
+    return reinterpret_cast<const uint4 *>(reinterpret_cast<const char *>(offsets) +
+                                           dir_offsets_bytes(D));
+}
+inline uint4 *dir_inline(uint32_t *offsets, uint32_t D) {
+    return reinterpret_cast<uint4 *>(reinterpret_cast<char *>(offsets) + dir_offsets_bytes(D));
+}
 // directory of the G^2 lines of row r bucketed by the top D bits of L
 cudaError_t launch_dir_build(const SketchDesc &d, int r, uint32_t D, uint32_t *offsets,
                              uint32_t *cursor, DirRecord *rec, uint32_t *scan_scratch,

@@ -16,6 +16,8 @@
 // reading at most two directory slots.  The work is proportional to
 // F * (G^2 + G * |hot buckets|) instead of G^3, and every cell that could pass
 // is still examined exactly once, so the result equals the exhaustive search.
+#include <algorithm>
+
 #include "hs_device.cuh"
 #include "hs_kernels.h"
 
@@ -141,12 +143,38 @@ __global__ void k_hot_list(const uint32_t *__restrict__ bits, uint64_t words_per
     }
 }
 
+// The first records of every slot, inline: slot i's 16-byte entry holds its
+// records (up to kInline of them) followed by kEmpty, or kInline times kCrowded
+// when the slot has more (then the counting-sorted arrays are read).  A record
+// is cy | cz << 16 with cz < G - 1 < 65535, so neither marker is a record.
+constexpr uint32_t kInline = 4;
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+constexpr uint32_t kCrowded = 0xFFFFFFFEu;
+
+__global__ void k_dir_inline(const uint32_t *__restrict__ offsets, const DirRecord *__restrict__ rec,
+                             uint64_t nslots, uint4 *__restrict__ inl) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nslots; i += stride) {
+        const uint32_t e0 = offsets[i], n = offsets[i + 1] - e0;
+        uint4 v;
+        if (n > kInline) {
+            v = make_uint4(kCrowded, kCrowded, kCrowded, kCrowded);
+        } else {
+            v.x = n > 0 ? rec[e0] : kEmpty;
+            v.y = n > 1 ? rec[e0 + 1] : kEmpty;
+            v.z = n > 2 ? rec[e0 + 2] : kEmpty;
+            v.w = n > 3 ? rec[e0 + 3] : kEmpty;
+        }
+        inl[i] = v;
+    }
+}
+
 // one thread per (cx, hot bucket of row r)
 template <int T>
 __global__ void __launch_bounds__(256)
     k_dir_query(const int32_t *__restrict__ C, const SketchDesc d, int r, uint32_t D,
                 const uint32_t *__restrict__ offsets, const DirRecord *__restrict__ rec,
-                const uint32_t *__restrict__ hot, uint64_t n_hot,
+                const uint4 *__restrict__ inl, const uint32_t *__restrict__ hot, uint64_t n_hot,
                 const uint32_t *__restrict__ bits, int32_t theta, uint32_t mode, uint64_t line_lo,
                 uint64_t line_hi, SearchOut out, RouteFilter skip) {
     const uint32_t rows = T > 0 ? (uint32_t)T : d.rows;
@@ -162,41 +190,50 @@ __global__ void __launch_bounds__(256)
         const uint64_t Tx = d.seed[r].a0 * (uint64_t)cx;
         const uint64_t lo = ((uint64_t)h << s) - Tx;
         const uint64_t slot0 = lo >> (64 - D);
+        // one mesh line (cy, cz) of the directory: its cell in column cx, if it
+        // falls in bucket h, is estimated when row r is its first hot row
+        auto visit = [&](DirRecord p) {
+            const uint32_t cy = p & 0xFFFFu, cz = p >> 16;
+            if (((line_value(d.seed[r], cy, cz) + Tx) >> s) != h) return;
+            const uint64_t line = (uint64_t)cy + (uint64_t)d.G * cz;
+            if (line < line_lo || line >= line_hi) return;
+            if (skip.bits && routed_cell(skip, cx, cy, cz)) return;
+            uint64_t v[T > 0 ? T : kMaxRows];
+            bool first = true;
+            uint32_t nhot = 1;
+            for (uint32_t rr = 0; rr < rows; ++rr) {
+                v[rr] = row_value(d.seed[rr], cx, cy, cz);
+                if ((int)rr == r) continue;
+                bool hh = exact_hot(bits, words_per_row, (int)rr, bucket_of(v[rr], d.log2w));
+                if ((int)rr < r && hh) first = false;
+                nhot += hh;
+            }
+            if (!first || nhot < need) return;
+            int32_t ev[T > 0 ? T : kMaxRows];
+            for (uint32_t rr = 0; rr < rows; ++rr)
+                ev[rr] = signed_count(__ldg(C + rr * d.W + bucket_of(v[rr], d.log2w)), v[rr],
+                                      d.log2w);
+            int32_t est = T == 5 ? median5(ev[0], ev[1], ev[2], ev[3], ev[4])
+                                 : lower_median_dyn(ev, (int)rows);
+            bool pass = mode == kGE ? est >= theta : (mode == kGT ? est > theta : est == theta);
+            if (!pass) return;
+            unsigned long long idx = atomicAdd(out.count, 1ull);
+            if (idx < out.cap) {
+                out.key[idx] = key_of(cx, cy, cz, d.G);
+                out.est[idx] = est;
+            }
+        };
         for (int j = 0; j < 2; ++j) {
             const uint64_t slot = (slot0 + j) & (nslots - 1);
-            const uint32_t e0 = offsets[slot], e1 = offsets[slot + 1];
-            for (uint32_t e = e0; e < e1; ++e) {
-                const DirRecord p = rec[e];
-                const struct { uint32_t cy, cz; } R = {p & 0xFFFFu, p >> 16};
-                if (((line_value(d.seed[r], R.cy, R.cz) + Tx) >> s) != h) continue;
-                const uint64_t line = (uint64_t)R.cy + (uint64_t)d.G * R.cz;
-                if (line < line_lo || line >= line_hi) continue;
-                if (skip.bits && routed_cell(skip, cx, R.cy, R.cz)) continue;
-                // reported from the first hot row only; count the hot rows
-                uint64_t v[T > 0 ? T : kMaxRows];
-                bool first = true;
-                uint32_t nhot = 1;
-                for (uint32_t rr = 0; rr < rows; ++rr) {
-                    v[rr] = row_value(d.seed[rr], cx, R.cy, R.cz);
-                    if ((int)rr == r) continue;
-                    bool hh = exact_hot(bits, words_per_row, (int)rr, bucket_of(v[rr], d.log2w));
-                    if ((int)rr < r && hh) first = false;
-                    nhot += hh;
-                }
-                if (!first || nhot < need) continue;
-                int32_t ev[T > 0 ? T : kMaxRows];
-                for (uint32_t rr = 0; rr < rows; ++rr)
-                    ev[rr] = signed_count(__ldg(C + rr * d.W + bucket_of(v[rr], d.log2w)), v[rr],
-                                          d.log2w);
-                int32_t est = T == 5 ? median5(ev[0], ev[1], ev[2], ev[3], ev[4])
-                                     : lower_median_dyn(ev, (int)rows);
-                bool pass = mode == kGE ? est >= theta : (mode == kGT ? est > theta : est == theta);
-                if (!pass) continue;
-                unsigned long long idx = atomicAdd(out.count, 1ull);
-                if (idx < out.cap) {
-                    out.key[idx] = key_of(cx, R.cy, R.cz, d.G);
-                    out.est[idx] = est;
-                }
+            const uint4 v = inl ? __ldg(inl + slot) : make_uint4(kCrowded, 0, 0, 0);
+            if (v.x == kCrowded) {
+                const uint32_t e0 = offsets[slot], e1 = offsets[slot + 1];
+                for (uint32_t e = e0; e < e1; ++e) visit(rec[e]);
+            } else {
+                if (v.x != kEmpty) visit(v.x);
+                if (v.y != kEmpty) visit(v.y);
+                if (v.z != kEmpty) visit(v.z);
+                if (v.w != kEmpty) visit(v.w);
             }
         }
     }
@@ -228,6 +265,12 @@ cudaError_t launch_dir_build(const SketchDesc &d, int r, uint32_t D, uint32_t *o
     if (e != cudaSuccess) return e;
     k_dir_scatter<<<(unsigned)blocks, 256, 0, s>>>(d, r, D, cursor, rec);
     *launches += 1;
+    if (dir_has_inline(d.G, D)) {
+        uint64_t sb = std::min<uint64_t>((nslots + 255) / 256, (uint64_t)max_blocks);
+        k_dir_inline<<<(unsigned)std::max<uint64_t>(sb, 1), 256, 0, s>>>(offsets, rec, nslots,
+                                                                         dir_inline(offsets, D));
+        *launches += 1;
+    }
     return cudaGetLastError();
 }
 
@@ -251,10 +294,14 @@ cudaError_t launch_dir_query(const int32_t *C, const SketchDesc &d, int r, uint3
     uint64_t blocks = (total + 255) / 256;
     if (blocks > (uint64_t)max_blocks) blocks = (uint64_t)max_blocks;
     if (d.rows == 5)
-        k_dir_query<5><<<(unsigned)blocks, 256, 0, s>>>(C, d, r, D, offsets, rec, hot, n_hot, bits,
+        k_dir_query<5><<<(unsigned)blocks, 256, 0, s>>>(C, d, r, D, offsets, rec,
+                                                       dir_has_inline(d.G, D) ? dir_inline(offsets, D) : nullptr,
+                                                       hot, n_hot, bits,
                                                        theta, mode, line_lo, line_hi, out, skip);
     else
-        k_dir_query<0><<<(unsigned)blocks, 256, 0, s>>>(C, d, r, D, offsets, rec, hot, n_hot, bits,
+        k_dir_query<0><<<(unsigned)blocks, 256, 0, s>>>(C, d, r, D, offsets, rec,
+                                                       dir_has_inline(d.G, D) ? dir_inline(offsets, D) : nullptr,
+                                                       hot, n_hot, bits,
                                                        theta, mode, line_lo, line_hi, out, skip);
     return cudaGetLastError();
 }
