@@ -76,10 +76,16 @@ typedef enum {
  * any read of the counters); these flags force one (same counters). */
 #define HS_FLAG_UPDATE_DIRECT 4u
 #define HS_FLAG_UPDATE_BINNED 8u
+/* The directory of mesh lines keeps each slot's first records inline beside
+ * its offset when that saves a dependent read (large directories with about
+ * two lines per slot); this flag keeps them for every mesh (for testing; same
+ * result). */
+#define HS_FLAG_DIR_INLINE 16u
 
 /* Sketch parameters.  rows in [1, 32]; log2_width in [1, 30]; box > 0 and
  * cell > 0 with 1 <= round(box / cell) <= 2^21; flags: 0, or at most one
- * HS_FLAG_SEARCH_* and at most one HS_FLAG_UPDATE_* value. */
+ * HS_FLAG_SEARCH_* and at most one HS_FLAG_UPDATE_* value, plus optionally
+ * HS_FLAG_DIR_INLINE. */
 typedef struct {
     uint32_t rows;        /* t: number of independent rows (Sec. 2.2)         */
     uint32_t log2_width;  /* b = W = 2^log2_width counters per row            */

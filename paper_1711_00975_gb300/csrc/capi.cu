@@ -46,7 +46,7 @@ hs_status check_params(const hs_params *p) {
     if (g < 1 || g > (double)(1u << 21))
         return fail(HS_ERR_ARG, "grid round(box/cell)=%.0f outside [1, 2^21]", g);
     const uint32_t known = HS_FLAG_SEARCH_SCAN | HS_FLAG_SEARCH_DIRECTORY | HS_FLAG_UPDATE_DIRECT |
-                           HS_FLAG_UPDATE_BINNED;
+                           HS_FLAG_UPDATE_BINNED | HS_FLAG_DIR_INLINE;
     if ((p->flags & ~known) != 0 || p->reserved != 0)
         return fail(HS_ERR_ARG, "unknown flags or reserved != 0");
     if ((p->flags & HS_FLAG_SEARCH_SCAN) && (p->flags & HS_FLAG_SEARCH_DIRECTORY))
@@ -190,16 +190,17 @@ hs_status ensure_dir_scratch(hs_sketch *h) {
 // short
 bool ensure_dir(hs_sketch *h, int r) {
     uint64_t lines = (uint64_t)h->d.G * h->d.G;
+    const bool force = (h->p.flags & HS_FLAG_DIR_INLINE) != 0;
     if (h->dir_off[r] && h->dir_G[r] == h->d.G) return true;
-    if (h->dir_off[r] && (h->dir_lines_cap[r] < lines ||
-                          dir_bytes(h->dir_G[r], h->dir_D) < dir_bytes(h->d.G, h->dir_D))) {
+    if (h->dir_off[r] && (h->dir_lines_cap[r] < lines || dir_bytes(h->dir_G[r], h->dir_D, force) <
+                                                             dir_bytes(h->d.G, h->dir_D, force))) {
         cudaFree(h->dir_off[r]);
         cudaFree(h->dir_rec[r]);
         h->dir_off[r] = nullptr;
         h->dir_rec[r] = nullptr;
     }
     if (!h->dir_off[r]) {
-        if (cudaMalloc(&h->dir_off[r], dir_bytes(h->d.G, h->dir_D)) != cudaSuccess ||
+        if (cudaMalloc(&h->dir_off[r], dir_bytes(h->d.G, h->dir_D, force)) != cudaSuccess ||
             cudaMalloc(&h->dir_rec[r], lines * sizeof(DirRecord)) != cudaSuccess) {
             cudaGetLastError();
             if (h->dir_off[r]) cudaFree(h->dir_off[r]);
@@ -210,8 +211,9 @@ bool ensure_dir(hs_sketch *h, int r) {
         h->dir_lines_cap[r] = lines;
     }
     int launches = 0;
-    cudaError_t e = launch_dir_build(h->d, r, h->dir_D, h->dir_off[r], h->dir_cursor, h->dir_rec[r],
-                                     h->scan_scratch, h->num_sms * 8, h->stream, &launches);
+    cudaError_t e = launch_dir_build(h->d, r, h->dir_D, dir_has_inline(h->d.G, h->dir_D, force),
+                                     h->dir_off[r], h->dir_cursor, h->dir_rec[r], h->scan_scratch,
+                                     h->num_sms * 8, h->stream, &launches);
     h->stats.kernel_launches += launches;
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -419,7 +421,10 @@ hs_status search_pass_dir(hs_sketch *h, int32_t theta, SearchMode mode, int64_t 
     EventPair ev = take_events(h);
     cudaEventRecord(ev.a, h->stream);
     for (uint32_t r = 0; r < F; ++r) {
-        HS_CUDA(launch_dir_query(h->C, h->d, (int)r, h->dir_D, h->dir_off[r], h->dir_rec[r],
+        HS_CUDA(launch_dir_query(h->C, h->d, (int)r, h->dir_D,
+                                 dir_has_inline(h->d.G, h->dir_D,
+                                                (h->p.flags & HS_FLAG_DIR_INLINE) != 0),
+                                 h->dir_off[r], h->dir_rec[r],
                                  h->hot_list + r * h->hot_cap, cnt[r], h->xbits, theta, mode,
                                  line_lo, line_hi, out, h->num_sms * 16, h->stream,
                                  h->route.filter));

@@ -155,14 +155,14 @@ typedef uint32_t DirRecord;
 // uint32 slot offsets, then (16-byte aligned) 2^D inline slots of up to 4
 // records.  The inline slots save a dependent DRAM read when the directory is
 // too large for L2 (G^2 >= 2^23 lines) and slots hold about 2 lines or fewer
-// (G^2 <= 2^(D+1)); otherwise only the offsets are kept.
-inline bool dir_has_inline(uint32_t G, uint32_t D) {
+// (G^2 <= 2^(D+1)), or always when forced; otherwise only the offsets are kept.
+inline bool dir_has_inline(uint32_t G, uint32_t D, bool force) {
     const uint64_t lines = (uint64_t)G * G;
-    return lines >= (1ull << 23) && lines <= (2ull << D);
+    return force || (lines >= (1ull << 23) && lines <= (2ull << D));
 }
 inline size_t dir_offsets_bytes(uint32_t D) { return (((size_t)1 << D) * 4 + 4 + 15) & ~(size_t)15; }
-inline size_t dir_bytes(uint32_t G, uint32_t D) {
-    return dir_offsets_bytes(D) + (dir_has_inline(G, D) ? ((size_t)16 << D) : 0);
+inline size_t dir_bytes(uint32_t G, uint32_t D, bool force) {
+    return dir_offsets_bytes(D) + (dir_has_inline(G, D, force) ? ((size_t)16 << D) : 0);
 }
 inline const uint4 *dir_inline(const uint32_t *offsets, uint32_t D) {
     return reinterpret_cast<const uint4 *>(reinterpret_cast<const char *>(offsets) +
@@ -171,8 +171,9 @@ inline const uint4 *dir_inline(const uint32_t *offsets, uint32_t D) {
 inline uint4 *dir_inline(uint32_t *offsets, uint32_t D) {
     return reinterpret_cast<uint4 *>(reinterpret_cast<char *>(offsets) + dir_offsets_bytes(D));
 }
-// directory of the G^2 lines of row r bucketed by the top D bits of L
-cudaError_t launch_dir_build(const SketchDesc &d, int r, uint32_t D, uint32_t *offsets,
+// directory of the G^2 lines of row r bucketed by the top D bits of L, with
+// inline slots when `inl` (dir_has_inline of the allocation)
+cudaError_t launch_dir_build(const SketchDesc &d, int r, uint32_t D, bool inl, uint32_t *offsets,
                              uint32_t *cursor, DirRecord *rec, uint32_t *scan_scratch,
                              int max_blocks, cudaStream_t s, int *launches);
 // bucket indices of the set bits of row r of an exact (one bit per bucket) hot bitmap
@@ -180,7 +181,7 @@ cudaError_t launch_hot_list(const uint32_t *bits, const SketchDesc &d, int r, ui
                             unsigned long long *count, uint64_t cap, int max_blocks,
                             cudaStream_t s);
 // cells first hot in row r, with at least `need` hot rows and a passing estimate
-cudaError_t launch_dir_query(const int32_t *C, const SketchDesc &d, int r, uint32_t D,
+cudaError_t launch_dir_query(const int32_t *C, const SketchDesc &d, int r, uint32_t D, bool inl,
                              const uint32_t *offsets, const DirRecord *rec, const uint32_t *hot,
                              uint64_t n_hot, const uint32_t *bits, int32_t theta, SearchMode mode,
                              uint64_t line_lo, uint64_t line_hi, SearchOut out, int max_blocks,

@@ -248,7 +248,7 @@ cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t *out, uint64_t n,
     return exclusive_scan(in, out, n, scratch, s, launches);
 }
 
-cudaError_t launch_dir_build(const SketchDesc &d, int r, uint32_t D, uint32_t *offsets,
+cudaError_t launch_dir_build(const SketchDesc &d, int r, uint32_t D, bool inl, uint32_t *offsets,
                              uint32_t *cursor, DirRecord *rec, uint32_t *scan_scratch,
                              int max_blocks, cudaStream_t s, int *launches) {
     const uint64_t nslots = 1ull << D;
@@ -265,7 +265,7 @@ cudaError_t launch_dir_build(const SketchDesc &d, int r, uint32_t D, uint32_t *o
     if (e != cudaSuccess) return e;
     k_dir_scatter<<<(unsigned)blocks, 256, 0, s>>>(d, r, D, cursor, rec);
     *launches += 1;
-    if (dir_has_inline(d.G, D)) {
+    if (inl) {
         uint64_t sb = std::min<uint64_t>((nslots + 255) / 256, (uint64_t)max_blocks);
         k_dir_inline<<<(unsigned)std::max<uint64_t>(sb, 1), 256, 0, s>>>(offsets, rec, nslots,
                                                                          dir_inline(offsets, D));
@@ -284,7 +284,7 @@ cudaError_t launch_hot_list(const uint32_t *bits, const SketchDesc &d, int r, ui
     return cudaGetLastError();
 }
 
-cudaError_t launch_dir_query(const int32_t *C, const SketchDesc &d, int r, uint32_t D,
+cudaError_t launch_dir_query(const int32_t *C, const SketchDesc &d, int r, uint32_t D, bool inl,
                              const uint32_t *offsets, const DirRecord *rec, const uint32_t *hot,
                              uint64_t n_hot, const uint32_t *bits, int32_t theta, SearchMode mode,
                              uint64_t line_lo, uint64_t line_hi, SearchOut out, int max_blocks,
@@ -295,12 +295,12 @@ cudaError_t launch_dir_query(const int32_t *C, const SketchDesc &d, int r, uint3
     if (blocks > (uint64_t)max_blocks) blocks = (uint64_t)max_blocks;
     if (d.rows == 5)
         k_dir_query<5><<<(unsigned)blocks, 256, 0, s>>>(C, d, r, D, offsets, rec,
-                                                       dir_has_inline(d.G, D) ? dir_inline(offsets, D) : nullptr,
+                                                       inl ? dir_inline(offsets, D) : nullptr,
                                                        hot, n_hot, bits,
                                                        theta, mode, line_lo, line_hi, out, skip);
     else
         k_dir_query<0><<<(unsigned)blocks, 256, 0, s>>>(C, d, r, D, offsets, rec,
-                                                       dir_has_inline(d.G, D) ? dir_inline(offsets, D) : nullptr,
+                                                       inl ? dir_inline(offsets, D) : nullptr,
                                                        hot, n_hot, bits,
                                                        theta, mode, line_lo, line_hi, out, skip);
     return cudaGetLastError();

@@ -20,6 +20,7 @@ HS_FLAG_SEARCH_SCAN = 1
 HS_FLAG_SEARCH_DIRECTORY = 2
 HS_FLAG_UPDATE_DIRECT = 4
 HS_FLAG_UPDATE_BINNED = 8
+HS_FLAG_DIR_INLINE = 16
 
 HS_OK, HS_ERR_ARG, HS_ERR_CUDA, HS_ERR_OOM, HS_ERR_TABLE_FULL, HS_ERR_TIMEOUT, HS_ERR_STATE = range(7)
 _NAMES = ["HS_OK", "HS_ERR_ARG", "HS_ERR_CUDA", "HS_ERR_OOM", "HS_ERR_TABLE_FULL",

@@ -55,7 +55,10 @@ def test_argument_checks_need_no_device():
     h = ctypes.c_void_p()
     for bad in (hsk.make_params(0, 16, 100.0, 0.1), hsk.make_params(33, 16, 100.0, 0.1),
                 hsk.make_params(5, 0, 100.0, 0.1), hsk.make_params(5, 31, 100.0, 0.1),
-                hsk.make_params(5, 16, -1.0, 0.1), hsk.make_params(5, 16, 1e9, 1e-3)):
+                hsk.make_params(5, 16, -1.0, 0.1), hsk.make_params(5, 16, 1e9, 1e-3),
+                hsk.make_params(5, 16, 100.0, 0.1, flags=32),
+                hsk.make_params(5, 16, 100.0, 0.1, flags=hsk.HS_FLAG_SEARCH_SCAN | hsk.HS_FLAG_SEARCH_DIRECTORY),
+                hsk.make_params(5, 16, 100.0, 0.1, flags=hsk.HS_FLAG_UPDATE_DIRECT | hsk.HS_FLAG_UPDATE_BINNED)):
         assert L.sketch_create(ctypes.byref(bad), 0, ctypes.byref(h)) == hsk.HS_ERR_ARG
     assert L.sketch_create(None, 0, ctypes.byref(h)) == hsk.HS_ERR_ARG
     n = ctypes.c_uint32()

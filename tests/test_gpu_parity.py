@@ -29,7 +29,9 @@ def small():
     return spec, synth.HaloBox(spec).generate()
 
 
-SEARCH = {"auto": 0, "scan": 1, "directory": 2}
+# "inline": the directory with every slot's first records inline (the layout
+# large meshes use), forced on the small meshes the oracle searches in full
+SEARCH = {"auto": 0, "scan": 1, "directory": 2, "inline": 2 | 16}
 UPDATE = {"auto": 0, "direct": 4, "binned": 8}
 
 
@@ -303,7 +305,7 @@ def test_topk_after_reset_and_requery(hs, small, search):
     assert np.array_equal(keys, wk) and np.array_equal(est, we)
 
 
-@pytest.mark.parametrize("search", ["scan", "directory"])
+@pytest.mark.parametrize("search", ["scan", "directory", "inline"])
 def test_topk_heavy_ties_at_positive_threshold(hs, search):
     # many cells share the k-th estimate (every occupied cell has count 3):
     # the positive-threshold tie path must return the smallest keys among them
