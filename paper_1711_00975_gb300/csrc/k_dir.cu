@@ -198,21 +198,23 @@ __global__ void __launch_bounds__(256)
             const uint64_t line = (uint64_t)cy + (uint64_t)d.G * cz;
             if (line < line_lo || line >= line_hi) return;
             if (skip.bits && routed_cell(skip, cx, cy, cz)) return;
-            uint64_t v[T > 0 ? T : kMaxRows];
-            bool first = true;
-            uint32_t nhot = 1;
+            // the rows before r must be cold (the cell is reported from its
+            // first hot row) and at least `need` rows hot; nearly every line
+            // fails one of the two after a row or two, so stop there
+            uint32_t nhot = 1, left = rows - 1;
             for (uint32_t rr = 0; rr < rows; ++rr) {
-                v[rr] = row_value(d.seed[rr], cx, cy, cz);
                 if ((int)rr == r) continue;
-                bool hh = exact_hot(bits, words_per_row, (int)rr, bucket_of(v[rr], d.log2w));
-                if ((int)rr < r && hh) first = false;
+                const uint64_t v = row_value(d.seed[rr], cx, cy, cz);
+                const bool hh = exact_hot(bits, words_per_row, (int)rr, bucket_of(v, d.log2w));
+                if ((int)rr < r && hh) return;
                 nhot += hh;
+                if (nhot + --left < need) return;
             }
-            if (!first || nhot < need) return;
             int32_t ev[T > 0 ? T : kMaxRows];
-            for (uint32_t rr = 0; rr < rows; ++rr)
-                ev[rr] = signed_count(__ldg(C + rr * d.W + bucket_of(v[rr], d.log2w)), v[rr],
-                                      d.log2w);
+            for (uint32_t rr = 0; rr < rows; ++rr) {
+                const uint64_t v = row_value(d.seed[rr], cx, cy, cz);
+                ev[rr] = signed_count(__ldg(C + rr * d.W + bucket_of(v, d.log2w)), v, d.log2w);
+            }
             int32_t est = T == 5 ? median5(ev[0], ev[1], ev[2], ev[3], ev[4])
                                  : lower_median_dyn(ev, (int)rows);
             bool pass = mode == kGE ? est >= theta : (mode == kGT ? est > theta : est == theta);
