@@ -99,14 +99,17 @@ __global__ void k_take(const uint64_t *__restrict__ key, const int32_t *__restri
 
 // rank[i] += number of entries of slice blockIdx.y ranked before entry i: the
 // entries are split over blockIdx.x (one per thread) and the slices of the
-// comparison range over blockIdx.y, staged through shared memory.
-constexpr uint32_t kRankSlice = 8192;
+// comparison range (`slice` entries each) over blockIdx.y, staged through
+// shared memory.  Small blocks and slices spread a top-k of 10^4 entries over
+// about 400 blocks.
+constexpr uint32_t kRankThreads = 256;
+constexpr uint32_t kRankSlice = 1024;
 
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(kRankThreads)
     k_rank_count(const uint64_t *__restrict__ tk, const int32_t *__restrict__ te, uint64_t n,
-                 uint32_t *__restrict__ rank) {
-    __shared__ uint32_t s_hi[1024];
-    __shared__ uint64_t s_lo[1024];
+                 uint64_t slice, uint32_t *__restrict__ rank) {
+    __shared__ uint32_t s_hi[kRankThreads];
+    __shared__ uint64_t s_lo[kRankThreads];
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t hi = 0;
     uint64_t lo = 0;
@@ -114,8 +117,8 @@ __global__ void __launch_bounds__(1024)
         hi = rank_hi(te[i]);
         lo = rank_lo(tk[i]);
     }
-    const uint64_t s0 = (uint64_t)blockIdx.y * kRankSlice;
-    const uint64_t s1 = s0 + kRankSlice < n ? s0 + kRankSlice : n;
+    const uint64_t s0 = (uint64_t)blockIdx.y * slice;
+    const uint64_t s1 = s0 + slice < n ? s0 + slice : n;
     uint32_t before = 0;
     for (uint64_t base = s0; base < s1; base += blockDim.x) {
         const uint64_t j = base + threadIdx.x;
@@ -242,8 +245,11 @@ cudaError_t launch_take_sorted(const uint64_t *key, const int32_t *est, uint64_t
     }
     e = cudaMemsetAsync(tmp_rank, 0, n_take * 4, s);
     if (e != cudaSuccess) return e;
-    const dim3 grid((unsigned)((n_take + 1023) / 1024), (unsigned)((n_take + kRankSlice - 1) / kRankSlice));
-    k_rank_count<<<grid, 1024, 0, s>>>(tmp_key, tmp_est, n_take, tmp_rank);
+    uint64_t slice = kRankSlice;
+    while ((n_take + slice - 1) / slice > 65535) slice *= 2;   // grid.y limit
+    const dim3 grid((unsigned)((n_take + kRankThreads - 1) / kRankThreads),
+                    (unsigned)((n_take + slice - 1) / slice));
+    k_rank_count<<<grid, kRankThreads, 0, s>>>(tmp_key, tmp_est, n_take, slice, tmp_rank);
     k_rank_place<<<(unsigned)((n_take + 255) / 256), 256, 0, s>>>(tmp_key, tmp_est, tmp_rank, n_take,
                                                                  out_key, out_est);
     *launches += 3;
