@@ -363,7 +363,7 @@ hs_status mlp_destroy(hs_mlp *m);
  * (12 bytes a slot; linear probing from a 64-bit mix of the key, at most 64
  * slots per key).  The reads below fail with HS_ERR_TABLE_FULL when some key
  * found no free slot (size the table about 2x the distinct cells or more).
- * Used as the judge of top-k recall and for the router's training labels.
+ * Used as the ground truth of top-k recall and for the router's training labels.
  * All calls are ordered on cuda_stream; the reads are synchronous. */
 typedef struct hs_exact hs_exact;
 hs_status exact_create(double box, double cell, uint32_t log2_slots, void *cuda_stream,

@@ -18,7 +18,7 @@
  *   - Count Sketch with Full Search (Algorithm 1): estimate every cell of the
  *     dictionary and keep the k largest;
  *   - the exact algorithm of Sec. 4.2 (one counter per occupied cell, k
- *     heaviest), the judge of recall.
+ *     heaviest), the ground truth of recall.
  *
  * Readings where the paper is silent (each is listed in the design notes):
  *   - hash family: vector multiply-shift over the three cell coordinates,

@@ -1,7 +1,7 @@
 // k_exact.cu - the exact algorithm of Sec. 4.2: one counter per occupied
 // cell, kept in an open-addressing hash table in device memory (uint64 key,
 // all ones = empty, + int32 count; linear probing from a 64-bit mix of the
-// key, at most kTableProbes slots per key).  Used as the judge of recall and
+// key, at most kTableProbes slots per key).  Used as the ground truth of recall and
 // for the router's training labels.
 #include <algorithm>
 
