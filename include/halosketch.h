@@ -259,21 +259,23 @@ hs_status hs_measure_red_rate(uint64_t n_counters, uint64_t total_ops, double *o
 
 /*
  * Point queries that allocate nothing.  No counterpart in the paper: this is
- * for callers that cannot call cudaMalloc when they query - code running
- * while its stream is captured into a CUDA graph, processes whose device
- * memory belongs to another allocator or a fixed budget, latency-critical
- * loops.  Same results as sketch_query (keys and est host or device arrays;
- * synchronous; a key >= G^3 gives HS_ERR_ARG with its est entry 0), but every
- * temporary lives in one static device array of the library, sized for
+ * for callers that cannot call cudaMalloc when they query - processes whose
+ * device memory belongs to another allocator or is held to a fixed budget,
+ * and query loops that must not pay for an allocation (a cudaMalloc may
+ * synchronise the device).  Same results as sketch_query (keys and est host
+ * or device arrays, in any combination; a key >= G^3 gives HS_ERR_ARG with
+ * its est entry 0), through the same estimate kernel, but every temporary
+ * lives in one static device array of the library, sized for
  * HS_NOALLOC_QUERY_MAX keys (about 3 MiB, held on every GPU that loads the
  * library until the process exits).  m > HS_NOALLOC_QUERY_MAX gives
  * HS_ERR_ARG: split the query.  The sketch's device must be current.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress), which may load the library's device code: make that
- * first call before any stream capture.  All calls share the array, which
- * keeps the previous call's contents (the call clears its own flag); calls
- * that overlap on the GPU - from several host threads or handles - race on it.
- * Pending binned increments are applied first, as by every reader.
+ * The call is synchronous: it waits on the handle's stream to read back the
+ * bad-key flag (and est, for a host array).  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress), which may load the
+ * library's device code.  All calls share the array, which keeps the previous
+ * call's contents (the call clears its own flag); calls that overlap on the
+ * GPU - from several host threads or handles - race on it.  Pending binned
+ * increments are applied first, as by every reader.
  */
 #define HS_NOALLOC_QUERY_MAX 262144u
 hs_status sketch_query_noalloc(hs_sketch *h, const uint64_t *keys, uint64_t m, int32_t *est);

@@ -20,7 +20,7 @@
  *   - the exact algorithm of Sec. 4.2 (one counter per occupied cell, k
  *     heaviest), the ground truth of recall.
  *
- * Readings where the paper is silent (each is listed in the design notes):
+ * Readings taken where the paper is silent, ambiguous or garbled:
  *   - hash family: vector multiply-shift over the three cell coordinates,
  *     v = (a0*cx + a1*cy + a2*cz + b) mod 2^64, bucket = top log2W bits of v,
  *     sign bit = the next bit (1 -> -1) (strongly universal, Thorup 2015,

@@ -56,16 +56,45 @@ hs_status check_params(const hs_params *p) {
     return HS_OK;
 }
 
-EventPair take_events(hs_sketch *h) {
+// An event pair for timing one launch: from the pool, else newly created.
+// Lists of pairs still waiting to be folded into the stats are bounded: past
+// kMaxPendingEvents entries the older half is waited for and folded, so a long
+// loop of updates and point queries neither grows them nor creates events
+// without end.
+hs_status take_events(hs_sketch *h, EventPair *out) {
+    for (auto *v : {&h->pending_update, &h->pending_search, &h->pending_flush}) {
+        if (v->size() < kMaxPendingEvents) continue;
+        const size_t half = v->size() / 2;
+        HS_CUDA(cudaEventSynchronize((*v)[half - 1].b));
+        for (size_t i = 0; i < half; ++i) {
+            float ms = 0;
+            if (cudaEventElapsedTime(&ms, (*v)[i].a, (*v)[i].b) == cudaSuccess) {
+                if (v == &h->pending_search) h->stats.search_ms += ms;
+                else h->stats.update_ms += ms;
+                if (v == &h->pending_flush) h->stats.flush_ms += ms;
+            }
+            h->pool.push_back((*v)[i]);
+        }
+        v->erase(v->begin(), v->begin() + (ptrdiff_t)half);
+        cudaGetLastError();
+    }
     if (!h->pool.empty()) {
-        EventPair e = h->pool.back();
+        *out = h->pool.back();
         h->pool.pop_back();
-        return e;
+        return HS_OK;
     }
     EventPair e{nullptr, nullptr};
-    cudaEventCreate(&e.a);
-    cudaEventCreate(&e.b);
-    return e;
+    cudaError_t err = cudaEventCreate(&e.a);
+    if (err == cudaSuccess) {
+        err = cudaEventCreate(&e.b);
+        if (err != cudaSuccess) cudaEventDestroy(e.a);
+    }
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return fail(HS_ERR_CUDA, "cudaEventCreate failed: %s", cudaGetErrorString(err));
+    }
+    *out = e;
+    return HS_OK;
 }
 
 // fold finished event pairs into the stats (caller has synchronised)
@@ -92,6 +121,20 @@ void drain_timings(hs_sketch *h) {
     }
     h->pending_flush.clear();
     cudaGetLastError();
+}
+
+// A top-k list must be strictly ranked (estimate desc, key asc): each
+// candidate is placed at the count of candidates ranked before it, so two
+// equal candidates would share a slot and leave another one stale.  Checked on
+// the host copy of every list before it is returned.
+hs_status check_ranked(const uint64_t *keys, const int32_t *est, uint64_t n) {
+    for (uint64_t i = 1; i < n; ++i) {
+        const bool before = est[i - 1] > est[i] || (est[i - 1] == est[i] && keys[i - 1] < keys[i]);
+        if (!before)
+            return fail(HS_ERR_STATE, "top-k entries %llu and %llu are not strictly ranked",
+                        (unsigned long long)(i - 1), (unsigned long long)i);
+    }
+    return HS_OK;
 }
 
 void free_topk_scratch(hs_sketch *h) {
@@ -256,7 +299,8 @@ hs_status ensure_query_scratch(hs_sketch *h, uint64_t m) {
 // add every binned code to the counters (before anything reads them)
 hs_status drain(hs_sketch *h) {
     if (h->pending <= 0) return HS_OK;
-    EventPair ev = take_events(h);
+    EventPair ev;
+    HS_TRY(take_events(h, &ev));
     cudaEventRecord(ev.a, h->stream);
     if (h->carry_valid) {
         HS_CUDA(launch_carry_flush(h->bl, h->carry, (uint32_t)h->num_sms, h->bins, h->bin_cursor,
@@ -330,7 +374,8 @@ hs_status launch_update_timed(hs_sketch *h, const float *xyz, uint64_t n, uint64
                     st = drain(h);
                     if (st != HS_OK) return st;
                 }
-                EventPair ev = take_events(h);
+                EventPair ev;
+                HS_TRY(take_events(h, &ev));
                 cudaEventRecord(ev.a, h->stream);
                 const float *src = reinterpret_cast<const float *>(
                     reinterpret_cast<const char *>(xyz) + off * esz);
@@ -355,7 +400,8 @@ hs_status launch_update_timed(hs_sketch *h, const float *xyz, uint64_t n, uint64
 
 hs_status launch_update_direct(hs_sketch *h, const float *xyz, uint64_t n, uint64_t g0,
                                double rate, bool packed) {
-    EventPair ev = take_events(h);
+    EventPair ev;
+    HS_TRY(take_events(h, &ev));
     cudaEventRecord(ev.a, h->stream);
     if (packed)
         HS_CUDA(launch_update_packed(reinterpret_cast<const uint64_t *>(xyz), n, g0, h->d, h->C,
@@ -418,7 +464,8 @@ hs_status search_pass_dir(hs_sketch *h, int32_t theta, SearchMode mode, int64_t 
             return HS_OK;
         }
     }
-    EventPair ev = take_events(h);
+    EventPair ev;
+    HS_TRY(take_events(h, &ev));
     cudaEventRecord(ev.a, h->stream);
     for (uint32_t r = 0; r < F; ++r) {
         HS_CUDA(launch_dir_query(h->C, h->d, (int)r, h->dir_D,
@@ -469,7 +516,8 @@ hs_status search_pass(hs_sketch *h, int32_t theta, SearchMode mode, uint64_t lin
                         "threshold); use the hierarchical query (sketch_set_hierarchy)",
                         (unsigned long long)((line_hi - line_lo) * G));
         const uint64_t seg = std::max<uint64_t>(1, (1ull << 34) / G);
-        EventPair ev = take_events(h);
+        EventPair ev;
+        HS_TRY(take_events(h, &ev));
         cudaEventRecord(ev.a, h->stream);
         for (uint64_t l0 = line_lo; l0 < line_hi; l0 += seg) {
             HS_CUDA(launch_full_search(h->C, h->d, theta, mode, h->bitmap, h->nb, prune, l0,
@@ -699,6 +747,7 @@ hs_status sketch_query(hs_sketch *h, const uint64_t *keys, uint64_t m, int32_t *
     uint32_t bad = 0;
     HS_CUDA(cudaMemcpyAsync(&bad, &h->flags[0], 4, cudaMemcpyDeviceToHost, h->stream));
     HS_CUDA(cudaStreamSynchronize(h->stream));
+    drain_timings(h);
     if (bad) return fail(HS_ERR_ARG, "a key is >= G^3 = %llu", (unsigned long long)h->n_cells);
     return HS_OK;
 }
@@ -732,7 +781,8 @@ static hs_status expand_pass(hs_sketch *h, const uint64_t *skeys, uint64_t ns, i
                             cudaMemcpyHostToDevice, h->stream));
     SearchOut out{h->cand_key, h->cand_est, &h->counters[0], h->cap};
     if (!(mode == kGT && theta == INT32_MAX) && key_hi > key_lo) {
-        EventPair ev = take_events(h);
+        EventPair ev;
+        HS_TRY(take_events(h, &ev));
         cudaEventRecord(ev.a, h->stream);
         int launches = 0;
         HS_CUDA(launch_expand(h->C, h->d, skeys, ns, h->super->d.F, h->super->d.G, theta, mode,
@@ -772,7 +822,8 @@ static hs_status topk_hier(hs_sketch *h, uint64_t kk, uint64_t *keys, int32_t *e
     st = ensure_topk_scratch(h, kk);
     if (st != HS_OK) return st;
     h->stats.last_passes = 0;
-    EventPair whole = take_events(h);
+    EventPair whole;
+    HS_TRY(take_events(h, &whole));
     cudaEventRecord(whole.a, h->stream);
     const uint64_t n_cells = h->n_cells;
     // a first threshold from the probe; if the selected super-items hold fewer
@@ -847,6 +898,7 @@ static hs_status topk_hier(hs_sketch *h, uint64_t kk, uint64_t *keys, int32_t *e
     h->pool.push_back(whole);
     h->stats.topk_calls += 1;
     drain_timings(h);
+    HS_TRY(check_ranked(keys, est, n));
     *n_out = (uint32_t)n;
     return HS_OK;
 }
@@ -861,7 +913,8 @@ hs_status topk_extract(hs_sketch *h, uint32_t k, uint64_t *keys, int32_t *est, u
     st = ensure_topk_scratch(h, kk);
     if (st != HS_OK) return st;
     h->stats.last_passes = 0;
-    EventPair whole = take_events(h);
+    EventPair whole;
+    HS_TRY(take_events(h, &whole));
     cudaEventRecord(whole.a, h->stream);
     const uint64_t lines = (uint64_t)h->d.G * h->d.G;
 
@@ -936,6 +989,7 @@ hs_status topk_extract(hs_sketch *h, uint32_t k, uint64_t *keys, int32_t *est, u
     h->pool.push_back(whole);
     h->stats.topk_calls += 1;
     drain_timings(h);
+    HS_TRY(check_ranked(keys, est, n));
     *n_out = (uint32_t)n;
     return HS_OK;
 }
@@ -1087,26 +1141,26 @@ hs_status hs_measure_red_rate(uint64_t n_counters, uint64_t total_ops, double *o
     HS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     uint32_t *t = nullptr;
     HS_CUDA(cudaMalloc(&t, n_counters * 4));
-    cudaStream_t s;
-    cudaEvent_t a, b;
-    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-    cudaEventCreate(&a);
-    cudaEventCreate(&b);
+    cudaStream_t s = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
     int blocks = sms * 8;
     uint64_t per = std::max<uint64_t>(1, total_ops / ((uint64_t)blocks * 256));
-    cudaMemsetAsync(t, 0, n_counters * 4, s);
-    launch_red_rate(t, n_counters, per, blocks, s);   // warm the table into L2
-    cudaEventRecord(a, s);
-    cudaError_t e = launch_red_rate(t, n_counters, per, blocks, s);
-    cudaEventRecord(b, s);
-    cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(t, 0, n_counters * 4, s);
+    if (e == cudaSuccess) e = launch_red_rate(t, n_counters, per, blocks, s);   // warm the table into L2
+    if (e == cudaSuccess) e = cudaEventRecord(a, s);
+    if (e == cudaSuccess) e = launch_red_rate(t, n_counters, per, blocks, s);
+    if (e == cudaSuccess) e = cudaEventRecord(b, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     float ms = 0;
-    cudaEventElapsedTime(&ms, a, b);
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-    cudaStreamDestroy(s);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (s) cudaStreamDestroy(s);
     cudaFree(t);
-    if (e != cudaSuccess) return fail(HS_ERR_CUDA, "red-rate kernel: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(HS_ERR_CUDA, "red-rate measurement: %s", cudaGetErrorString(e));
     *ops_per_s = (double)per * blocks * 256 / (ms * 1e-3);
     return HS_OK;
 }

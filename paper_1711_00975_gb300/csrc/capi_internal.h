@@ -30,6 +30,13 @@ hs_status fail(hs_status st, const char *fmt, ...);
                         __LINE__);                                                         \
     } while (0)
 
+// return st unless it is HS_OK
+#define HS_TRY(call)                          \
+    do {                                      \
+        hs_status st_ = (call);               \
+        if (st_ != HS_OK) return st_;         \
+    } while (0)
+
 constexpr uint64_t kProbeCap = 1ull << 20;        // keys of the first 2^20 particles
 constexpr uint32_t kProbeSlotsLog2 = 21;
 constexpr uint64_t kStageParticles = 1ull << 24;  // 192 MiB per staging buffer
@@ -40,6 +47,7 @@ constexpr uint64_t kBinBudgetBytes = 4ull << 30;   // global bins, at most
 constexpr double kBinnedMinUpdates = 1 << 20;      // smaller calls add directly
 constexpr uint64_t kMaxScanCells = 1ull << 40;      // largest full scan one top-k may run
 constexpr uint32_t kBatchViews = 8;                 // volumes whose top-k run concurrently
+constexpr size_t kMaxPendingEvents = 256;           // timing pairs kept before folding
 
 struct EventPair {
     cudaEvent_t a, b;
@@ -135,8 +143,9 @@ namespace capi {
 
 bool is_device_ptr(const void *p);
 hs_status check_params(const hs_params *p);
-EventPair take_events(hs_sketch *h);
+hs_status take_events(hs_sketch *h, EventPair *out);
 void drain_timings(hs_sketch *h);
+hs_status check_ranked(const uint64_t *keys, const int32_t *est, uint64_t n);
 void free_topk_scratch(hs_sketch *h);
 hs_status ensure_topk_scratch(hs_sketch *h, uint64_t k);
 void free_dir(hs_sketch *h);

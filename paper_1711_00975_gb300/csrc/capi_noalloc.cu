@@ -6,15 +6,15 @@
 // ---------------------------------------------------------------------------
 // sketch_query_noalloc: point queries without any device allocation.
 //
-// Some callers cannot call cudaMalloc at the moment they query: code running
-// while a CUDA stream is being captured into a graph (allocation is not a
-// capturable operation), processes whose device memory is fully reserved by
-// another allocator or a fixed budget, and latency-critical loops where an
-// allocation's synchronisation is not acceptable.  sketch_query may allocate
-// staging buffers on its first call with host arrays; this variant instead
-// uses one file-scope device array, sized for at most
-// HS_NOALLOC_QUERY_MAX keys, that every GPU loading this library holds until
-// the process exits.
+// Some callers cannot call cudaMalloc at the moment they query: processes
+// whose device memory is fully reserved by another allocator or held to a
+// fixed budget, and query loops that must not pay for an allocation (a
+// cudaMalloc may synchronise the device).  sketch_query may allocate staging
+// buffers on its first call with host arrays; this variant instead uses one
+// file-scope device array, sized for at most HS_NOALLOC_QUERY_MAX keys, that
+// every GPU loading this library holds until the process exits.  The call is
+// synchronous (it waits for the handle's stream to read back the bad-key
+// flag), so it is not for code whose stream is being captured into a graph.
 // ---------------------------------------------------------------------------
 
 namespace {
@@ -49,32 +49,6 @@ hs_status noalloc_scratch(int dev, unsigned char **out) {
     return HS_OK;
 }
 
-// Estimate (Sec. 2.2) of each key; keys >= G^3 give 0 and set *bad.
-__global__ void k_point_query_noalloc(const int32_t *__restrict__ C, const SketchDesc d,
-                                      const uint64_t *__restrict__ keys, uint64_t m,
-                                      int32_t *__restrict__ est, uint32_t *__restrict__ bad) {
-    const uint64_t n_cells = (uint64_t)d.G * d.G * d.G;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-        uint64_t key = keys[i];
-        if (key >= n_cells) {
-            est[i] = 0;
-            atomicOr(bad, 1u);
-            continue;
-        }
-        uint32_t cx = (uint32_t)(key % d.G);
-        uint64_t rest = key / d.G;
-        uint32_t cy = (uint32_t)(rest % d.G), cz = (uint32_t)(rest / d.G);
-        int32_t ev[kMaxRows];
-        for (uint32_t r = 0; r < d.rows; ++r) {
-            uint64_t v = row_value(d.seed[r], cx, cy, cz);
-            ev[r] = signed_count(C[r * d.W + bucket_of(v, d.log2w)], v, d.log2w);
-        }
-        est[i] = d.rows == 5 ? median5(ev[0], ev[1], ev[2], ev[3], ev[4])
-                             : lower_median_dyn(ev, (int)d.rows);
-    }
-}
-
 }  // namespace
 
 extern "C" hs_status sketch_query_noalloc(hs_sketch *h, const uint64_t *keys, uint64_t m,
@@ -106,14 +80,14 @@ extern "C" hs_status sketch_query_noalloc(hs_sketch *h, const uint64_t *keys, ui
         dk = s_keys;
     }
     HS_CUDA(cudaMemsetAsync(s_flag, 0, 4, h->stream));   // the previous call's flag stays otherwise
-    uint64_t blocks = std::min<uint64_t>((m + 255) / 256, 65535);
-    k_point_query_noalloc<<<(unsigned)blocks, 256, 0, h->stream>>>(h->C, h->d, dk, m, de, s_flag);
-    HS_CUDA(cudaGetLastError());
+    // the same estimate kernel as sketch_query, on the static scratch
+    HS_CUDA(launch_point_query(h->C, h->d, dk, m, de, s_flag, h->stream));
     h->stats.kernel_launches += 1;
     if (!ed) HS_CUDA(cudaMemcpyAsync(est, de, m * 4, cudaMemcpyDeviceToHost, h->stream));
     uint32_t bad = 0;
     HS_CUDA(cudaMemcpyAsync(&bad, s_flag, 4, cudaMemcpyDeviceToHost, h->stream));
     HS_CUDA(cudaStreamSynchronize(h->stream));
+    drain_timings(h);
     if (bad) return fail(HS_ERR_ARG, "a key is >= G^3 = %llu", (unsigned long long)h->n_cells);
     return HS_OK;
 }

@@ -1,8 +1,8 @@
 """sketch_query_noalloc: point queries for callers that cannot allocate device
-memory when they query (for example while their stream is being captured into
-a CUDA graph, or when another allocator owns the device memory).  Its results
-must equal sketch_query's, call after call, although every call reuses the
-same static scratch array of the library.
+memory when they query (another allocator owns the device memory, or a fixed
+budget leaves none to spare).  Its results must equal sketch_query's, call
+after call, although every call reuses the same static scratch array of the
+library.
 
 Collected last on purpose; it also passes when run alone in a fresh process.
 """
@@ -74,4 +74,26 @@ def test_noalloc_query_limits_and_bad_keys(hs):
     est2 = np.empty(99, np.int32)
     hs.sketch_query_noalloc(sk.h, np.delete(bad, 17), est2)
     assert np.array_equal(est2, want)
+    sk.close()
+
+
+def test_noalloc_query_at_the_limit_and_with_mixed_arrays(hs):
+    sk, keys = _sketch(hs, 11, 15)
+    rng = np.random.default_rng(11)
+    m = hs.HS_NOALLOC_QUERY_MAX
+    full = np.concatenate([keys, rng.integers(0, sk.n_cells, m - keys.size, dtype=np.uint64)])
+    assert full.size == m
+    want = sk.query(full)
+    for _ in range(2):
+        est = np.full(m, -7, np.int32)
+        hs.sketch_query_noalloc(sk.h, full, est)              # exactly the maximum
+        assert np.array_equal(est, want)
+    part = full[:70000]
+    # host keys with a device est, and device keys with a host est
+    dest = torch.full((part.size,), -7, dtype=torch.int32, device="cuda")
+    hs.sketch_query_noalloc(sk.h, part, dest)
+    assert np.array_equal(dest.cpu().numpy(), want[:part.size])
+    hest = np.full(part.size, -7, np.int32)
+    hs.sketch_query_noalloc(sk.h, torch.from_numpy(part).cuda(), hest)
+    assert np.array_equal(hest, want[:part.size])
     sk.close()
