@@ -27,7 +27,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 SCATTER_SOURCES = [os.path.join(ROOT, "paper_1711_00975_gb300", "csrc", f)
-                   for f in ("k_binned.cu", "hs_device.cuh")]
+                   for f in ("k_binned.cuh", "k_binned.cu", "hs_device.cuh")]
 sys.path.insert(0, ROOT)
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")

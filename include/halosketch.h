@@ -298,7 +298,7 @@ typedef struct hs_batch hs_batch;
 
 /* Scatter configuration chosen by batch_autotune. */
 typedef struct {
-    uint32_t threads;        /* threads per block of the scatter kernel           */
+    uint32_t rounds;         /* tiles of 4096 particles staged between flushes    */
     uint32_t slot;           /* shared-memory ring depth (codes per bin)          */
     uint32_t configs_tried;
     float best_ms;           /* its time for the tuning data                      */

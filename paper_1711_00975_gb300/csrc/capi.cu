@@ -296,19 +296,54 @@ hs_status ensure_query_scratch(hs_sketch *h, uint64_t m) {
 }
 
 
+uint32_t region_capacity(double mean, uint32_t half, double pad_halves) {
+    const double c = 1.08 * mean + 8.0 * std::sqrt(mean) + 64.0 + (pad_halves + 1.0) * half;
+    const double most = 4294967040.0;
+    return (uint32_t)((std::min(c, most) + 15.0) / 16.0) * 16u;
+}
+
+hs_status alloc_bins(BinBuffers &bb, const std::vector<uint32_t> &caps, uint32_t bpg,
+                     uint32_t nblocks, cudaStream_t s) {
+    free_bins(bb);
+    const size_t ng = caps.size();
+    if (ng == 0 || ng > kMaxBinGroups) return fail(HS_ERR_ARG, "%zu region groups (at most %u)", ng, kMaxBinGroups);
+    std::vector<uint64_t> base(ng);
+    uint64_t total = 0;
+    uint32_t lo = 0xFFFFFFFFu;
+    for (size_t g = 0; g < ng; ++g) {
+        base[g] = total;
+        total += (uint64_t)caps[g] * bpg * nblocks;
+        lo = std::min(lo, caps[g]);
+    }
+    HS_CUDA(cudaMalloc(&bb.codes, std::max<uint64_t>(total, 8) * 2));
+    HS_CUDA(cudaMalloc(&bb.gbase, ng * 8));
+    HS_CUDA(cudaMalloc(&bb.gcap, ng * 4));
+    HS_CUDA(cudaMalloc(&bb.fill, ng * bpg * nblocks * 4));
+    HS_CUDA(cudaMemcpyAsync(bb.gbase, base.data(), ng * 8, cudaMemcpyHostToDevice, s));
+    HS_CUDA(cudaMemcpyAsync(bb.gcap, caps.data(), ng * 4, cudaMemcpyHostToDevice, s));
+    HS_CUDA(cudaMemsetAsync(bb.fill, 0, ng * bpg * nblocks * 4, s));
+    HS_CUDA(cudaStreamSynchronize(s));   // the host vectors go out of scope
+    bb.nblocks = nblocks;
+    bb.bpg = bpg;
+    bb.ngroups = (uint32_t)ng;
+    bb.min_cap = lo;
+    return HS_OK;
+}
+
+void free_bins(BinBuffers &bb) {
+    void *ps[] = {bb.codes, bb.fill, bb.gbase, bb.gcap};
+    for (void *p : ps)
+        if (p) cudaFree(p);
+    bb = BinBuffers{};
+}
+
 // add every binned code to the counters (before anything reads them)
 hs_status drain(hs_sketch *h) {
     if (h->pending <= 0) return HS_OK;
     EventPair ev;
     HS_TRY(take_events(h, &ev));
     cudaEventRecord(ev.a, h->stream);
-    if (h->carry_valid) {
-        HS_CUDA(launch_carry_flush(h->bl, h->carry, (uint32_t)h->num_sms, h->bins, h->bin_cursor,
-                                   h->bin_cap, h->C, h->stream));
-        h->carry_valid = false;
-        h->stats.kernel_launches += 1;
-    }
-    HS_CUDA(launch_bin_accumulate(h->bl, h->bins, h->bin_cursor, h->bin_cap, h->C, h->stream));
+    HS_CUDA(launch_bin_accumulate(h->bl, h->bb.store(), h->C, h->stream));
     cudaEventRecord(ev.b, h->stream);
     h->pending_flush.push_back(ev);
     h->stats.kernel_launches += 1;
@@ -319,10 +354,9 @@ hs_status drain(hs_sketch *h) {
 
 // drop binned codes that were never drained (reset / load)
 hs_status discard_pending(hs_sketch *h) {
-    if (h->pending > 0 && h->bin_cursor)
-        HS_CUDA(cudaMemsetAsync(h->bin_cursor, 0, (size_t)h->bl.nbins * 4, h->stream));
+    if (h->pending > 0 && h->bb.fill)
+        HS_CUDA(cudaMemsetAsync(h->bb.fill, 0, (size_t)h->bl.nbins * h->bb.nblocks * 4, h->stream));
     h->pending = 0;
-    h->carry_valid = false;
     return HS_OK;
 }
 
@@ -334,25 +368,22 @@ bool want_binned(hs_sketch *h, uint64_t n, double rate) {
     return (double)n * rate * h->d.rows >= kBinnedMinUpdates;
 }
 
-hs_status ensure_bins(hs_sketch *h, uint64_t n, double rate) {
-    if (h->bins) return HS_OK;
-    const double per_bin = (double)(1ull << (h->d.log2w - h->bl.S));   // bins per row
-    uint64_t want = (uint64_t)(1.3 * (double)n * rate / per_bin) + 8192;
-    uint64_t most = kBinBudgetBytes / (2ull * h->bl.nbins);
-    uint64_t cap = std::min(want, most);
-    cap = std::max<uint64_t>(cap, 4096);
-    cap = std::min<uint64_t>(cap, 0xFFFFFFF0ull);
-    cap = (cap + 15) & ~15ull;
-    HS_CUDA(cudaMalloc(&h->carry, (size_t)h->num_sms * carry_words16(h->bl) * 16));
-    HS_CUDA(cudaMalloc(&h->bins, (size_t)h->bl.nbins * cap * 2));
-    HS_CUDA(cudaMalloc(&h->bin_cursor, (size_t)h->bl.nbins * 4));
-    HS_CUDA(cudaMemsetAsync(h->bin_cursor, 0, (size_t)h->bl.nbins * 4, h->stream));
-    h->bin_cap = (uint32_t)cap;
-    // expected codes per bin = kept particles / bins per row; keep a margin of
-    // 20 % and 6 standard deviations below the capacity
-    double c = (double)cap;
-    double safe = c - 6.0 * std::sqrt(c) - 4096.0;
-    h->pending_limit = std::max(0.0, 0.8 * safe) * per_bin;
+// Regions sized for a call of n particles in `launches` scatter launches (a
+// host buffer is staged in pieces, each its own launch).  Every bin of a plain
+// sketch receives the same expected share.
+hs_status ensure_bins(hs_sketch *h, uint64_t n, double rate, uint64_t launches) {
+    if (h->bb.codes) return HS_OK;
+    const uint32_t nblocks = (uint32_t)h->num_sms;
+    const double per_region = (double)n * rate * h->d.rows / ((double)h->bl.nbins * nblocks);
+    uint32_t cap = region_capacity(per_region, h->bl.half, (double)launches);
+    const uint64_t most = kBinBudgetBytes / (2ull * h->bl.nbins * nblocks);
+    cap = (uint32_t)std::min<uint64_t>(cap, most & ~15ull);
+    cap = std::max<uint32_t>(cap, std::max<uint32_t>(4 * h->bl.slot, 1024));
+    HS_TRY(alloc_bins(h->bb, std::vector<uint32_t>(1, cap), h->bl.nbins, nblocks, h->stream));
+    // drain before the expected fill of a region comes within 8 standard
+    // deviations and 64 codes of its capacity
+    const double c = (double)cap;
+    h->pending_limit = std::max(0.0, c - 8.0 * std::sqrt(c) - 64.0);
     return HS_OK;
 }
 
@@ -361,39 +392,44 @@ hs_status launch_update_timed(hs_sketch *h, const float *xyz, uint64_t n, uint64
                               double rate, bool packed) {
     const size_t esz = packed ? 8 : 12;
     if (want_binned(h, n, rate)) {
-        hs_status st = ensure_bins(h, n, rate);
-        if (st != HS_OK) return st;
-        if (h->routing && h->pending_limit < 1.0)
-            return fail(HS_ERR_STATE, "routing needs bins of useful capacity");
-        if (h->pending_limit >= 1.0) {
-            // launches small enough that no bin is expected to fill
-            uint64_t piece = (uint64_t)std::max(1.0, h->pending_limit / rate);
-            for (uint64_t off = 0; off < n; off += piece) {
-                uint64_t cnt = std::min(piece, n - off);
-                if (h->pending + (double)cnt * rate > h->pending_limit) {
-                    st = drain(h);
-                    if (st != HS_OK) return st;
-                }
-                EventPair ev;
-                HS_TRY(take_events(h, &ev));
-                cudaEventRecord(ev.a, h->stream);
-                const float *src = reinterpret_cast<const float *>(
-                    reinterpret_cast<const char *>(xyz) + off * esz);
-                HS_CUDA(launch_bin_scatter(src, cnt, g0 + off, h->d, h->C, rate,
-                                           h->p.sample_seed, h->probe, h->probe_base, kProbeCap,
-                                           h->bl, h->bins, h->bin_cursor, h->bin_cap, h->num_sms,
-                                           h->stream, nullptr, 0, 0, 1024,
-                                           h->routing ? &h->route : nullptr, h->carry,
-                                           h->carry_valid ? 1 : 0, 1, packed ? 1 : 0));
-                h->carry_valid = true;
-                cudaEventRecord(ev.b, h->stream);
-                h->pending_update.push_back(ev);
-                h->pending += (double)cnt * rate;
-                h->stats.update_launches += 1;
-                h->stats.kernel_launches += 1;
+        if (h->bb.codes) {   // regions sized for a smaller call: grow them for this one
+            const double mean = (double)n * rate * h->d.rows / ((double)h->bl.nbins * h->bb.nblocks);
+            if (region_capacity(mean, h->bl.half, 1.0) > h->bb.min_cap && !h->routing) {
+                HS_TRY(drain(h));
+                HS_CUDA(cudaStreamSynchronize(h->stream));
+                free_bins(h->bb);
             }
-            return HS_OK;
         }
+        HS_TRY(ensure_bins(h, n, rate));
+        // expected codes per region of one particle; each launch adds at most
+        // one partial half (padded) per region
+        const double per = rate * h->d.rows / ((double)h->bl.nbins * h->bb.nblocks);
+        const double room = h->pending_limit - h->bl.half;
+        if (room < 1.0) {
+            if (h->routing) return fail(HS_ERR_STATE, "routing needs regions of useful capacity");
+            return launch_update_direct(h, xyz, n, g0, rate, packed);
+        }
+        const uint64_t piece = std::max<uint64_t>(4, (uint64_t)std::floor(room / per) & ~3ull);
+        for (uint64_t off = 0; off < n; off += piece) {
+            const uint64_t cnt = std::min(piece, n - off);
+            const double add = (double)cnt * per + h->bl.half;
+            if (h->pending + add > h->pending_limit) HS_TRY(drain(h));
+            EventPair ev;
+            HS_TRY(take_events(h, &ev));
+            cudaEventRecord(ev.a, h->stream);
+            const float *src = reinterpret_cast<const float *>(
+                reinterpret_cast<const char *>(xyz) + off * esz);
+            HS_CUDA(launch_bin_scatter(src, cnt, g0 + off, h->d, h->C, rate, h->p.sample_seed,
+                                       h->probe, h->probe_base, kProbeCap, h->bl, h->bb.store(),
+                                       h->stream, nullptr, 0, 0,
+                                       h->routing ? &h->route : nullptr, packed ? 1 : 0));
+            cudaEventRecord(ev.b, h->stream);
+            h->pending_update.push_back(ev);
+            h->pending += add;
+            h->stats.update_launches += 1;
+            h->stats.kernel_launches += 1;
+        }
+        return HS_OK;
     }
     return launch_update_direct(h, xyz, n, g0, rate, packed);
 }
@@ -625,9 +661,7 @@ hs_status sketch_destroy(hs_sketch *h) {
     if (h->super) sketch_destroy(h->super);
     free_topk_scratch(h);
     free_dir(h);
-    if (h->bins) cudaFree(h->bins);
-    if (h->carry) cudaFree(h->carry);
-    if (h->bin_cursor) cudaFree(h->bin_cursor);
+    free_bins(h->bb);
     if (h->C && !h->is_view) cudaFree(h->C);
     if (h->probe && !h->is_view) cudaFree(h->probe);
     if (h->q_keys) cudaFree(h->q_keys);
@@ -673,9 +707,10 @@ static hs_status update_common(hs_sketch *h, const void *src, uint64_t n, double
         if (st != HS_OK) return st;
         // size the bins for the whole call, not for one staged piece
         const uint64_t first = std::min(kStageParticles, n);
-        if (want_binned(h, first, sample_rate)) st = ensure_bins(h, n, sample_rate);
+        const uint64_t pieces = (n + kStageParticles - 1) / kStageParticles;
+        if (want_binned(h, first, sample_rate)) st = ensure_bins(h, n, sample_rate, pieces);
         if (st == HS_OK && h->super && want_binned(h->super, first, sample_rate))
-            st = ensure_bins(h->super, n, sample_rate);
+            st = ensure_bins(h->super, n, sample_rate, pieces);
         if (st != HS_OK) return st;
         int i = 0;
         for (uint64_t off = 0; off < n; off += kStageParticles, ++i) {

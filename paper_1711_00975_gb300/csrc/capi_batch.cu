@@ -29,12 +29,11 @@ struct hs_batch {
     int32_t *C = nullptr;               // nvol x rows x W
     uint64_t *probe = nullptr;          // nvol x kBatchProbe
     BinLayout bl{};                     // over nvol * rows rows
-    uint16_t *bins = nullptr;
-    uint32_t *cursor = nullptr;
-    uint32_t cap = 0;
+    BinBuffers bb;                      // code regions, sized per volume
+    uint32_t rounds = 0;                // scatter tiles between flushes (0: default)
+    uint32_t slot = 0;                  // scatter ring depth (0: largest that fits)
     VolumeDesc *d_vols = nullptr;
     VolumeDesc *h_vols = nullptr;       // pinned: read by the graph's copy node
-    int threads = 1024;
     hs_sketch *view = nullptr;          // views[0]
     std::vector<hs_sketch *> views;     // top-k of one volume each, concurrently, own streams
     std::vector<cudaEvent_t> vdone;     // each view's stream has finished
@@ -67,29 +66,33 @@ SketchDesc batch_flat_desc(const hs_batch *b) {
     return dd;
 }
 
+// Regions sized per volume: a volume of N particles spans about N / tile + 2
+// scatter tiles, dealt round-robin to the blocks, and each tile adds tile *
+// rate / (bins per row) codes to each of the volume's bins on average.
 hs_status batch_ensure_bins(hs_batch *b, const uint64_t *offsets, double rate) {
-    if (b->bins) return HS_OK;
-    const double bins_per_row = (double)(1ull << (b->d.log2w - b->bl.S));
-    uint64_t most = 0;
-    for (uint32_t v = 0; v < b->nvol; ++v) most = std::max(most, offsets[v + 1] - offsets[v]);
-    uint64_t want = (uint64_t)(1.3 * (double)most * rate / bins_per_row) + 8192;
-    uint64_t cap = std::min<uint64_t>(want, kBinBudgetBytes / (2ull * b->bl.nbins));
-    cap = std::min<uint64_t>(std::max<uint64_t>(cap, 4096), 0xFFFFFFF0ull);
-    cap = (cap + 15) & ~15ull;
-    HS_CUDA(cudaMalloc(&b->bins, (size_t)b->bl.nbins * cap * 2));
-    b->cap = (uint32_t)cap;
-    return HS_OK;
+    if (b->bb.codes) return HS_OK;
+    const uint32_t nblocks = (uint32_t)b->num_sms;
+    const uint32_t bpr = 1u << (b->d.log2w - b->bl.S);
+    const uint32_t bpv = b->d.rows * bpr;
+    std::vector<uint32_t> caps(b->nvol);
+    for (uint32_t v = 0; v < b->nvol; ++v) {
+        const uint64_t N = offsets[v + 1] - offsets[v];
+        const uint64_t tiles = N / kScatterTile + 2;
+        const uint64_t per_block = (tiles + nblocks - 1) / nblocks;
+        const double mean = (double)per_block * kScatterTile * rate / bpr;
+        caps[v] = std::max<uint32_t>(region_capacity(mean, b->bl.half, 1.0), 4 * b->bl.slot);
+    }
+    return alloc_bins(b->bb, caps, bpv, nblocks, b->stream);
 }
 
 // scatter + accumulate of the whole batch on b->stream (captured or direct)
 hs_status batch_enqueue(hs_batch *b, const float *xyz, uint64_t n, double rate) {
     HS_CUDA(cudaMemcpyAsync(b->d_vols, b->h_vols, b->nvol * sizeof(VolumeDesc),
                             cudaMemcpyHostToDevice, b->stream));
-    int grid = b->num_sms * (b->threads == 512 ? 2 : 1);
     HS_CUDA(launch_bin_scatter(xyz, n, 0, b->d, b->C, rate, b->p.sample_seed, b->probe, 0,
-                               kBatchProbe, b->bl, b->bins, b->cursor, b->cap, grid, b->stream,
-                               b->d_vols, b->nvol, kBatchProbe, b->threads));
-    HS_CUDA(launch_bin_accumulate(b->bl, b->bins, b->cursor, b->cap, b->C, b->stream));
+                               kBatchProbe, b->bl, b->bb.store(), b->stream, b->d_vols, b->nvol,
+                               kBatchProbe, nullptr, 0, b->rounds, b->slot));
+    HS_CUDA(launch_bin_accumulate(b->bl, b->bb.store(), b->C, b->stream));
     return HS_OK;
 }
 
@@ -165,7 +168,7 @@ hs_status batch_create(const hs_params *params, uint32_t n_volumes, const double
     b->d.Gq = b->d.G;
     b->d.F = 1;
     b->bl = bin_layout(batch_flat_desc(b), kBinSmemBudget);
-    if (b->bl.slot == 0 || b->bl.nbins >= 65536) {
+    if (b->bl.slot == 0 || b->bl.nbins >= 65536 || n_volumes > kMaxBinGroups) {
         delete b;
         return fail(HS_ERR_ARG, "%u volumes x %u rows x 2^%u counters need too many bins; "
                     "split the batch", n_volumes, p.rows, p.log2_width);
@@ -182,7 +185,6 @@ hs_status batch_create(const hs_params *params, uint32_t n_volumes, const double
     }
     if (e == cudaSuccess) e = cudaMalloc(&b->C, counters * 4);
     if (e == cudaSuccess) e = cudaMalloc(&b->probe, (size_t)n_volumes * kBatchProbe * 8);
-    if (e == cudaSuccess) e = cudaMalloc(&b->cursor, (size_t)b->bl.nbins * 4);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_vols, n_volumes * sizeof(VolumeDesc));
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_vols, n_volumes * sizeof(VolumeDesc));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
@@ -191,7 +193,6 @@ hs_status batch_create(const hs_params *params, uint32_t n_volumes, const double
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev_b);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->C, 0, counters * 4, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->probe, 0xFF, (size_t)n_volumes * kBatchProbe * 8, b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->cursor, 0, (size_t)b->bl.nbins * 4, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     const uint32_t nviews = std::min<uint32_t>(n_volumes, kBatchViews);
     for (uint32_t t = 0; t < nviews && e == cudaSuccess; ++t) {
@@ -237,7 +238,8 @@ hs_status batch_destroy(hs_batch *b) {
         if (vs) cudaStreamDestroy(vs);
         if (b->vdone[t]) cudaEventDestroy(b->vdone[t]);
     }
-    void *ps[] = {b->C, b->probe, b->cursor, b->d_vols, b->bins};
+    free_bins(b->bb);
+    void *ps[] = {b->C, b->probe, b->d_vols};
     for (void *q : ps)
         if (q) cudaFree(q);
     for (auto *q : b->vdir_off)
@@ -384,7 +386,8 @@ hs_status batch_reset(hs_batch *b) {
     if (!b) return fail(HS_ERR_ARG, "batch is NULL");
     HS_CUDA(cudaMemsetAsync(b->C, 0, (size_t)b->nvol * b->d.rows * b->d.W * 4, b->stream));
     HS_CUDA(cudaMemsetAsync(b->probe, 0xFF, (size_t)b->nvol * kBatchProbe * 8, b->stream));
-    HS_CUDA(cudaMemsetAsync(b->cursor, 0, (size_t)b->bl.nbins * 4, b->stream));
+    if (b->bb.fill)
+        HS_CUDA(cudaMemsetAsync(b->bb.fill, 0, (size_t)b->bl.nbins * b->bb.nblocks * 4, b->stream));
     std::fill(b->n_seen.begin(), b->n_seen.end(), 0);
     std::fill(b->probe_base.begin(), b->probe_base.end(), 0);
     return HS_OK;
@@ -438,24 +441,18 @@ hs_status batch_autotune(hs_batch *b, const float *xyz, const uint64_t *offsets,
     st = batch_ensure_bins(b, offsets, sample_rate);
     if (st != HS_OK) return st;
     batch_drop_graph(b);
-    const BinLayout base = b->bl;
-    const int threads_opt[2] = {1024, 512};
-    const uint32_t slot_opt[2] = {32, 16};
+    // candidates: the ring depth that fits and half of it, by 1 or 2 tiles
+    // staged between flush phases
+    const uint32_t slot_opt[2] = {0, b->bl.slot / 2};
+    const uint32_t rounds_opt[2] = {1, 2};
     float best = 1e30f;
-    int best_t = b->threads;
-    BinLayout best_l = base;
+    uint32_t best_slot = 0, best_rounds = 1;
     int tried = 0;
-    for (int ti = 0; ti < 2; ++ti)
-        for (int si = 0; si < 2; ++si) {
-            BinLayout L = base;
-            L.slot = slot_opt[si];
-            size_t queue = (size_t)(1024 / 32) * 128 * 8;
-            L.smem = ((L.nbins * 4 + 15) & ~15ull) + ((L.nbins * L.slot * 2 + 15) & ~15ull) + queue +
-                     ((L.nbins + 31) / 32) * 4;
-            if (L.smem > kBinSmemBudget) continue;
-            if (threads_opt[ti] == 512 && L.nbins > 6u * 512) continue;
-            b->bl = L;
-            b->threads = threads_opt[ti];
+    for (int si = 0; si < 2; ++si)
+        for (int ri = 0; ri < 2; ++ri) {
+            if (slot_opt[si] == 1 || (si == 1 && slot_opt[si] < 16)) continue;
+            b->slot = slot_opt[si];
+            b->rounds = rounds_opt[ri];
             float ms_best = 1e30f;
             for (int rep = 0; rep < 2; ++rep) {
                 batch_fill_vols(b, offsets);
@@ -471,17 +468,17 @@ hs_status batch_autotune(hs_batch *b, const float *xyz, const uint64_t *offsets,
             ++tried;
             if (ms_best < best) {
                 best = ms_best;
-                best_t = threads_opt[ti];
-                best_l = L;
+                best_slot = slot_opt[si];
+                best_rounds = rounds_opt[ri];
             }
         }
-    b->bl = best_l;
-    b->threads = best_t;
+    b->slot = best_slot;
+    b->rounds = best_rounds;
     st = batch_reset(b);                              // tuning runs touched the counters
     if (st != HS_OK) return st;
     HS_CUDA(cudaStreamSynchronize(b->stream));
-    out->threads = (uint32_t)best_t;
-    out->slot = best_l.slot;
+    out->rounds = best_rounds;
+    out->slot = best_slot ? best_slot : b->bl.slot;
     out->configs_tried = (uint32_t)tried;
     out->best_ms = best;
     return HS_OK;

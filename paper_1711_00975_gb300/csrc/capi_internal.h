@@ -43,7 +43,7 @@ constexpr uint64_t kStageParticles = 1ull << 24;  // 192 MiB per staging buffer
 constexpr int kStageBuffers = 3;                    // copies run ahead through a drain
 constexpr size_t kSearchSmemBudget = 192 * 1024;
 constexpr size_t kBinSmemBudget = 224 * 1024;
-constexpr uint64_t kBinBudgetBytes = 4ull << 30;   // global bins, at most
+constexpr uint64_t kBinBudgetBytes = 16ull << 30;  // global code regions of one sketch, at most
 constexpr double kBinnedMinUpdates = 1 << 20;      // smaller calls add directly
 constexpr uint64_t kMaxScanCells = 1ull << 40;      // largest full scan one top-k may run
 constexpr uint32_t kBatchViews = 8;                 // volumes whose top-k run concurrently
@@ -52,6 +52,28 @@ constexpr size_t kMaxPendingEvents = 256;           // timing pairs kept before 
 struct EventPair {
     cudaEvent_t a, b;
 };
+
+// Global code regions of a binned update (see BinStore) and their host-side
+// sizes.
+struct BinBuffers {
+    uint16_t *codes = nullptr;
+    uint32_t *fill = nullptr;
+    uint64_t *gbase = nullptr;
+    uint32_t *gcap = nullptr;
+    uint32_t nblocks = 0, bpg = 0, ngroups = 0;
+    uint32_t min_cap = 0;       // smallest region capacity
+    BinStore store() const { return BinStore{codes, fill, gbase, gcap, nblocks, bpg, ngroups}; }
+};
+
+// Region capacity (codes, a multiple of 16) for `mean` expected codes per
+// region: 8 % and 8 standard deviations of margin, plus `pad_halves` partial
+// halves (one per launch) of `half` entries.
+uint32_t region_capacity(double mean, uint32_t half, double pad_halves);
+// Allocate regions for groups of bpg bins, group g's regions of caps[g] codes
+// (multiples of 16), nblocks per bin; fills zeroed.
+hs_status alloc_bins(BinBuffers &bb, const std::vector<uint32_t> &caps, uint32_t bpg,
+                     uint32_t nblocks, cudaStream_t s);
+void free_bins(BinBuffers &bb);
 
 }  // namespace capi
 }  // namespace hs
@@ -123,15 +145,11 @@ struct hs_sketch {
     bool routing = false;                 // learned router: routed cells go to a table
     RouteTarget route{};
 
-    // binned update: codes waiting in global bins until the next drain
+    // binned update: codes waiting in the global regions until the next drain
     BinLayout bl{};
-    uint16_t *bins = nullptr;
-    uint32_t *bin_cursor = nullptr;
-    uint32_t bin_cap = 0;
-    uint4 *carry = nullptr;         // scatter rings carried from one launch to the next
-    bool carry_valid = false;
-    double pending = 0;          // kept particles binned since the last drain
-    double pending_limit = 0;    // drain before the expected bin load passes this
+    BinBuffers bb;
+    double pending = 0;          // expected codes per region since the last drain
+    double pending_limit = 0;    // drain before the expected fill passes this
 
     // benchmarking
     hs_stats stats;
@@ -157,7 +175,7 @@ hs_status ensure_query_scratch(hs_sketch *h, uint64_t m);
 hs_status drain(hs_sketch *h);
 hs_status discard_pending(hs_sketch *h);
 bool want_binned(hs_sketch *h, uint64_t n, double rate);
-hs_status ensure_bins(hs_sketch *h, uint64_t n, double rate);
+hs_status ensure_bins(hs_sketch *h, uint64_t n, double rate, uint64_t launches = 1);
 hs_status launch_update_timed(hs_sketch *h, const float *xyz, uint64_t n, uint64_t g0,
                               double rate, bool packed = false);
 hs_status launch_update_direct(hs_sketch *h, const float *xyz, uint64_t n, uint64_t g0,

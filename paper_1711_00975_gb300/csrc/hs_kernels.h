@@ -26,13 +26,35 @@ struct VolumeDesc {
     uint32_t bin0;
     uint32_t pad;
 };
+// Shared-memory layout of the binned scatter: per bin a ring of `slot` 16-bit
+// codes in two halves, flushed a half at a time between block barriers;
+// per-warp queues of kept cells for sampled calls.
 struct BinLayout {
     uint32_t S;        // log2 counters per bin
     uint32_t nbins;    // rows * W / 2^S
-    uint32_t slot;     // shared-memory staging entries per bin (0: binning unavailable)
-    size_t smem;       // dynamic shared memory of the scatter kernel
+    uint32_t slot;     // ring entries per bin (0: binning unavailable)
+    uint32_t half;     // flush granule in entries (slot / 2, a multiple of 8)
+    size_t smem;       // dynamic shared memory of the scatter kernel (no queues)
 };
 BinLayout bin_layout(const SketchDesc &d, size_t smem_budget);
+constexpr uint32_t kMaxBinGroups = 128;
+constexpr uint32_t kScatterTile = 3072;   // particles of one scatter tile (768 threads x 4)
+// Global side of the binned update.  Each scatter block owns one region per
+// bin.  Bins come in groups of bpg bins whose regions have the same capacity
+// (one group for a sketch, one per volume for a batch): region (bin j, block b)
+// of group g = j / bpg starts at code gbase[g] + (b bpg + j - g bpg) gcap[g],
+// so a block writes into one span of the group.  fill[j * nblocks + b]
+// codes of it are written (whole halves; the unused entries of a last,
+// partial half hold pairs of codes that cancel).
+struct BinStore {
+    uint16_t *codes;
+    uint32_t *fill;            // per (bin, block), codes written since the last accumulation
+    const uint64_t *gbase;     // per group
+    const uint32_t *gcap;      // per group: codes per region (a multiple of 16)
+    uint32_t nblocks;          // scatter blocks (regions per bin)
+    uint32_t bpg;              // bins per group
+    uint32_t ngroups;          // <= kMaxBinGroups
+};
 // where routed particles go: one dense block of R^3 int32 counters per routed
 // coarse cell, blocks in coarse-key order; the block of routed cell ck is
 // prefix[ck / 32] + (number of routed cells below ck in its bitmap word)
@@ -42,23 +64,19 @@ struct RouteTarget {
     int32_t *blocks;
 };
 // xyz: float32 positions, or 64-bit packed records when packed != 0 (plain and
-// super-item sketches only)
+// super-item sketches only).  Launches B.nblocks blocks.  rounds: tiles of
+// 3072 particles a block stages between flush phases (0: chosen from the rate);
+// slot: ring depth (0: the largest that fits shared memory).
 cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const SketchDesc &d,
                                int32_t *C, double rate, uint64_t sample_seed, uint64_t *probe,
                                uint64_t probe_base, uint64_t probe_cap, const BinLayout &L,
-                               uint16_t *bins, uint32_t *cursor, uint32_t cap, int blocks,
-                               cudaStream_t s, const VolumeDesc *vols = nullptr, uint32_t nvol = 0,
-                               uint32_t probe_per_vol = 0, int threads = 1024,
-                               const RouteTarget *route = nullptr, uint4 *carry = nullptr,
-                               int carry_in = 0, int carry_out = 0, int packed = 0);
-// 16-byte words of one scatter block's carried rings (fill words + rings)
-uint32_t carry_words16(const BinLayout &L);
-// move the carried rings of nblocks scatter blocks into the global bins
-cudaError_t launch_carry_flush(const BinLayout &L, const uint4 *carry, uint32_t nblocks,
-                               uint16_t *bins, uint32_t *cursor, uint32_t cap, int32_t *C,
-                               cudaStream_t s);
-cudaError_t launch_bin_accumulate(const BinLayout &L, uint16_t *bins, uint32_t *cursor,
-                                  uint32_t cap, int32_t *C, cudaStream_t s);
+                               const BinStore &B, cudaStream_t s,
+                               const VolumeDesc *vols = nullptr, uint32_t nvol = 0,
+                               uint32_t probe_per_vol = 0, const RouteTarget *route = nullptr,
+                               int packed = 0, uint32_t rounds = 0, uint32_t slot = 0);
+// C[bin range] += the codes of every region, then fill = 0
+cudaError_t launch_bin_accumulate(const BinLayout &L, const BinStore &B, int32_t *C,
+                                  cudaStream_t s);
 
 // ---- learned router (k_learned.cu) ----
 cudaError_t launch_coarse_hist(const float *xyz, uint64_t n, uint64_t g0, const SketchDesc &d,

@@ -48,7 +48,7 @@ class hs_info(ctypes.Structure):
 
 
 class hs_tune(ctypes.Structure):
-    _fields_ = [("threads", ctypes.c_uint32), ("slot", ctypes.c_uint32),
+    _fields_ = [("rounds", ctypes.c_uint32), ("slot", ctypes.c_uint32),
                 ("configs_tried", ctypes.c_uint32), ("best_ms", ctypes.c_float)]
 
 

@@ -81,7 +81,7 @@ def test_batch_autotune_then_exact(hs):
     b = hs.Batch(5, 16, [s.box for s in specs], 0.1, hash_seed=11, sample_seed=2)
     d = torch.from_numpy(xyz).cuda()
     tune = b.autotune(d, off, 0.5)
-    assert tune["configs_tried"] >= 2 and tune["threads"] in (512, 1024)
+    assert tune["configs_tried"] >= 2 and tune["rounds"] in (1, 2)
     assert b.info(0).n_seen == 0 and not b.counters(1).any()     # tuning reset the batch
     b.update(d, off, 0.5)
     for v, spec in enumerate(specs):
