@@ -122,6 +122,8 @@ typedef struct {
     uint32_t last_passes;       /* full-search passes of the last query        */
     uint64_t flush_launches;    /* launches accumulating binned increments     */
     double flush_ms;            /* their summed device time (part of update_ms)*/
+    uint64_t h2d_bytes;         /* bytes staged from host buffers              */
+    double h2d_ms;              /* summed device time of those copies          */
 } hs_stats;
 
 /*

@@ -62,7 +62,7 @@ hs_status check_params(const hs_params *p) {
 // loop of updates and point queries neither grows them nor creates events
 // without end.
 hs_status take_events(hs_sketch *h, EventPair *out) {
-    for (auto *v : {&h->pending_update, &h->pending_search, &h->pending_flush}) {
+    for (auto *v : {&h->pending_update, &h->pending_search, &h->pending_flush, &h->pending_copy}) {
         if (v->size() < kMaxPendingEvents) continue;
         const size_t half = v->size() / 2;
         HS_CUDA(cudaEventSynchronize((*v)[half - 1].b));
@@ -70,6 +70,7 @@ hs_status take_events(hs_sketch *h, EventPair *out) {
             float ms = 0;
             if (cudaEventElapsedTime(&ms, (*v)[i].a, (*v)[i].b) == cudaSuccess) {
                 if (v == &h->pending_search) h->stats.search_ms += ms;
+                else if (v == &h->pending_copy) h->stats.h2d_ms += ms;
                 else h->stats.update_ms += ms;
                 if (v == &h->pending_flush) h->stats.flush_ms += ms;
             }
@@ -120,6 +121,12 @@ void drain_timings(hs_sketch *h) {
         h->pool.push_back(e);
     }
     h->pending_flush.clear();
+    for (auto &e : h->pending_copy) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) h->stats.h2d_ms += ms;
+        h->pool.push_back(e);
+    }
+    h->pending_copy.clear();
     cudaGetLastError();
 }
 
@@ -673,7 +680,7 @@ hs_status sketch_destroy(hs_sketch *h) {
         if (h->ev_free[i]) cudaEventDestroy(h->ev_free[i]);
     }
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
-    for (auto *v : {&h->pending_update, &h->pending_search, &h->pending_flush, &h->pool})
+    for (auto *v : {&h->pending_update, &h->pending_search, &h->pending_flush, &h->pending_copy, &h->pool})
         for (auto &e : *v) {
             cudaEventDestroy(e.a);
             cudaEventDestroy(e.b);
@@ -717,8 +724,14 @@ static hs_status update_common(hs_sketch *h, const void *src, uint64_t n, double
             uint64_t cnt = std::min(kStageParticles, n - off);
             int b = i % kStageBuffers;
             HS_CUDA(cudaStreamWaitEvent(h->copy_stream, h->ev_free[b], 0));
+            EventPair ce;
+            HS_TRY(take_events(h, &ce));
+            HS_CUDA(cudaEventRecord(ce.a, h->copy_stream));
             HS_CUDA(cudaMemcpyAsync(h->stage[b], static_cast<const char *>(src) + off * esz,
                                     cnt * esz, cudaMemcpyHostToDevice, h->copy_stream));
+            HS_CUDA(cudaEventRecord(ce.b, h->copy_stream));
+            h->pending_copy.push_back(ce);
+            h->stats.h2d_bytes += cnt * esz;
             HS_CUDA(cudaEventRecord(h->ev_copied[b], h->copy_stream));
             HS_CUDA(cudaStreamWaitEvent(h->stream, h->ev_copied[b], 0));
             st = launch_update_timed(h, h->stage[b], cnt, h->n_seen + off, sample_rate, packed);

@@ -153,7 +153,7 @@ struct hs_sketch {
 
     // benchmarking
     hs_stats stats;
-    std::vector<EventPair> pending_update, pending_search, pending_flush, pool;
+    std::vector<EventPair> pending_update, pending_search, pending_flush, pending_copy, pool;
 };
 
 namespace hs {

@@ -1,18 +1,29 @@
 """Parity at the benchmark's full sizes, in the benchmark's launch configuration.
 
 Counters are compared whole (the oracle runs the same stream with private
-per-thread counters).  A top-k over 1.25e11 (or 8e12) cells is out of the
-oracle's reach, so it is checked on samples the oracle computes one by one:
-every returned estimate, the ranking, and completeness on sampled mesh lines
-(every cell of a sampled line that ranks ahead of the k-th entry must have
-been returned), with lines through the returned cells among the samples.
+per-thread counters).  The top-k of the 10^9-particle box is compared entry by
+entry with the oracle's exhaustive full search over all 1.25e11 cells, stored
+in tests/golden/ by tests/golden/make_fullsize_topk.py (an hour of host cores
+per sample rate, so not rerun here); the particles and counters are checked
+against that file's digests first.  A top-k over 8e12 cells is out of the
+oracle's reach, so that one is checked on samples the oracle computes one by
+one: every returned estimate, the ranking, and completeness on sampled mesh
+lines (every cell of a sampled line that ranks ahead of the k-th entry must
+have been returned), with lines through the returned cells among the samples.
 """
+import hashlib
+import os
+import sys
+
 import numpy as np
 import pytest
 
 import oracle
 import oracle.learned as OL
 import synth
+
+sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+import make_fullsize_topk as golden  # noqa: E402
 
 torch = pytest.importorskip("torch")
 
@@ -71,6 +82,8 @@ def sample_lines(keys, G, rng, n_random=300, n_from_keys=60):
 @pytest.mark.parametrize("rate", [1.0, 0.1])
 def test_halo_box_1e9_counters_and_topk(hs, big, rate):
     spec, host, dev = big
+    meta, gkeys, gest = golden.read_golden(golden.golden_path(rate))
+    assert meta["particles_sha256"] == golden.sha256_of(host), "the generator's output differs"
     stream = torch.cuda.current_stream()
     k = 10 ** 4
     sk = hs.Sketch(5, 24, 500.0, 0.1, 1, 2, stream=stream)     # the benchmark's handle
@@ -79,14 +92,16 @@ def test_halo_box_1e9_counters_and_topk(hs, big, rate):
     hs.sketch_update(sk.h, dev, spec.n, rate)
     hs.sketch_flush(sk.h)
     n = hs.topk_extract(sk.h, k, keys, est)
+    counters = sk.counters()
+    assert golden.sha256_of(counters) == meta["counters_sha256"]
     p = oracle.Params(5, 24, 500.0, 0.1, 1, 2)
     C = oracle.sketch_update(oracle.new_counters(p), p, host, rate=rate, nthreads=NT)
-    assert np.array_equal(sk.counters(), C)
-    assert n == k and ranked(keys, est)
+    assert np.array_equal(counters, C)
+    # the whole ranked list equals the oracle's exhaustive search
+    assert n == k and gkeys.size == k
+    assert np.array_equal(keys, gkeys) and np.array_equal(est, gest)
+    assert ranked(keys, est) and len(set(keys.tolist())) == k
     assert np.array_equal(oracle.estimate(C, p, keys), est)
-    rng = np.random.default_rng(int(rate * 10))
-    check_complete_on_lines(keys, est, lambda c: oracle.estimate(C, p, c), p.G,
-                            sample_lines(keys, p.G, rng))
     sk.close()
 
 
