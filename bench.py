@@ -270,7 +270,7 @@ def run_reference(args):
     value = n / step_s
     line = {"impl": "reference", "metric": "particles/s into sketch+top-k", "value": value,
             "unit": "particles/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": WORKLOAD["name"], "particles": n, "grid": G,
                        "rows": WORKLOAD["rows"], "width": 1 << WORKLOAD["log2_width"],
@@ -667,9 +667,14 @@ def run_ours(args):
     G = round(WORKLOAD["box"] / WORKLOAD["cell"])
     numa = bind_near_gpu(local)
     spec, box = make_box(n)
+    # one rank: the whole stream; several: this rank's contiguous shard by
+    # particle index, the counters summed over the ranks (Sec. 5) before rank
+    # 0's top-k
+    from paper_1711_00975_gb300.distributed import shard_range
+    lo, n_local = shard_range(n, rank, world)
     t0 = time.time()
-    host = torch.empty((n, 3), dtype=torch.float32).pin_memory()
-    box.generate_into_ptr(host.data_ptr(), 0, n)
+    host = torch.empty((n_local, 3), dtype=torch.float32).pin_memory()
+    box.generate_into_ptr(host.data_ptr(), lo, n_local)
     gen_s = time.time() - t0
     dev = host.to(f"cuda:{local}", non_blocking=False)
     stream = torch.cuda.current_stream()
@@ -677,12 +682,30 @@ def run_ours(args):
                    WORKLOAD["hash_seed"], WORKLOAD["sample_seed"], stream=stream)
     keys = np.empty(k, np.uint64)
     ests = np.empty(k, np.int32)
+    merge_buf = torch.empty((sk.rows, sk.width), dtype=torch.int32, device=f"cuda:{local}") \
+        if world > 1 else None
+
+    def begin():
+        hs.sketch_reset(sk.h)
+        if world > 1:
+            hs.sketch_seek(sk.h, lo)
+
+    def finish():
+        """counters of the whole stream (all-reduce over the ranks), then the
+        top-k on rank 0"""
+        if world > 1:
+            hs.sketch_counters(sk.h, merge_buf)
+            dist.all_reduce(merge_buf, op=dist.ReduceOp.SUM)
+            hs.sketch_load_counters(sk.h, merge_buf)
+        if rank == 0:
+            return hs.topk_extract(sk.h, k, keys, ests)
+        return 0
 
     def step(src, rate):
-        hs.sketch_reset(sk.h)
-        hs.sketch_update(sk.h, src, n, rate)
+        begin()
+        hs.sketch_update(sk.h, src, n_local, rate)
         hs.sketch_flush(sk.h)
-        return hs.topk_extract(sk.h, k, keys, ests)
+        return finish()
 
     def barrier():
         torch.cuda.synchronize()
@@ -699,12 +722,12 @@ def run_ours(args):
         ev0.record(stream)
         for _ in range(steps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            hs.sketch_reset(sk.h)
+            begin()
             a.record(stream)
-            hs.sketch_update(sk.h, src, n, rate)
+            hs.sketch_update(sk.h, src, n_local, rate)
             hs.sketch_flush(sk.h)
             b.record(stream)
-            hs.topk_extract(sk.h, k, keys, ests)
+            finish()
             upd.append((a, b))
         ev1.record(stream)
         barrier()
@@ -722,18 +745,18 @@ def run_ours(args):
         total_ms, upd_ms, st = timed(dev, args.rate, args.steps, args.warmup)
     clocks = clk.summary()
     ms_step = total_ms / args.steps
-    value = n * world / (ms_step * 1e-3)
+    value = n / (ms_step * 1e-3)              # every rank's particles (the whole stream)
     upd_avg = float(np.mean(upd_ms))
     search_avg = st["search_ms"] / max(1, st["search_launches"])
     search_per_step = st["search_ms"] / args.steps
     topk_per_step = st["topk_ms"] / args.steps
-    stream_gbs = 12.0 * n / (upd_avg * 1e-3) / 1e9
+    stream_gbs = 12.0 * n_local / (upd_avg * 1e-3) / 1e9
 
     # Dominant kernel by device time per step: the scatter of the binned update
     # (several launches per step) or the directory query of the full search.
     scatter_launches = max(1, st["update_launches"])
     scatter_ms = (st["update_ms"] - st["flush_ms"]) / scatter_launches
-    per_launch = n * args.steps / scatter_launches
+    per_launch = n_local * args.steps / scatter_launches
     scatter_per_step = st["update_ms"] - st["flush_ms"]
     scatter_gbs = 12.0 * per_launch / (scatter_ms * 1e-3) / 1e9
     cap = scatter_capture()
@@ -762,12 +785,12 @@ def run_ours(args):
                    if search_per_step > 0 else None, "ms_per_step": search_per_step}
 
     second = None
-    if args.second_rate and args.second_rate != args.rate:
+    if args.second_rate and args.second_rate != args.rate and world == 1:
         t2, u2, s2 = timed(dev, args.second_rate, max(2, args.steps // 2), 1)
         u2avg = float(np.mean(u2))
-        second = {"sample_rate": args.second_rate, "value": n * world / (t2 / max(2, args.steps // 2) * 1e-3),
-                  "update_ms": u2avg, "stream_gbs": 12.0 * n / (u2avg * 1e-3) / 1e9,
-                  "stream_frac": 12.0 * n / (u2avg * 1e-3) / 1e9 / hbm}
+        second = {"sample_rate": args.second_rate, "value": n / (t2 / max(2, args.steps // 2) * 1e-3),
+                  "update_ms": u2avg, "stream_gbs": 12.0 * n_local / (u2avg * 1e-3) / 1e9,
+                  "stream_frac": 12.0 * n_local / (u2avg * 1e-3) / 1e9 / hbm}
 
     red = None
     if not args.no_red:
@@ -803,12 +826,12 @@ def run_ours(args):
         dev.copy_(host, non_blocking=True)
         c1.record(stream)
         torch.cuda.synchronize()
-        link_gbs = 12.0 * n / (c0.elapsed_time(c1) * 1e-3) / 1e9
+        link_gbs = 12.0 * n_local / (c0.elapsed_time(c1) * 1e-3) / 1e9
         step_ms = max(ems, wall * 1e3)
-        e2e = {"value": n * world / (step_ms * 1e-3), "unit": "particles/s",
+        e2e = {"value": n / (step_ms * 1e-3), "unit": "particles/s",
                "h2d_bytes_per_step": 12 * n, "d2h_bytes_per_step": 12 * k,
                "ms_per_step": step_ms,
-               "h2d_gbs": 12.0 * n / (step_ms * 1e-3) / 1e9,
+               "h2d_gbs": 12.0 * n_local / (step_ms * 1e-3) / 1e9,
                "h2d_gbs_copies": est["h2d_bytes"] / (est["h2d_ms"] * 1e-3) / 1e9 if est["h2d_ms"] else None,
                "h2d_gbs_plain_copy": link_gbs,
                "note": "h2d_gbs: bytes over the link per step time; h2d_gbs_copies: the staged "
@@ -816,7 +839,7 @@ def run_ours(args):
 
     main_keys = keys.copy()            # the float path's top-k, for the recall comparison
     packed = None
-    if not args.no_packed:
+    if not args.no_packed and world == 1:
         # the same particles as 64-bit records (Sec. 4's data layout): 8 bytes
         # a particle in HBM and over the host link
         rec = torch.empty(n, dtype=torch.int64, device=dev.device)
@@ -865,24 +888,24 @@ def run_ours(args):
         torch.cuda.empty_cache()
 
     learned = None
-    if not args.no_learned and rank == 0:
+    if not args.no_learned and world == 1:
         learned = run_learned(dev, n, main_keys, args.train_boxes, stream)
 
     stream_leg = None
-    if not args.no_stream and rank == 0:
+    if not args.no_stream and world == 1:
         del dev
         torch.cuda.empty_cache()
         dev = None
         stream_leg = run_stream(int(args.stream_n), hbm, not args.no_learned, not args.no_packed)
 
     batched = None
-    if not args.no_batch:
+    if not args.no_batch and world == 1:
         del dev
         torch.cuda.empty_cache()
         batched = run_batched(max(3, args.steps // 2), args.warmup)
 
     cpu = None
-    if not args.no_cpu and rank == 0:
+    if not args.no_cpu and world == 1:
         n_upd = min(n, 1 << 27)
         n_cells = min(G ** 3, 2 * 10**9)
         ru, rq, cores, secs = cpu_sample_rates(host.numpy(), n_upd, n_cells, k, args.rate)
@@ -894,13 +917,15 @@ def run_ours(args):
 
     line = {"metric": "particles/s into sketch+top-k", "value": value, "unit": "particles/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
             "config": {"workload": WORKLOAD["name"], "particles": n, "box_mpc_h": WORKLOAD["box"],
                        "cell_mpc_h": WORKLOAD["cell"], "grid": G, "rows": WORKLOAD["rows"],
                        "width": 1 << WORKLOAD["log2_width"], "k": k, "sample_rate": args.rate,
                        "l2": "inputs (12 GB) larger than L2", "generation_s": gen_s,
-                       "host_numa_node": numa},
+                       "host_numa_node": numa,
+                       "parallelism": (f"{world} particle-index shards, int32 counters all-reduced, "
+                                       "top-k on rank 0") if world > 1 else "one GPU"},
             "breakdown": {"update_ms": upd_avg, "flush_ms": st["flush_ms"] / args.steps,
                           "topk_ms": topk_per_step,
                           "full_search_ms": search_per_step,

@@ -141,11 +141,14 @@ hs_status sketch_create(const hs_params *params, void *cuda_stream, hs_sketch **
  * (xyz, 3n floats) with global indices n_seen .. n_seen + n - 1, then
  * n_seen += n.  sample_rate in (0, 1]; rate 1 keeps every particle.
  * Device xyz: asynchronous on the handle's stream; the buffer must stay valid
- * until that work completes.  Host xyz: copied in chunks through the
- * library's staging buffers (three device buffers of 2^24 particles: copies on
- * the handle's own copy stream run ahead of the updates of earlier pieces); the
- * call returns after the last copy is issued (pageable memory may be reused on
- * return; pinned memory after sketch_wait_copies).  n == 0 is a no-op.
+ * until that work completes.  Page-locked host xyz (cudaHostAlloc,
+ * cudaHostRegister) of a sketch without a hierarchy: read by the update
+ * kernels over the host link directly, asynchronous like device memory.  Other
+ * host xyz: copied in chunks through the library's staging buffers (three
+ * device buffers of 2^24 particles: copies on the handle's own copy stream run
+ * ahead of the updates of earlier pieces); the call returns after the last
+ * copy is issued (pageable memory may be reused on return; page-locked memory
+ * after sketch_wait_copies).  n == 0 is a no-op.
  * HS_ERR_ARG for a null handle, a null xyz with n > 0, or a rate outside (0, 1].
  */
 hs_status sketch_update(hs_sketch *h, const float *xyz, uint64_t n, double sample_rate);

@@ -25,6 +25,16 @@ hs_status fail(hs_status st, const char *fmt, ...) {
 }
 
 
+// The device address of page-locked host memory (nullptr for anything else).
+const void *pinned_device_view(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 bool is_device_ptr(const void *p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -704,11 +714,18 @@ static hs_status update_common(hs_sketch *h, const void *src, uint64_t n, double
         return fail(HS_ERR_ARG, "packed records need a plain or hierarchical sketch");
     const size_t esz = packed ? 8 : 12;
     const float *xyz = static_cast<const float *>(src);
+    const void *view = nullptr;
     if (is_device_ptr(src)) {
         hs_status st = launch_update_timed(h, xyz, n, h->n_seen, sample_rate, packed);
         if (st == HS_OK && h->super)
             st = launch_update_timed(h->super, xyz, n, h->n_seen, sample_rate, packed);
         if (st != HS_OK) return st;
+    } else if (!h->super && (view = pinned_device_view(src)) != nullptr) {
+        // page-locked host memory: the kernels read it over the host link
+        // once (a hierarchy would read it twice, so it stages instead)
+        HS_TRY(launch_update_timed(h, static_cast<const float *>(view), n, h->n_seen, sample_rate,
+                                   packed));
+        h->stats.h2d_bytes += n * esz;
     } else {
         hs_status st = ensure_staging(h);
         if (st != HS_OK) return st;

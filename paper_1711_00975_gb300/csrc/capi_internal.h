@@ -160,6 +160,7 @@ namespace hs {
 namespace capi {
 
 bool is_device_ptr(const void *p);
+const void *pinned_device_view(const void *p);
 hs_status check_params(const hs_params *p);
 hs_status take_events(hs_sketch *h, EventPair *out);
 void drain_timings(hs_sketch *h);

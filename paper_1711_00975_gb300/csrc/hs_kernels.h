@@ -8,6 +8,15 @@
 
 namespace hs {
 
+// Raise a kernel's dynamic shared-memory limit on the current device to at
+// least `bytes`, calling the runtime only when the limit grows (launch paths
+// run this before every launch; cudaFuncSetAttribute itself is not free).
+cudaError_t ensure_smem_limit(const void *kernel, size_t bytes);
+template <typename K>
+inline cudaError_t ensure_smem_limit(K *kernel, size_t bytes) {
+    return ensure_smem_limit(reinterpret_cast<const void *>(kernel), bytes);
+}
+
 // ---- update mode (k_update.cu) ----
 cudaError_t launch_update(const float *xyz, uint64_t n, uint64_t g0, const SketchDesc &d,
                           int32_t *C, double rate, uint64_t sample_seed, uint64_t *probe,

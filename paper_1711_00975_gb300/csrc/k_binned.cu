@@ -2,6 +2,8 @@
 // variants of k_binned.cuh) and its second pass, the accumulation.
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 
 #include "k_binned.cuh"
 
@@ -91,6 +93,20 @@ uint32_t magic_of(uint32_t d) { return (uint32_t)((0x100000000ull + d - 1) / d);
 
 }  // namespace
 
+cudaError_t ensure_smem_limit(const void *kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, size_t> limits;   // (kernel, device) -> bytes
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &cur = limits[{kernel, dev}];
+    if (cur >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
+
 BinLayout bin_layout(const SketchDesc &d, size_t smem_budget) {
     BinLayout L{};
     L.S = d.log2w < 15 ? d.log2w : 15;
@@ -163,8 +179,7 @@ cudaError_t launch_bin_accumulate(const BinLayout &L, const BinStore &B, int32_t
                                   cudaStream_t s) {
     if (L.slot == 0 || B.nblocks == 0 || B.ngroups == 0) return cudaErrorInvalidValue;
     const size_t smem = ((size_t)4 << L.S) + 4 * ((size_t)B.nblocks + 1);
-    cudaError_t e = cudaFuncSetAttribute(k_bin_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = ensure_smem_limit(k_bin_accumulate, smem);
     if (e != cudaSuccess) return e;
     k_bin_accumulate<<<L.nbins, kAccThreads, smem, s>>>(B, L.S, magic_of(B.bpg),
                                                         reinterpret_cast<uint32_t *>(C));

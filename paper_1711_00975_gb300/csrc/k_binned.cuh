@@ -607,7 +607,7 @@ cudaError_t launch_mode(const float *xyz, const SketchDesc &d, const ScatterArgs
                         size_t smem, uint32_t *C, cudaStream_t s) {
     const bool vec = (reinterpret_cast<uintptr_t>(xyz) & 15u) == 0;
     auto launch = [&](auto kern) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = ensure_smem_limit(kern, smem);
         if (e != cudaSuccess) return e;
         kern<<<a.B.nblocks, kScatterThreads, smem, s>>>(xyz, d, a, C);
         return cudaGetLastError();

@@ -395,8 +395,7 @@ cudaError_t launch_mlp_grad(const float *P, const uint16_t *feats, const float *
     if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, 8, s);
     if (e != cudaSuccess || m == 0) return e;
     uint64_t blocks = (m + kTrainBlock - 1) / kTrainBlock;
-    cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(TrainSmem));
+    ensure_smem_limit(k_mlp_grad, sizeof(TrainSmem));
     k_mlp_grad<<<(unsigned)blocks, kTrainBlock, sizeof(TrainSmem), s>>>(P, feats, y, w, m, grad,
                                                                        loss);
     return cudaGetLastError();

@@ -306,12 +306,12 @@ cudaError_t launch_full_search(const int32_t *C, const SketchDesc &d, int32_t th
     if (b < 1) b = 1;
     if (d.rows == 5) {
         auto k = k_full_search<5>;
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        ensure_smem_limit(k, smem);
         k<<<(unsigned)b, 1024, smem, s>>>(C, d, theta, mode, bitmap, nb, prune, line_lo, line_hi,
                                          out, skip);
     } else {
         auto k = k_full_search<0>;
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        ensure_smem_limit(k, smem);
         k<<<(unsigned)b, 1024, smem, s>>>(C, d, theta, mode, bitmap, nb, prune, line_lo, line_hi,
                                          out, skip);
     }

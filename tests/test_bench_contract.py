@@ -37,7 +37,7 @@ def test_reference_line_has_the_contract_keys(reference_line):
         assert key in d, key
     assert d["metric"] == "particles/s into sketch+top-k" and d["unit"] == "particles/s"
     assert d["value"] > 0 and d["ms_per_step"] > 0
-    assert d["higher_is_better"] is True and d["scaling"] == "weak"
+    assert d["higher_is_better"] is True and d["scaling"] == "strong"
     assert d["steps"] == 1 and d["warmup"] == 0 and d["n_gpus"] == 1
     assert d["config"]["workload"] == "halo-box-1e9" and d["config"]["particles"] == 200000
     cb = d["cpu_baseline"]
