@@ -346,11 +346,13 @@ def train_router(spec_of, n_boxes: int, k_label: int, stream):
     return mlp, info
 
 
-def run_learned(dev, n: int, main_keys: np.ndarray, train_boxes: int, stream):
+def run_learned(dev, n: int, train_boxes: int, stream):
     """The learned router on the 10^9-particle box: train on 100 Mpc/h boxes,
-    then top-k recall against exact counts for the plain sketch at 5 x 2^24
-    (320 MiB, the main leg's last top-k) and 5 x 2^23 (160 MiB), and for the
-    learned sketch (5 x 2^23 + exact blocks of a 2^20-slot table's bytes)."""
+    then top-k recall against exact counts for plain sketches of 5 x 2^23
+    (160 MiB), 6 x 2^23 (192 MiB), 7 x 2^23 (224 MiB, more than the learned
+    sketch's whole footprint) and 5 x 2^24 (320 MiB), and for the learned sketch (5 x 2^23 +
+    exact blocks of a 2^20-slot table's bytes + its routing bitmap and prefix),
+    with the memory of each beside its recall."""
     import torch
 
     import synth
@@ -362,6 +364,7 @@ def run_learned(dev, n: int, main_keys: np.ndarray, train_boxes: int, stream):
     out = {"workload": W["name"], "k": k, "train_boxes": train_boxes}
     mlp, out["training"] = train_router(lambda i: synth.training_box(1000 + i), train_boxes,
                                         C["k_label"], stream)
+    out["training"]["params_sha256_16"] = hashlib.sha256(mlp.get_params().tobytes()).hexdigest()[:16]
     # ---- evaluation on the main box
     E = hs.Exact(W["box"], W["cell"], C["exact_log2_slots"], stream)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -380,13 +383,17 @@ def run_learned(dev, n: int, main_keys: np.ndarray, train_boxes: int, stream):
         torch.cuda.synchronize()
         return r, a.elapsed_time(b)
 
-    plain_320 = E.recall(main_keys, k)
-    sk = hs.Sketch(W["rows"], C["sketch_log2_width"], W["box"], W["cell"], W["hash_seed"],
-                   W["sample_seed"], stream=stream)
-    _, up_ms = timed_call(lambda: (sk.update(dev, n), sk.flush()))
-    (pk, _), tk_ms = timed_call(lambda: sk.topk(k))
-    plain_160 = E.recall(pk, k)
-    sk.close()
+    plain = {}
+    for rows, log2w in ((5, C["sketch_log2_width"]), (6, C["sketch_log2_width"]),
+                        (7, C["sketch_log2_width"]), (W["rows"], W["log2_width"])):
+        sk = hs.Sketch(rows, log2w, W["box"], W["cell"], W["hash_seed"], W["sample_seed"],
+                       stream=stream)
+        _, up_ms = timed_call(lambda: (sk.update(dev, n), sk.flush()))
+        (pk, _), tk_ms = timed_call(lambda: sk.topk(k))
+        nbytes = rows * 4 << log2w
+        plain[f"{rows}x2^{log2w}"] = {"recall": E.recall(pk, k), "memory_bytes": nbytes,
+                                      "update_ms": up_ms, "topk_ms": tk_ms}
+        sk.close()
     L = hs.Learned(W["rows"], C["sketch_log2_width"], W["box"], W["cell"], W["hash_seed"],
                    W["sample_seed"], coarse_factor=C["coarse_factor"], table_log2=C["table_log2"],
                    feature_seed=C["feature_seed"], feature_rate=C["feature_rate"], stream=stream)
@@ -395,16 +402,13 @@ def run_learned(dev, n: int, main_keys: np.ndarray, train_boxes: int, stream):
     (lk, _), ltk_ms = timed_call(lambda: L.topk(k))
     learned = E.recall(lk, k)
     sketch_bytes = W["rows"] * 4 << C["sketch_log2_width"]
+    aux = (L.Gc ** 3 + 31) // 32 * 8          # routing bitmap + one prefix count a word
     out.update({
-        "recall_plain_320MiB": plain_320, "recall_plain_160MiB": plain_160,
-        "recall_learned": learned,
-        "memory_bytes": {"plain_320MiB": W["rows"] * 4 << W["log2_width"],
-                         "plain_160MiB": sketch_bytes,
-                         "learned": sketch_bytes + L.table_bytes,
-                         "learned_table": L.table_bytes,
-                         "learned_routing_aux": (L.Gc ** 3 + 31) // 32 * 8},
+        "recall_plain": plain,
+        "recall_learned": {"recall": learned, "memory_bytes": sketch_bytes + L.table_bytes + aux,
+                           "sketch_bytes": sketch_bytes, "exact_block_bytes": L.table_bytes,
+                           "routing_aux_bytes": aux},
         "routed_coarse_cells": int(nr), "max_routed": int(L.max_routed),
-        "plain_160MiB_ms": {"update": up_ms, "topk": tk_ms},
         "learned_ms": {"prepare": prep_ms, "update": lup_ms, "topk": ltk_ms},
         "learned_particles_per_s": n / ((prep_ms + lup_ms + ltk_ms) * 1e-3),
         "roofline": {"kernel": "k_bin_scatter<routed> + k_bin_accumulate", "bound": "hbm",
@@ -837,7 +841,6 @@ def run_ours(args):
                "note": "h2d_gbs: bytes over the link per step time; h2d_gbs_copies: the staged "
                        "copies' own rate; h2d_gbs_plain_copy: one copy of the same pinned buffer"}
 
-    main_keys = keys.copy()            # the float path's top-k, for the recall comparison
     packed = None
     if not args.no_packed and world == 1:
         # the same particles as 64-bit records (Sec. 4's data layout): 8 bytes
@@ -889,7 +892,7 @@ def run_ours(args):
 
     learned = None
     if not args.no_learned and world == 1:
-        learned = run_learned(dev, n, main_keys, args.train_boxes, stream)
+        learned = run_learned(dev, n, args.train_boxes, stream)
 
     stream_leg = None
     if not args.no_stream and world == 1:

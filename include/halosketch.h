@@ -354,7 +354,10 @@ hs_status mlp_get_params(hs_mlp *m, float *params);
 /* logits[i] of features[i*27 .. i*27+26]; arrays host or device; synchronous */
 hs_status mlp_forward(hs_mlp *m, const uint16_t *features, uint64_t n, float *logits);
 /* summed (not averaged) gradient of sum(w (softplus(z) - y z)) and that loss;
- * grad: HS_MLP_PARAMS floats.  The bf16 roundings pass gradients unchanged. */
+ * grad: HS_MLP_PARAMS floats.  The bf16 roundings pass gradients unchanged.
+ * Every sum runs in a fixed order (per block of 128 samples, then over the
+ * blocks in order), so equal inputs give equal gradients bit for bit and a
+ * training run repeats exactly. */
 hs_status mlp_gradient(hs_mlp *m, const uint16_t *features, const float *y, const float *w,
                        uint64_t n, float *grad, float *loss);
 /* one Adam step (beta 0.9 / 0.999, eps 1e-8) on the weight-averaged loss;

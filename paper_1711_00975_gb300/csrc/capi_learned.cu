@@ -8,6 +8,8 @@
 
 struct hs_mlp {
     float *P = nullptr, *M = nullptr, *V = nullptr, *grad = nullptr, *loss = nullptr;
+    float *part = nullptr;      // per-block gradient sums of one mini-batch
+    size_t part_cap = 0;        // floats
     int step = 0;
     cudaStream_t stream = nullptr;
     int device = 0;
@@ -96,7 +98,7 @@ extern "C" {
 
 hs_status mlp_destroy(hs_mlp *m) {
     if (!m) return HS_OK;
-    void *ps[] = {m->P, m->M, m->V, m->grad, m->loss};
+    void *ps[] = {m->P, m->M, m->V, m->grad, m->loss, m->part};
     for (void *q : ps)
         if (q) cudaFree(q);
     delete m;
@@ -189,7 +191,17 @@ static hs_status mlp_grad_common(hs_mlp *m, const uint16_t *feats, const float *
     hs_status st = device_input(feats, n * kMlpIn, m->stream, &df, &tf);
     if (st == HS_OK) st = device_input(y, n, m->stream, &dy, &ty);
     if (st == HS_OK) st = device_input(w, n, m->stream, &dw, &tw);
-    cudaError_t e = st == HS_OK ? launch_mlp_grad(m->P, df, dy, dw, n, m->grad, m->loss, m->stream)
+    const size_t need = mlp_grad_scratch_floats(n);
+    if (st == HS_OK && need > m->part_cap) {
+        if (m->part) cudaFree(m->part);
+        m->part = nullptr;
+        m->part_cap = 0;
+        cudaError_t ea = cudaMalloc(&m->part, need * 4);
+        if (ea != cudaSuccess) st = fail(HS_ERR_OOM, "gradient scratch: %s", cudaGetErrorString(ea));
+        else m->part_cap = need;
+    }
+    cudaError_t e = st == HS_OK ? launch_mlp_grad(m->P, df, dy, dw, n, m->grad, m->loss, m->part,
+                                                  m->stream)
                                 : cudaSuccess;
     if (tf || ty || tw) cudaStreamSynchronize(m->stream);
     if (tf) cudaFree(tf);

@@ -98,9 +98,11 @@ cudaError_t launch_features(const int32_t *counts, uint32_t Gc, const uint64_t *
                             cudaStream_t s);
 cudaError_t launch_mlp_forward(const float *P, const uint16_t *feats, uint64_t m, float *logits,
                                cudaStream_t s);
+// grad = summed gradient, loss[0] = sum w * bce, loss[1] = sum w, each summed in a
+// fixed order (reproducible); part: mlp_grad_scratch_floats(m) floats of scratch
+size_t mlp_grad_scratch_floats(uint64_t m);
 cudaError_t launch_mlp_grad(const float *P, const uint16_t *feats, const float *y, const float *w,
-                            uint64_t m, float *grad, float *loss, cudaStream_t s);
-// loss[0] += sum w * bce, loss[1] += sum w (both zeroed first)
+                            uint64_t m, float *grad, float *loss, float *part, cudaStream_t s);
 cudaError_t launch_adam(float *P, float *M, float *V, const float *grad, const float *gscale,
                         float lr, int step, cudaStream_t s);
 cudaError_t launch_logit_rank(const float *logits, uint64_t m, int32_t *rank,

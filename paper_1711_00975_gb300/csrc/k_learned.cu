@@ -148,7 +148,11 @@ __global__ void __launch_bounds__(128)
 // ---- training: forward + backward of a mini-batch, gradients summed ----
 // Loss per sample: w * (softplus(z) - y z); the caller divides by sum(w).
 // The gradient treats the bf16 roundings as identities (straight-through).
+// Each block leaves its sums (every parameter's gradient, then the loss and
+// the weight sum) in its own row of `part`; k_grad_sum adds the rows in block
+// order, so a training run is reproducible bit for bit.
 constexpr int kTrainBlock = 128;
+constexpr int kPartWidth = kMlpParams + 2;
 
 struct TrainSmem {
     MlpSmem s;
@@ -163,7 +167,7 @@ struct TrainSmem {
 __global__ void __launch_bounds__(kTrainBlock)
     k_mlp_grad(const float *__restrict__ P, const uint16_t *__restrict__ feats,
                const float *__restrict__ y, const float *__restrict__ w, uint64_t m,
-               float *__restrict__ grad, float *__restrict__ loss) {
+               float *__restrict__ part) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TrainSmem &S = *reinterpret_cast<TrainSmem *>(smem_raw);
     MlpSmem &s = S.s;
@@ -229,18 +233,33 @@ __global__ void __launch_bounds__(kTrainBlock)
         } else {                                           // b3
             for (int q = 0; q < nb; ++q) acc += sdz[q];
         }
-        if (nb) atomicAdd(&grad[p], acc);
+        part[(uint64_t)blockIdx.x * kPartWidth + p] = acc;
     }
-    // loss and weight sums: warp sums then one atomic per warp
-    float wsum = smp < m ? w[smp] : 0.0f;
-    for (int o = 16; o > 0; o >>= 1) {
-        lsum += __shfl_down_sync(0xFFFFFFFFu, lsum, o);
-        wsum += __shfl_down_sync(0xFFFFFFFFu, wsum, o);
+    // loss and weight sums of the block, added in sample order
+    __syncthreads();
+    sdz[t] = lsum;
+    sx[t][0] = smp < m ? w[smp] : 0.0f;
+    __syncthreads();
+    if (t == 0) {
+        float ls = 0.0f, ws = 0.0f;
+        for (int q = 0; q < kTrainBlock; ++q) {
+            ls += sdz[q];
+            ws += sx[q][0];
+        }
+        part[(uint64_t)blockIdx.x * kPartWidth + kMlpParams] = ls;
+        part[(uint64_t)blockIdx.x * kPartWidth + kMlpParams + 1] = ws;
     }
-    if ((t & 31) == 0) {
-        if (lsum != 0.0f) atomicAdd(&loss[0], lsum);
-        if (wsum != 0.0f) atomicAdd(&loss[1], wsum);
-    }
+}
+
+// grad[p] = sum over blocks b (in order) of part[b][p]; loss[0..1] likewise
+__global__ void k_grad_sum(const float *__restrict__ part, uint32_t nblocks,
+                           float *__restrict__ grad, float *__restrict__ loss) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= kPartWidth) return;
+    float acc = 0.0f;
+    for (uint32_t b = 0; b < nblocks; ++b) acc += part[(uint64_t)b * kPartWidth + p];
+    if (p < kMlpParams) grad[p] = acc;
+    else loss[p - kMlpParams] = acc;
 }
 
 // Adam on the float32 master parameters; gradients are divided by *gscale
@@ -389,15 +408,21 @@ cudaError_t launch_mlp_forward(const float *P, const uint16_t *feats, uint64_t m
     return cudaGetLastError();
 }
 
+size_t mlp_grad_scratch_floats(uint64_t m) {
+    return (size_t)((m + kTrainBlock - 1) / kTrainBlock) * kPartWidth;
+}
+
 cudaError_t launch_mlp_grad(const float *P, const uint16_t *feats, const float *y, const float *w,
-                            uint64_t m, float *grad, float *loss, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(grad, 0, kMlpParams * 4, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, 8, s);
-    if (e != cudaSuccess || m == 0) return e;
-    uint64_t blocks = (m + kTrainBlock - 1) / kTrainBlock;
-    ensure_smem_limit(k_mlp_grad, sizeof(TrainSmem));
-    k_mlp_grad<<<(unsigned)blocks, kTrainBlock, sizeof(TrainSmem), s>>>(P, feats, y, w, m, grad,
-                                                                       loss);
+                            uint64_t m, float *grad, float *loss, float *part, cudaStream_t s) {
+    if (m == 0) {
+        cudaError_t e = cudaMemsetAsync(grad, 0, kMlpParams * 4, s);
+        return e == cudaSuccess ? cudaMemsetAsync(loss, 0, 8, s) : e;
+    }
+    const uint64_t blocks = (m + kTrainBlock - 1) / kTrainBlock;
+    cudaError_t e = ensure_smem_limit(k_mlp_grad, sizeof(TrainSmem));
+    if (e != cudaSuccess) return e;
+    k_mlp_grad<<<(unsigned)blocks, kTrainBlock, sizeof(TrainSmem), s>>>(P, feats, y, w, m, part);
+    k_grad_sum<<<(kPartWidth + 255) / 256, 256, 0, s>>>(part, (uint32_t)blocks, grad, loss);
     return cudaGetLastError();
 }
 

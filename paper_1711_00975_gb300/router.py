@@ -50,6 +50,10 @@ def box_examples(xyz, n: int, box: float, cell: float, mlp: hs.MLP, coarse_facto
             L.close()
         if own_e:
             E.close()
+    # examples in coarse-key order: the library lists coarse cells in the
+    # order its threads reach them, and training must not depend on that
+    order = np.argsort(ckeys, kind="stable")
+    ckeys, feats = ckeys[order], feats[order]
     if counts.size == 0:
         return feats, np.zeros(len(ckeys), np.float32), ckeys
     fk = counts[min(k_label, counts.size) - 1]

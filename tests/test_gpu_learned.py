@@ -92,6 +92,44 @@ def test_mlp_gradient_vs_float64(hs, m):
     assert np.mean(np.abs(g - g64)[big] <= 1e-3 * np.abs(g64[big]) + 1e-5) > 0.99
 
 
+def test_box_examples_do_not_depend_on_thread_order(hs):
+    """Examples of one box come out in coarse-key order, identical on repeats."""
+    from paper_1711_00975_gb300 import router
+    spec = synth.BoxSpec(n=1 << 20, box=50.0, n_halo=500, seed=17)
+    xyz = synth.HaloBox(spec).generate()
+    mlp = hs.MLP(seed=2)
+    d = _dev(xyz)
+    runs = [router.box_examples(d, spec.n, spec.box, 0.1, mlp, k_label=20,
+                                feature_rate=1.0 / 8) for _ in range(2)]
+    (f0, y0, k0), (f1, y1, k1) = runs
+    assert np.all(k0[:-1] < k0[1:])
+    assert np.array_equal(k0, k1) and np.array_equal(f0, f1) and np.array_equal(y0, y1)
+    assert y0.sum() > 0
+    mlp.close()
+
+
+def test_training_repeats_bit_for_bit(hs):
+    """The gradient sums run in a fixed order, so two training runs from the
+    same seed on the same examples end with identical parameters."""
+    from paper_1711_00975_gb300 import router
+    rng = np.random.default_rng(11)
+    counts = rng.integers(0, 300, size=(150_000, 27))
+    y = ((counts[:, 13] > 250) | (rng.random(counts.shape[0]) < 0.02)).astype(np.float32)
+    F = OL.feature_of(counts)
+    runs = []
+    for _ in range(2):
+        mlp = hs.MLP(seed=3)
+        losses = router.train(mlp, F, y, epochs=2, batch=65536, lr=1e-3, seed=5)
+        runs.append((mlp.get_params(), np.array(losses)))
+        g, l = mlp.gradient(_dev(F[:70_001]), _dev(y[:70_001]), _dev(np.ones(70_001, np.float32)))
+        runs[-1] += (g, l)
+        mlp.close()
+    (p0, l0, g0, s0), (p1, l1, g1, s1) = runs
+    assert np.array_equal(p0.view(np.uint32), p1.view(np.uint32))
+    assert np.array_equal(l0, l1) and s0 == s1
+    assert np.array_equal(g0.view(np.uint32), g1.view(np.uint32))
+
+
 def test_mlp_training_reduces_loss(hs):
     rng = np.random.default_rng(7)
     counts = rng.integers(0, 200, size=(20000, 27))
