@@ -444,7 +444,7 @@ hs_status launch_update_timed(hs_sketch *h, const float *xyz, uint64_t n, uint64
             h->pending_update.push_back(ev);
             h->pending += add;
             h->stats.update_launches += 1;
-            h->stats.kernel_launches += 1;
+            h->stats.kernel_launches += (h->d.rows + h->bl.rows_per_pass - 1) / h->bl.rows_per_pass;
         }
         return HS_OK;
     }

@@ -167,7 +167,7 @@ hs_status batch_create(const hs_params *params, uint32_t n_volumes, const double
     b->d.inv_cell = b->inv[0];
     b->d.Gq = b->d.G;
     b->d.F = 1;
-    b->bl = bin_layout(batch_flat_desc(b), kBinSmemBudget);
+    b->bl = bin_layout(batch_flat_desc(b), kBinSmemBudget, true);
     if (b->bl.slot == 0 || b->bl.nbins >= 65536 || n_volumes > kMaxBinGroups) {
         delete b;
         return fail(HS_ERR_ARG, "%u volumes x %u rows x 2^%u counters need too many bins; "

@@ -43,9 +43,12 @@ struct BinLayout {
     uint32_t nbins;    // rows * W / 2^S
     uint32_t slot;     // ring entries per bin (0: binning unavailable)
     uint32_t half;     // flush granule in entries (slot / 2, a multiple of 8)
+    uint32_t rows_per_pass;   // rows one scatter launch stages (all: one pass)
     size_t smem;       // dynamic shared memory of the scatter kernel (no queues)
 };
-BinLayout bin_layout(const SketchDesc &d, size_t smem_budget);
+// single_pass: every row in one launch or not at all (batches: a volume's bins
+// are offset within one launch)
+BinLayout bin_layout(const SketchDesc &d, size_t smem_budget, bool single_pass = false);
 constexpr uint32_t kMaxBinGroups = 128;
 constexpr uint32_t kScatterTile = 3072;   // particles of one scatter tile (768 threads x 4)
 // Global side of the binned update.  Each scatter block owns one region per

@@ -107,18 +107,27 @@ cudaError_t ensure_smem_limit(const void *kernel, size_t bytes) {
     return e;
 }
 
-BinLayout bin_layout(const SketchDesc &d, size_t smem_budget) {
+BinLayout bin_layout(const SketchDesc &d, size_t smem_budget, bool single_pass) {
     BinLayout L{};
     L.S = d.log2w < 15 ? d.log2w : 15;
     const uint64_t nb = (uint64_t)d.rows << (d.log2w - L.S);
     if (nb >= 65536) return L;                // bins are 16-bit numbers (group division)
     L.nbins = (uint32_t)nb;
+    const uint32_t bpr = 1u << (d.log2w - L.S);
     const size_t budget = std::min<size_t>(smem_budget, kSmemLimit);
-    // binning is available when even a sampled call's layout (with queues) fits
-    if (ring_slot(L.nbins, kMaxBinGroups, 1, budget) == 0) return L;
-    L.slot = ring_slot(L.nbins, kMaxBinGroups, 0, budget);
+    // as many rows a launch as fit even a sampled call's layout (with queues);
+    // a sketch whose rings do not fit at once stages its rows in passes
+    for (uint32_t rpp = d.rows; rpp >= 1; --rpp) {
+        if (ring_slot(rpp * bpr, kMaxBinGroups, 1, budget) != 0) {
+            L.rows_per_pass = rpp;
+            break;
+        }
+        if (single_pass) return L;
+    }
+    if (L.rows_per_pass == 0) return L;
+    L.slot = ring_slot(L.rows_per_pass * bpr, kMaxBinGroups, 0, budget);
     L.half = L.slot / 2;
-    L.smem = smem_layout(L.nbins, L.slot, kMaxBinGroups, 0).total;
+    L.smem = smem_layout(L.rows_per_pass * bpr, L.slot, kMaxBinGroups, 0).total;
     return L;
 }
 
@@ -141,20 +150,10 @@ cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const 
     a.thr = sampled ? (uint64_t)ldexp(rate, 64) : 0;
     a.sample_seed = sample_seed;
     a.probe = probe;
-    a.probe_base = probe_base;
-    a.probe_end = probe ? probe_base + probe_cap : probe_base;
     a.S = L.S;
-    a.nbins = L.nbins;
-    a.slot = ring_slot(L.nbins, B.ngroups, sampled ? 1 : 0, kSmemLimit);
-    if (slot && slot < a.slot) a.slot = slot;     // a shallower ring (power of two)
-    if (a.slot < 16 || (a.slot & (a.slot - 1))) return cudaErrorInvalidValue;
-    a.half = a.slot / 2;
-    a.team = a.half <= 64 ? 1u : 32u;
     a.hshift = 31 - d.log2w;
     a.code_mask = (2u << L.S) - 1u;
     a.gmagic = magic_of(B.bpg);
-    const uint32_t lbpr = d.log2w - L.S;
-    for (uint32_t r = 0; r < kMaxRows; ++r) a.rbase[r] = r << lbpr;
     // two tiles between flush phases (about 12 codes a bin at 2560 bins); at
     // sample rate r a tile stages about r times the codes of a full tile
     a.rounds = rounds ? rounds
@@ -166,13 +165,40 @@ cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const 
     a.vols = vols;
     a.nvol = vols ? nvol : 0;
     a.probe_per_vol = probe_per_vol;
-    const size_t smem = smem_layout(a.nbins, a.slot, B.ngroups, sampled ? 1 : 0).total;
+    const uint32_t lbpr = d.log2w - L.S;
+    const uint32_t rpp = L.rows_per_pass ? L.rows_per_pass : d.rows;
+    if (vols && rpp < d.rows) return cudaErrorInvalidValue;   // a batch stages in one pass
     uint32_t *Cu = reinterpret_cast<uint32_t *>(C);
-    if (vols) return launch_modes_batch_route(kModeBatch, xyz, d, a, sampled, smem, Cu, s);
-    if (route) return launch_modes_batch_route(kModeRoute, xyz, d, a, sampled, smem, Cu, s);
-    const int mode = packed ? (d.F > 1 ? kModeSuperPacked : kModePlainPacked)
-                            : (d.F > 1 ? kModeSuper : kModePlain);
-    return launch_modes_sketch(mode, xyz, d, a, sampled, smem, Cu, s);
+    // one launch per pass over the rows [row0, row0 + nrows); only the first
+    // pass records the probe and counts routed particles
+    for (uint32_t row0 = 0; row0 < d.rows; row0 += rpp) {
+        a.row0 = row0;
+        a.nrows = std::min(rpp, d.rows - row0);
+        a.bin_base = vols ? 0u : row0 << lbpr;
+        a.nbins = vols ? L.nbins : a.nrows << lbpr;
+        for (uint32_t i = 0; i < kMaxRows; ++i) a.rbase[i] = i << lbpr;
+        a.route_adds = row0 == 0 ? 1u : 0u;
+        a.probe_base = probe_base;
+        a.probe_end = probe && row0 == 0 ? probe_base + probe_cap : probe_base;
+        a.slot = ring_slot(a.nbins, B.ngroups, sampled ? 1 : 0, kSmemLimit);
+        if (slot && slot < a.slot) a.slot = slot;     // a shallower ring (power of two)
+        if (a.slot < 16 || (a.slot & (a.slot - 1))) return cudaErrorInvalidValue;
+        a.half = a.slot / 2;
+        a.team = a.half <= 64 ? 1u : 32u;
+        const size_t smem = smem_layout(a.nbins, a.slot, B.ngroups, sampled ? 1 : 0).total;
+        cudaError_t e;
+        if (vols) {
+            e = launch_modes_batch_route(kModeBatch, xyz, d, a, sampled, smem, Cu, s);
+        } else if (route) {
+            e = launch_modes_batch_route(kModeRoute, xyz, d, a, sampled, smem, Cu, s);
+        } else {
+            const int mode = packed ? (d.F > 1 ? kModeSuperPacked : kModePlainPacked)
+                                    : (d.F > 1 ? kModeSuper : kModePlain);
+            e = launch_modes_sketch(mode, xyz, d, a, sampled, smem, Cu, s);
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_bin_accumulate(const BinLayout &L, const BinStore &B, int32_t *C,

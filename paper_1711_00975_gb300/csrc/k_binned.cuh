@@ -57,7 +57,10 @@ struct ScatterArgs {
     uint64_t probe_base;  // probe[g - probe_base] = key for probe_base <= g < probe_end
     uint64_t probe_end;
     uint32_t S;           // log2 of counters per bin
-    uint32_t nbins;
+    uint32_t nbins;       // bins staged by this launch (rows row0 .. row0 + nrows - 1)
+    uint32_t bin_base;    // global number of this launch's bin 0
+    uint32_t row0, nrows; // the rows this launch stages
+    uint32_t route_adds;  // routed particles are counted by this launch (the first pass)
     uint32_t slot;        // ring entries per bin (two halves)
     uint32_t half;        // flush granule
     uint32_t hshift;      // 31 - log2W: top log2W+1 bits of v = bucket and sign bit
@@ -65,7 +68,7 @@ struct ScatterArgs {
     uint32_t rounds;      // tiles between flush phases
     uint32_t team;        // lanes that flush one bin (1 or 32)
     uint32_t gmagic;      // ceil(2^32 / bpg): bin / bpg = umulhi(bin, gmagic)
-    uint32_t rbase[kMaxRows];   // first bin of row r
+    uint32_t rbase[kMaxRows];   // first (local) bin of row row0 + i
     BinStore B;
     RouteFilter route;        // routed cells go to exact dense blocks instead
     const uint32_t *rprefix;
@@ -197,7 +200,7 @@ __device__ __forceinline__ bool prep_particle(float x, float y, float z, uint64_
     if (PROBE && g - a.probe_base < a.probe_end - a.probe_base)   // the sketch's cells only
         write_probe(a.probe, g - a.probe_base, valid && !routed, c.cx, c.cy, c.cz, d.G);
     if (MODE == kModeRoute && routed && keep) {
-        route_add(a, c.cx, c.cy, c.cz);
+        if (a.route_adds) route_add(a, c.cx, c.cy, c.cz);
         return false;
     }
     return keep && valid;
@@ -257,7 +260,7 @@ __device__ __forceinline__ bool prep_particle_batch(float x, float y, float z, u
 __device__ __forceinline__ void stage_full(uint32_t bin, uint32_t code, const ScatterArgs &a,
                                            const Smem &s, uint32_t *C) {
     atomicAdd(&s.fill[bin], 0xFFFEFFFEu);   // minus (1 << 16 | 2)
-    direct_add(C, a.S, bin, code);
+    direct_add(C, a.S, bin + a.bin_base, code);
 }
 
 // The top 32 bits of v = a0*cx + a1*cy + a2*cz + b (mod 2^64), written as
@@ -298,9 +301,9 @@ __device__ __forceinline__ void stage_cell(const Cell &c, const SketchDesc &d, c
                 stage_full(bin[r], code[r], a, s, C);
         }
     } else {
-        for (uint32_t r = 0; r < d.rows; ++r) {
-            const uint32_t h = row_hi(d.seed[r], c.cx, c.cy, c.cz) >> a.hshift;
-            const uint32_t bin = (h >> (a.S + 1)) + a.rbase[r] + c.bin0;
+        for (uint32_t i = 0; i < a.nrows; ++i) {
+            const uint32_t h = row_hi(d.seed[a.row0 + i], c.cx, c.cy, c.cz) >> a.hshift;
+            const uint32_t bin = (h >> (a.S + 1)) + a.rbase[i] + c.bin0;
             const uint32_t code = h & a.code_mask;
             const uint32_t w = atomicAdd(&s.fill[bin], 0x10002u);
             if ((w >> 16) < a.slot)
@@ -343,10 +346,11 @@ __device__ __forceinline__ uint4 ring_chunk(const uint16_t *ring, uint32_t p0, u
 __device__ __forceinline__ void write_out(uint32_t bin, uint32_t p0, uint32_t cnt, uint32_t rp,
                                           uint32_t pad_from, uint32_t tl, uint32_t TS,
                                           const ScatterArgs &a, const Smem &s, uint32_t *C) {
-    const uint32_t g = a.B.ngroups > 1 ? __umulhi(bin, a.gmagic) : 0u;
+    const uint32_t gbin = bin + a.bin_base;
+    const uint32_t g = a.B.ngroups > 1 ? __umulhi(gbin, a.gmagic) : 0u;
     const uint32_t cap = s.gcap[g];
     uint16_t *dst = a.B.codes + s.gbase[g] +
-                    ((uint64_t)blockIdx.x * a.B.bpg + (bin - g * a.B.bpg)) * cap;
+                    ((uint64_t)blockIdx.x * a.B.bpg + (gbin - g * a.B.bpg)) * cap;
     const uint32_t fit = rp >= cap ? 0u : min(cnt, cap - rp);
     const uint16_t *ring = s.ring + bin * a.slot;
     if (a.half >= 16) {
@@ -358,7 +362,7 @@ __device__ __forceinline__ void write_out(uint32_t bin, uint32_t p0, uint32_t cn
         for (uint32_t j = tl; j < fit / 8; j += TS) d4[j] = ring_chunk(ring, p0, 8 * j, pad_from, a);
     }
     for (uint32_t e = fit + tl; e < cnt && e < pad_from; e += TS)   // region full: add directly
-        direct_add(C, a.S, bin, ring[(p0 + e) & (a.slot - 1)]);
+        direct_add(C, a.S, gbin, ring[(p0 + e) & (a.slot - 1)]);
 }
 
 // How many entries of a bin to write: every complete half (oldest first);
@@ -381,7 +385,8 @@ __device__ __forceinline__ uint32_t flush_bin(uint32_t b, uint32_t w, uint32_t r
     uint32_t pad_from = 0xFFFFFFFFu;
     if (final) {
         pad_from = pend & ~1u;
-        if ((pend & 1u) && tl == 0) direct_add(C, a.S, b, s.ring[b * a.slot + ((p0 + pend - 1) & (a.slot - 1))]);
+        if ((pend & 1u) && tl == 0)
+            direct_add(C, a.S, b + a.bin_base, s.ring[b * a.slot + ((p0 + pend - 1) & (a.slot - 1))]);
     }
     write_out(b, p0, cnt, rp, pad_from, tl, TS, a, s, C);
     return cnt;
@@ -407,7 +412,7 @@ __device__ __forceinline__ void flush_phase(bool final, const ScatterArgs &a, co
             const uint32_t cnt = flush_bin(b, w, rp, final, tl, TS, a, s, C);
             if (tl == 0) {
                 if (final) {
-                    a.B.fill[(uint64_t)b * a.B.nblocks + blockIdx.x] = rp + cnt;
+                    a.B.fill[(uint64_t)(b + a.bin_base) * a.B.nblocks + blockIdx.x] = rp + cnt;
                 } else {
                     s.cur[b] = rp + cnt;
                     s.fill[b] = (w - (cnt << 16)) & (0xFFFF0000u | rmask);
@@ -452,7 +457,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1)
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (uint32_t b = threadIdx.x; b < a.nbins; b += blockDim.x) {
         s.fill[b] = 0;
-        s.cur[b] = a.B.fill[(uint64_t)b * a.B.nblocks + blockIdx.x];
+        s.cur[b] = a.B.fill[(uint64_t)(b + a.bin_base) * a.B.nblocks + blockIdx.x];
     }
     for (uint32_t g = threadIdx.x; g < a.B.ngroups; g += blockDim.x) {
         s.gbase[g] = a.B.gbase[g];
@@ -612,9 +617,10 @@ cudaError_t launch_mode(const float *xyz, const SketchDesc &d, const ScatterArgs
         kern<<<a.B.nblocks, kScatterThreads, smem, s>>>(xyz, d, a, C);
         return cudaGetLastError();
     };
-    // five rows (every configuration here) get a fully unrolled variant; an
-    // unaligned buffer (a slice of a larger one) the generic one
-    if (d.rows == 5 && vec)
+    // five rows in one pass (every configuration here but the largest
+    // sketches) get a fully unrolled variant; row passes and an unaligned
+    // buffer (a slice of a larger one) the generic one
+    if (a.nrows == 5 && a.row0 == 0 && vec)
         return sampled ? launch(k_bin_scatter<5, true, MODE, true>) : launch(k_bin_scatter<5, true, MODE, false>);
     if (vec)
         return sampled ? launch(k_bin_scatter<0, true, MODE, true>) : launch(k_bin_scatter<0, true, MODE, false>);

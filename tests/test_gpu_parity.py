@@ -87,7 +87,8 @@ def test_update_from_host_buffers(hs, small):
     assert np.array_equal(sk.counters(), want)
 
 
-@pytest.mark.parametrize("rows,log2w", [(1, 10), (3, 14), (4, 8), (7, 18), (32, 6), (5, 24)])
+@pytest.mark.parametrize("rows,log2w", [(1, 10), (3, 14), (4, 8), (7, 18), (32, 6), (5, 24),
+                                       (7, 24), (5, 26)])
 @pytest.mark.parametrize("update", ["direct", "binned"])
 def test_update_other_shapes(hs, small, rows, log2w, update):
     spec, xyz = small
