@@ -124,6 +124,8 @@ typedef struct {
     double flush_ms;            /* their summed device time (part of update_ms)*/
     uint64_t h2d_bytes;         /* bytes staged from host buffers              */
     double h2d_ms;              /* summed device time of those copies          */
+    uint64_t host_path_volumes; /* batch: volumes the last top-k answered one by
+                                   one instead of in its single graph           */
 } hs_stats;
 
 /*

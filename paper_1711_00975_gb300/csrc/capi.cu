@@ -404,20 +404,26 @@ hs_status ensure_bins(hs_sketch *h, uint64_t n, double rate, uint64_t launches) 
     return HS_OK;
 }
 
+// Regions for a call of n particles at `rate`: regions sized for a smaller
+// call are drained and grown for this one.
+static hs_status size_regions(hs_sketch *h, uint64_t n, double rate) {
+    if (h->bb.codes) {
+        const double mean = (double)n * rate * h->d.rows / ((double)h->bl.nbins * h->bb.nblocks);
+        if (region_capacity(mean, h->bl.half, 1.0) > h->bb.min_cap && !h->routing) {
+            HS_TRY(drain(h));
+            HS_CUDA(cudaStreamSynchronize(h->stream));
+            free_bins(h->bb);
+        }
+    }
+    return ensure_bins(h, n, rate);
+}
+
 // xyz: float32 positions, or packed 64-bit records when packed is set
 hs_status launch_update_timed(hs_sketch *h, const float *xyz, uint64_t n, uint64_t g0,
                               double rate, bool packed) {
     const size_t esz = packed ? 8 : 12;
     if (want_binned(h, n, rate)) {
-        if (h->bb.codes) {   // regions sized for a smaller call: grow them for this one
-            const double mean = (double)n * rate * h->d.rows / ((double)h->bl.nbins * h->bb.nblocks);
-            if (region_capacity(mean, h->bl.half, 1.0) > h->bb.min_cap && !h->routing) {
-                HS_TRY(drain(h));
-                HS_CUDA(cudaStreamSynchronize(h->stream));
-                free_bins(h->bb);
-            }
-        }
-        HS_TRY(ensure_bins(h, n, rate));
+        HS_TRY(size_regions(h, n, rate));
         // expected codes per region of one particle; each launch adds at most
         // one partial half (padded) per region
         const double per = rate * h->d.rows / ((double)h->bl.nbins * h->bb.nblocks);
@@ -470,6 +476,136 @@ hs_status launch_update_direct(hs_sketch *h, const float *xyz, uint64_t n, uint6
     h->stats.kernel_launches += 1;
     return HS_OK;
 }
+
+// Scatter passes one update of h takes over its input (row passes of a
+// sketch whose rings do not fit one block).
+static uint32_t scatter_passes(const hs_sketch *h) {
+    const uint32_t rpp = h->bl.rows_per_pass ? h->bl.rows_per_pass : h->d.rows;
+    return (h->d.rows + rpp - 1) / rpp;
+}
+
+// The compaction pass pays when the binned updates of h (and of its
+// super-item sketch) would read the float32 input in several passes: it
+// reads 12 bytes a particle once and writes 8 a kept one, which every pass
+// then reads instead of 12 a particle.
+bool want_compact(hs_sketch *h, uint64_t n, double rate, bool packed) {
+    if (packed || h->routing || h->is_view || h->d.F != 1 || h->d.Gq >= (1u << kPackBits))
+        return false;
+    if (!want_binned(h, n, rate)) return false;
+    uint32_t passes = scatter_passes(h);
+    if (h->super) {
+        if (!want_binned(h->super, n, rate)) return false;
+        passes += scatter_passes(h->super);
+    }
+    return 12.0 + 8.0 * rate * (1.0 + passes) < 12.0 * passes;
+}
+
+// Binned update of h from the cell records of a compaction pass: `bound`
+// records at most, *cells_cnt of them written; about bound * rate expected.
+static hs_status launch_cells_timed(hs_sketch *h, uint64_t bound, double rate) {
+    HS_TRY(size_regions(h, bound, rate));
+    const double per = (double)h->d.rows / ((double)h->bl.nbins * h->bb.nblocks);   // a record
+    const double room = h->pending_limit - h->bl.half;
+    if (room < 1.0) return fail(HS_ERR_STATE, "binned regions too small for an update");
+    // launches of room / per records up to a generous bound on the count;
+    // one more takes whatever lies beyond (in practice nothing)
+    const double expect = (double)bound * rate;
+    const uint64_t likely = std::min<uint64_t>(
+        bound, ((uint64_t)(1.05 * expect + 8.0 * std::sqrt(expect) + 4096.0) + 3) & ~3ull);
+    const uint64_t piece = std::max<uint64_t>(4, (uint64_t)std::floor(room / per) & ~3ull);
+    for (uint64_t off = 0; off < bound;) {
+        const uint64_t cnt = off < likely ? std::min(piece, likely - off) : bound - off;
+        const double add = (off < likely ? (double)cnt * per : 0.0) + h->bl.half;
+        if (h->pending + add > h->pending_limit) HS_TRY(drain(h));
+        EventPair ev;
+        HS_TRY(take_events(h, &ev));
+        cudaEventRecord(ev.a, h->stream);
+        HS_CUDA(launch_bin_scatter(reinterpret_cast<const float *>(h->cells + off), cnt, 0, h->d,
+                                   h->C, 1.0, h->p.sample_seed, nullptr, 0, 0, h->bl,
+                                   h->bb.store(), h->stream, nullptr, 0, 0, nullptr, 2, 0, 0,
+                                   nullptr, h->cells_cnt, off));
+        cudaEventRecord(ev.b, h->stream);
+        h->pending_update.push_back(ev);
+        h->pending += add;
+        h->stats.update_launches += 1;
+        h->stats.kernel_launches += scatter_passes(h);
+        off += cnt;
+    }
+    return HS_OK;
+}
+
+// The cells of a call's kept particles accumulate in h->cells (at most
+// h->cells_bound records: every particle appended so far) and go through the
+// binned passes of h and of its super-item sketch once per call, or when the
+// buffer would overflow.  The super-item sketch reads the same records (it
+// runs on h's stream).
+static hs_status cells_flush(hs_sketch *h, double rate) {
+    if (h->cells_bound == 0) return HS_OK;
+    HS_TRY(launch_cells_timed(h, h->cells_bound, rate));
+    if (hs_sketch *s = h->super) {
+        s->cells = h->cells;
+        s->cells_cnt = h->cells_cnt;
+        hs_status st = launch_cells_timed(s, h->cells_bound, rate);
+        s->cells = nullptr;
+        s->cells_cnt = nullptr;
+        HS_TRY(st);
+    }
+    HS_CUDA(cudaMemsetAsync(h->cells_cnt, 0, sizeof(unsigned long long), h->stream));
+    h->cells_bound = 0;
+    return HS_OK;
+}
+
+// The compaction pass over float32 particles (device or page-locked host
+// memory) of a call of call_n particles: the cells of the kept ones are
+// appended; it writes both sketches' probes.
+static hs_status cells_append(hs_sketch *h, const float *xyz, uint64_t n, uint64_t g0, double rate,
+                              uint64_t call_n) {
+    const uint64_t want = std::max<uint64_t>(std::min(call_n, kCellsMax), 1u << 20);
+    if (h->cells_bound == 0 && h->cells_cap < want) {
+        if (h->cells) cudaFree(h->cells);
+        h->cells = nullptr;
+        h->cells_cap = 0;
+        HS_CUDA(cudaMalloc(&h->cells, want * 8));
+        h->cells_cap = want;
+    }
+    if (!h->cells_cnt) {
+        HS_CUDA(cudaMalloc(&h->cells_cnt, sizeof(unsigned long long)));
+        HS_CUDA(cudaMemsetAsync(h->cells_cnt, 0, sizeof(unsigned long long), h->stream));
+    }
+    hs_sketch *s = h->super;
+    const CompactProbe p0{h->probe, h->probe_base, h->probe_base + kProbeCap, 1, 0, h->d.G};
+    const CompactProbe p1 = s ? CompactProbe{s->probe, s->probe_base, s->probe_base + kProbeCap,
+                                             s->d.F, s->d.fmagic, s->d.G}
+                              : CompactProbe{nullptr, 0, 0, 1, 0, 1};
+    for (uint64_t off = 0; off < n;) {
+        const uint64_t cnt = std::min(n - off, h->cells_cap);
+        if (h->cells_bound + cnt > h->cells_cap) HS_TRY(cells_flush(h, rate));
+        EventPair ev;
+        HS_TRY(take_events(h, &ev));
+        cudaEventRecord(ev.a, h->stream);
+        HS_CUDA(launch_compact_cells(xyz + 3 * off, cnt, g0 + off, h->d, rate, h->p.sample_seed, p0,
+                                     p1, h->cells, h->cells_cnt, h->num_sms * 8, h->stream));
+        cudaEventRecord(ev.b, h->stream);
+        h->pending_update.push_back(ev);
+        h->stats.kernel_launches += 1;
+        h->cells_bound += cnt;
+        off += cnt;
+    }
+    return HS_OK;
+}
+
+// One piece of an update call: appended to the call's compacted cells (when
+// the call compacts), else the sketch's (and its super-item sketch's) own
+// scatter.  update_finish ends the call.
+hs_status update_piece(hs_sketch *h, const float *xyz, uint64_t n, uint64_t g0, double rate,
+                       bool packed, bool compact, uint64_t call_n) {
+    if (compact) return cells_append(h, xyz, n, g0, rate, call_n);
+    HS_TRY(launch_update_timed(h, xyz, n, g0, rate, packed));
+    if (h->super) HS_TRY(launch_update_timed(h->super, xyz, n, g0, rate, packed));
+    return HS_OK;
+}
+
+hs_status update_finish(hs_sketch *h, double rate) { return cells_flush(h, rate); }
 
 // Directory search of one pass; *used = false when it does not apply (too
 // many hot buckets, more work than the scan, or memory short).
@@ -681,6 +817,8 @@ hs_status sketch_destroy(hs_sketch *h) {
     free_bins(h->bb);
     if (h->C && !h->is_view) cudaFree(h->C);
     if (h->probe && !h->is_view) cudaFree(h->probe);
+    if (h->cells) cudaFree(h->cells);
+    if (h->cells_cnt) cudaFree(h->cells_cnt);
     if (h->q_keys) cudaFree(h->q_keys);
     if (h->q_est) cudaFree(h->q_est);
     if (h->flags) cudaFree(h->flags);
@@ -715,16 +853,15 @@ static hs_status update_common(hs_sketch *h, const void *src, uint64_t n, double
     const size_t esz = packed ? 8 : 12;
     const float *xyz = static_cast<const float *>(src);
     const void *view = nullptr;
+    const bool compact = want_compact(h, n, sample_rate, packed);
     if (is_device_ptr(src)) {
-        hs_status st = launch_update_timed(h, xyz, n, h->n_seen, sample_rate, packed);
-        if (st == HS_OK && h->super)
-            st = launch_update_timed(h->super, xyz, n, h->n_seen, sample_rate, packed);
-        if (st != HS_OK) return st;
+        HS_TRY(update_piece(h, xyz, n, h->n_seen, sample_rate, packed, compact, n));
     } else if (!h->super && (view = pinned_device_view(src)) != nullptr) {
         // page-locked host memory: the kernels read it over the host link
-        // once (a hierarchy would read it twice, so it stages instead)
-        HS_TRY(launch_update_timed(h, static_cast<const float *>(view), n, h->n_seen, sample_rate,
-                                   packed));
+        // once (a hierarchy stages it: its compaction pass, reading the link
+        // directly, measured slower than staged copies overlapping the work)
+        HS_TRY(update_piece(h, static_cast<const float *>(view), n, h->n_seen, sample_rate, packed,
+                            compact, n));
         h->stats.h2d_bytes += n * esz;
     } else {
         hs_status st = ensure_staging(h);
@@ -751,14 +888,11 @@ static hs_status update_common(hs_sketch *h, const void *src, uint64_t n, double
             h->stats.h2d_bytes += cnt * esz;
             HS_CUDA(cudaEventRecord(h->ev_copied[b], h->copy_stream));
             HS_CUDA(cudaStreamWaitEvent(h->stream, h->ev_copied[b], 0));
-            st = launch_update_timed(h, h->stage[b], cnt, h->n_seen + off, sample_rate, packed);
-            if (st == HS_OK && h->super)
-                st = launch_update_timed(h->super, h->stage[b], cnt, h->n_seen + off, sample_rate,
-                                         packed);
-            if (st != HS_OK) return st;
+            HS_TRY(update_piece(h, h->stage[b], cnt, h->n_seen + off, sample_rate, packed, compact, n));
             HS_CUDA(cudaEventRecord(h->ev_free[b], h->stream));
         }
     }
+    HS_TRY(update_finish(h, sample_rate));
     h->n_seen += n;
     if (h->super) h->super->n_seen += n;
     return HS_OK;
@@ -1065,6 +1199,8 @@ hs_status sketch_reset(hs_sketch *h) {
     if (st != HS_OK) return st;
     HS_CUDA(cudaMemsetAsync(h->C, 0, (size_t)h->d.rows * h->d.W * 4, h->stream));
     HS_CUDA(cudaMemsetAsync(h->probe, 0xFF, kProbeCap * 8, h->stream));
+    if (h->cells_cnt) HS_CUDA(cudaMemsetAsync(h->cells_cnt, 0, sizeof(unsigned long long), h->stream));
+    h->cells_bound = 0;
     h->n_seen = 0;
     h->probe_base = 0;
     if (h->super) return sketch_reset(h->super);

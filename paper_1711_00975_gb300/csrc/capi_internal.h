@@ -38,6 +38,7 @@ hs_status fail(hs_status st, const char *fmt, ...);
     } while (0)
 
 constexpr uint64_t kProbeCap = 1ull << 20;        // keys of the first 2^20 particles
+constexpr uint64_t kCellsMax = 1ull << 27;       // cell records buffered (1 GiB)
 constexpr uint32_t kProbeSlotsLog2 = 21;
 constexpr uint64_t kStageParticles = 1ull << 24;  // 192 MiB per staging buffer
 constexpr int kStageBuffers = 3;                    // copies run ahead through a drain
@@ -105,6 +106,10 @@ struct hs_sketch {
     uint64_t cap = 0;               // candidate capacity
     uint64_t min_cap = 0;           // extra candidates a learned top-k appends
     hs_sketch *super = nullptr;     // hierarchy: sketch of F^3 super-items (Algorithm 3)
+    uint64_t *cells = nullptr;      // compaction: cells of a call's kept particles
+    uint64_t cells_cap = 0;
+    uint64_t cells_bound = 0;       // records appended at most (particles compacted)
+    unsigned long long *cells_cnt = nullptr;
     uint32_t super_mult = 0;        // hierarchy: c of the top-(c*k) super-items
     uint64_t *cand_key = nullptr;
     int32_t *cand_est = nullptr;
@@ -181,6 +186,10 @@ hs_status launch_update_timed(hs_sketch *h, const float *xyz, uint64_t n, uint64
                               double rate, bool packed = false);
 hs_status launch_update_direct(hs_sketch *h, const float *xyz, uint64_t n, uint64_t g0,
                                double rate, bool packed = false);
+bool want_compact(hs_sketch *h, uint64_t n, double rate, bool packed);
+hs_status update_piece(hs_sketch *h, const float *xyz, uint64_t n, uint64_t g0, double rate,
+                       bool packed, bool compact, uint64_t call_n);
+hs_status update_finish(hs_sketch *h, double rate);
 hs_status search_pass_dir(hs_sketch *h, int32_t theta, SearchMode mode, int64_t hot,
                           uint64_t line_lo, uint64_t line_hi, SearchOut out, bool *used);
 hs_status search_pass(hs_sketch *h, int32_t theta, SearchMode mode, uint64_t line_lo,

@@ -99,6 +99,18 @@ __device__ __forceinline__ int32_t signed_count(int32_t c, uint64_t v, uint32_t 
     return ((v >> (63 - log2w)) & 1ull) ? (int32_t)(0u - u) : (int32_t)u;
 }
 
+// L_r(cy, cz) = a1*cy + a2*cz + b (mod 2^64): row r's value of mesh line
+// (cy, cz) without the cx term (v_r = a0*cx + L_r)
+__device__ __forceinline__ uint64_t line_value(const RowSeed &s, uint32_t cy, uint32_t cz) {
+    return s.b + mul_lo64(s.a1, cy) + mul_lo64(s.a2, cz);
+}
+
+// bit `bucket` of row r of a hot-bucket bitmap (words_per_row 32-bit words a row)
+__device__ __forceinline__ bool exact_hot(const uint32_t *__restrict__ bits, uint64_t words_per_row,
+                                          int r, uint32_t bucket) {
+    return (__ldg(bits + (uint64_t)r * words_per_row + (bucket >> 5)) >> (bucket & 31)) & 1u;
+}
+
 // Periodic reduction of a cell index outside [0, G) (rare: only particles
 // outside the box); kept out of line so the common path stays short.
 static __device__ __noinline__ uint32_t wrap_cell(int i, uint32_t G) {

@@ -48,7 +48,10 @@ struct BinLayout {
 };
 // single_pass: every row in one launch or not at all (batches: a volume's bins
 // are offset within one launch)
-BinLayout bin_layout(const SketchDesc &d, size_t smem_budget, bool single_pass = false);
+// max_S: largest bin (log2 counters; 15 fills a block's shared memory in the
+// accumulation)
+BinLayout bin_layout(const SketchDesc &d, size_t smem_budget, bool single_pass = false,
+                     uint32_t max_S = 15);
 constexpr uint32_t kMaxBinGroups = 128;
 constexpr uint32_t kScatterTile = 3072;   // particles of one scatter tile (768 threads x 4)
 // Global side of the binned update.  Each scatter block owns one region per
@@ -85,7 +88,37 @@ cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const 
                                const BinStore &B, cudaStream_t s,
                                const VolumeDesc *vols = nullptr, uint32_t nvol = 0,
                                uint32_t probe_per_vol = 0, const RouteTarget *route = nullptr,
-                               int packed = 0, uint32_t rounds = 0, uint32_t slot = 0);
+                               int packed = 0, uint32_t rounds = 0, uint32_t slot = 0,
+                               uint32_t *tile_vols = nullptr,
+                               const unsigned long long *n_dev = nullptr, uint64_t n_base = 0);
+// packed: 0 float32 xyz, 1 packed position records, 2 cell records (from
+// launch_compact_cells; n is then a bound and the launch takes the records
+// [n_base, min(n_base + n, *n_dev)) of the buffer starting n_base before xyz)
+// Rings of a batch's scatter: the bins of a window of `wvols` consecutive
+// volumes (a power of two) have rings of `slot` entries; tiles holding
+// particles of later volumes move the window.  slot_cap: 0 or a smaller ring.
+struct BatchRing {
+    uint32_t wvols, nslots, slot;
+};
+BatchRing batch_ring(const BinLayout &L, const SketchDesc &d, uint32_t ngroups, double rate,
+                     uint32_t slot_cap);
+// Compaction of a stream piece for several passes over it: every particle is
+// sampled (index g0 + i) and quantised once on d's mesh (d.F == 1); the
+// cells of kept, valid particles are appended to `cells` (cx | cy << 21 |
+// cz << 42, in no particular order) and counted in *count (reset by the
+// caller).  The probes of the sketch (probe, G) and of its super-item sketch
+// (sprobe, mesh G / F) record every particle of their windows [base, end).
+struct CompactProbe {
+    uint64_t *probe;
+    uint64_t base, end;
+    uint32_t F;            // 1: the fine mesh; > 1: blocks of F^3 cells
+    uint32_t fmagic;       // ceil(2^32 / F)
+    uint32_t G;            // mesh of the keys
+};
+cudaError_t launch_compact_cells(const float *xyz, uint64_t n, uint64_t g0, const SketchDesc &d,
+                                 double rate, uint64_t sample_seed, const CompactProbe &p0,
+                                 const CompactProbe &p1, uint64_t *cells,
+                                 unsigned long long *count, int blocks, cudaStream_t s);
 // C[bin range] += the codes of every region, then fill = 0
 cudaError_t launch_bin_accumulate(const BinLayout &L, const BinStore &B, int32_t *C,
                                   cudaStream_t s);
@@ -218,6 +251,49 @@ cudaError_t launch_dir_query(const int32_t *C, const SketchDesc &d, int r, uint3
                              uint64_t n_hot, const uint32_t *bits, int32_t theta, SearchMode mode,
                              uint64_t line_lo, uint64_t line_hi, SearchOut out, int max_blocks,
                              cudaStream_t s, RouteFilter skip = RouteFilter{nullptr, 0, 0, 0});
+
+// ---- top-k of a batch of sketches in one launch sequence (k_batch_topk.cu) ----
+struct BatchTopkVol {     // one volume's query, filled by the host before each launch
+    uint64_t m_probe;     // probe entries recorded (at most probe_per_vol)
+    uint32_t G;           // mesh cells a side
+    uint32_t kk;          // min(k, G^3)
+    uint32_t use;         // 0: the host's general path answers this volume
+    uint32_t D;           // its directories have 2^D slots (D >= log2 W: a
+                          // bucket's lines are the records of a run of slots)
+};
+struct BatchTopkBufs {    // device buffers; per-volume arrays are volume-major
+    const BatchTopkVol *vol;
+    uint32_t nvol, F;     // F: rows enumerated by the directory search
+    uint32_t k;           // output stride per volume
+    uint32_t hot_cap;     // hot buckets listed per (volume, row)
+    uint32_t cand_cap;    // candidates per volume
+    uint32_t set_log2;    // probe set slots per volume = 2^set_log2
+    uint64_t probe_per_vol;
+    const uint64_t *probe;        // nvol x probe_per_vol probe keys
+    unsigned long long *set;      // nvol x 2^set_log2
+    uint64_t *dkey;               // distinct probe cells, nvol x probe_per_vol
+    int32_t *dest;
+    uint32_t *dcnt;               // nvol
+    int32_t *theta;               // nvol
+    uint32_t *status;             // nvol: 0, or why the host must answer the volume
+    uint32_t *scan;               // nvol: 1 when the volume's cells are scanned
+    uint32_t *bits;               // nvol x rows x W/32 hot bitmap
+    uint32_t *hot;                // nvol x F x hot_cap
+    uint32_t *hot_cnt;            // nvol x F
+    unsigned long long *pre;      // nvol x F + 1 work prefix
+    const uint32_t *const *dir_off;   // nvol x F directory slot offsets
+    const DirRecord *const *dir_rec;  // nvol x F directory records
+    uint64_t *ckey;               // nvol x cand_cap candidates
+    int32_t *cest;
+    uint32_t *ccnt;               // nvol
+    uint64_t *okey;               // nvol x k results in rank order
+    int32_t *oest;
+    uint32_t *on;                 // nvol: results written
+};
+// counters C: nvol x rows x W int32 (W >= 32); every launch on stream s
+cudaError_t launch_batch_topk(const int32_t *C, const SketchDesc &d, const BatchTopkBufs &b,
+                              int num_sms, cudaStream_t s, int *launches);
+size_t batch_topk_final_smem(uint32_t k);
 
 // ---- ranking (k_select.cu) ----
 struct SelectState {

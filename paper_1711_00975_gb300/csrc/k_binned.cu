@@ -91,6 +91,26 @@ __global__ void __launch_bounds__(kAccThreads)
 
 uint32_t magic_of(uint32_t d) { return (uint32_t)((0x100000000ull + d - 1) / d); }
 
+// Per scatter tile of a batch: its first and last particle's volumes
+// (first | last << 16; the volume of particle i is the last whose start <= i).
+__global__ void k_tile_vols(const VolumeDesc *__restrict__ vols, uint32_t nvol, uint64_t n,
+                            uint64_t ntiles, uint32_t *__restrict__ out) {
+    auto vol = [&](uint64_t i) {
+        uint32_t lo = 0, hi = nvol;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (vols[mid].start <= i) lo = mid; else hi = mid;
+        }
+        return lo;
+    };
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += stride) {
+        const uint64_t i0 = t * kScatterTile;
+        const uint64_t i1 = (i0 + kScatterTile < n ? i0 + kScatterTile : n) - 1;
+        out[t] = vol(i0) | (vol(i1) << 16);
+    }
+}
+
 }  // namespace
 
 cudaError_t ensure_smem_limit(const void *kernel, size_t bytes) {
@@ -107,9 +127,10 @@ cudaError_t ensure_smem_limit(const void *kernel, size_t bytes) {
     return e;
 }
 
-BinLayout bin_layout(const SketchDesc &d, size_t smem_budget, bool single_pass) {
+BinLayout bin_layout(const SketchDesc &d, size_t smem_budget, bool single_pass, uint32_t max_S) {
     BinLayout L{};
-    L.S = d.log2w < 15 ? d.log2w : 15;
+    if (max_S > 15) max_S = 15;
+    L.S = d.log2w < max_S ? d.log2w : max_S;
     const uint64_t nb = (uint64_t)d.rows << (d.log2w - L.S);
     if (nb >= 65536) return L;                // bins are 16-bit numbers (group division)
     L.nbins = (uint32_t)nb;
@@ -131,21 +152,46 @@ BinLayout bin_layout(const SketchDesc &d, size_t smem_budget, bool single_pass) 
     return L;
 }
 
+BatchRing batch_ring(const BinLayout &L, const SketchDesc &d, uint32_t ngroups, double rate,
+                     uint32_t slot_cap) {
+    const uint32_t lbpr = d.log2w - L.S;
+    const uint32_t bpv = d.rows << lbpr;
+    const bool sampled = rate < 1.0;
+    // codes one tile adds to each bin of its volume; a ring holds a half
+    // left over from the last flush and one tile's codes
+    const double per_tile = kScatterTile * rate / (double)(1u << lbpr);
+    BatchRing r{0, 0, 0};
+    for (uint32_t wv = 4; wv >= 1; wv >>= 1) {
+        uint32_t slot = ring_slot(wv * bpv, ngroups, sampled ? 1 : 0, kSmemLimit, true);
+        if (slot_cap && slot_cap < slot) slot = slot_cap;
+        if (slot >= 16 && (slot >= 2.5 * per_tile || wv == 1)) {
+            r = BatchRing{wv, wv * bpv, slot};
+            break;
+        }
+    }
+    return r;
+}
+
 cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const SketchDesc &d,
                                int32_t *C, double rate, uint64_t sample_seed, uint64_t *probe,
                                uint64_t probe_base, uint64_t probe_cap, const BinLayout &L,
                                const BinStore &B, cudaStream_t s, const VolumeDesc *vols,
                                uint32_t nvol, uint32_t probe_per_vol, const RouteTarget *route,
-                               int packed, uint32_t rounds, uint32_t slot) {
+                               int packed, uint32_t rounds, uint32_t slot, uint32_t *tile_vols,
+                               const unsigned long long *n_dev, uint64_t n_base) {
     if (n == 0) return cudaSuccess;
+    if (vols && (!tile_vols || nvol == 0 || nvol > 65535)) return cudaErrorInvalidValue;
     if (L.slot == 0 || B.nblocks == 0 || !B.codes || !B.fill || B.ngroups == 0 ||
         B.ngroups > kMaxBinGroups || (uint64_t)B.bpg * B.ngroups != L.nbins)
         return cudaErrorInvalidValue;
     if (packed && (vols || route)) return cudaErrorInvalidValue;   // float input only there
+    if (packed == 2 && (!n_dev || rate < 1.0 || probe)) return cudaErrorInvalidValue;   // already sampled
     ScatterArgs a;
     std::memset(&a, 0, sizeof(a));
     const bool sampled = rate < 1.0;
     a.n = n;
+    a.n_dev = packed == 2 ? n_dev : nullptr;
+    a.n_base = n_base;
     a.g0 = g0;
     a.thr = sampled ? (uint64_t)ldexp(rate, 64) : 0;
     a.sample_seed = sample_seed;
@@ -182,15 +228,32 @@ cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const 
         a.probe_end = probe && row0 == 0 ? probe_base + probe_cap : probe_base;
         a.slot = ring_slot(a.nbins, B.ngroups, sampled ? 1 : 0, kSmemLimit);
         if (slot && slot < a.slot) a.slot = slot;     // a shallower ring (power of two)
+        if (vols) {   // rings for a window of volumes, one tile between flushes
+            const BatchRing br = batch_ring(L, d, B.ngroups, rate, slot);
+            if (br.wvols == 0) return cudaErrorInvalidValue;
+            a.wvols = br.wvols;
+            a.bpv = d.rows << lbpr;
+            a.nbins = br.nslots;
+            a.slot = br.slot;
+            a.rounds = 1;
+            a.tvols = tile_vols;
+            const uint64_t ntiles = (n + kScatterTile - 1) / kScatterTile;
+            k_tile_vols<<<(unsigned)std::min<uint64_t>((ntiles + 255) / 256, 1024), 256, 0, s>>>(
+                vols, nvol, n, ntiles, tile_vols);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
         if (a.slot < 16 || (a.slot & (a.slot - 1))) return cudaErrorInvalidValue;
         a.half = a.slot / 2;
         a.team = a.half <= 64 ? 1u : 32u;
-        const size_t smem = smem_layout(a.nbins, a.slot, B.ngroups, sampled ? 1 : 0).total;
+        const size_t smem = smem_layout(a.nbins, a.slot, B.ngroups, sampled ? 1 : 0, a.wvols != 0).total;
         cudaError_t e;
         if (vols) {
             e = launch_modes_batch_route(kModeBatch, xyz, d, a, sampled, smem, Cu, s);
         } else if (route) {
             e = launch_modes_batch_route(kModeRoute, xyz, d, a, sampled, smem, Cu, s);
+        } else if (packed == 2) {
+            e = launch_modes_cells(d.F > 1 ? kModeSuperCells : kModeCells, xyz, d, a, smem, Cu, s);
         } else {
             const int mode = packed ? (d.F > 1 ? kModeSuperPacked : kModePlainPacked)
                                     : (d.F > 1 ? kModeSuper : kModePlain);

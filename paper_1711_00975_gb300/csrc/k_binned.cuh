@@ -47,9 +47,16 @@ constexpr uint32_t kSmemLimit = 227 * 1024;   // dynamic shared memory of one bl
 constexpr int kModePlain = 0, kModeBatch = 1, kModeRoute = 2, kModeSuper = 3;
 // the same for packed 64-bit particle records instead of float32 xyz
 constexpr int kModePlainPacked = 4, kModeSuperPacked = 5;
+// the same for cell records (kept particles' mesh cells, written by the
+// compaction pass: cx | cy << 21 | cz << 42, already sampled)
+constexpr int kModeCells = 6, kModeSuperCells = 7;
 
 struct ScatterArgs {
     uint64_t n;
+    // cell records: the buffer holds *n_dev records (device counter, read at
+    // launch) and this launch takes its elements [n_base, n_base + n)
+    const unsigned long long *n_dev;
+    uint64_t n_base;
     uint64_t g0;
     uint64_t thr;
     uint64_t sample_seed;
@@ -76,23 +83,30 @@ struct ScatterArgs {
     const VolumeDesc *vols;   // batch: one entry per volume (nullptr for one sketch)
     uint32_t nvol;
     uint32_t probe_per_vol;   // batch: probe window of each volume
+    // batch window: rings for the bins of `wvols` consecutive volumes only (a
+    // power of two; 0: every bin has a ring); volume v's bins use ring slots
+    // (v mod wvols) * bpv ... + bpv - 1 while v is in the window
+    uint32_t wvols;
+    uint32_t bpv;             // bins per volume
+    const uint32_t *tvols;    // per tile: first volume | last volume << 16
 };
 
 // Byte offsets of the scatter's shared memory (host and device agree).
 struct SmemLayout {
-    uint32_t fill, cur, gbase, gcap, ring, queue, total;
+    uint32_t fill, cur, gbase, gcap, gbin, ring, queue, total;
 };
 
 __host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 
 __host__ __device__ inline SmemLayout smem_layout(uint32_t nbins, uint32_t slot, uint32_t ngroups,
-                                                  uint32_t queue) {
+                                                  uint32_t queue, bool window = false) {
     SmemLayout L;
     uint32_t off = 0;
     L.fill = off;  off = align16(off + 4 * nbins);
     L.cur = off;   off = align16(off + 4 * nbins);
     L.gbase = off; off = align16(off + 8 * ngroups);
     L.gcap = off;  off = align16(off + 4 * ngroups);
+    L.gbin = off;  off = align16(off + (window ? 4 * nbins + 4 : 0u));   // + the next window
     L.ring = off;  off = align16(off + 2 * nbins * slot);
     L.queue = off; off = align16(off + (queue ? 8u * kQueue * (kScatterThreads / 32) : 0u));
     L.total = off;
@@ -100,20 +114,38 @@ __host__ __device__ inline SmemLayout smem_layout(uint32_t nbins, uint32_t slot,
 }
 
 // Largest ring (a power of two in [16, 16384] entries per bin) whose layout fits.
-inline uint32_t ring_slot(uint32_t nbins, uint32_t ngroups, uint32_t queue, size_t budget) {
+inline uint32_t ring_slot(uint32_t nbins, uint32_t ngroups, uint32_t queue, size_t budget,
+                          bool window = false) {
     for (uint32_t slot = 16384; slot >= 16; slot >>= 1)
-        if (smem_layout(nbins, slot, ngroups, queue).total <= budget) return slot;
+        if (smem_layout(nbins, slot, ngroups, queue, window).total <= budget) return slot;
     return 0;
 }
+
+constexpr uint32_t kNoBin = 0xFFFFFFFFu;   // a window's ring slot with no volume behind it
 
 struct Smem {
     uint32_t *fill;    // per bin: (entries not yet flushed << 16) | byte offset of the next entry
     uint32_t *cur;     // per bin: codes this block has written to its region
     uint64_t *gbase;   // per group: region base (codes)
     uint32_t *gcap;    // per group: region capacity (codes)
+    uint32_t *gbin;    // batch window: per ring slot, its global bin (or kNoBin); then the next window
     uint16_t *ring;    // per bin: `slot` entries
     uint64_t *queue;   // per warp: kQueue packed cells
 };
+
+// global bin of ring slot b (WIN: a batch, whose rings follow a window)
+template <bool WIN>
+__device__ __forceinline__ uint32_t gbin_of(const ScatterArgs &a, const Smem &s, uint32_t b) {
+    return WIN ? s.gbin[b] : b + a.bin_base;
+}
+
+// global bin of ring slot b while the window starts at volume w0: slot group
+// k = b / bpv holds the window's volume congruent to k modulo wvols
+__device__ __forceinline__ uint32_t window_gbin(const ScatterArgs &a, uint32_t w0, uint32_t b) {
+    const uint32_t k = b / a.bpv;
+    const uint32_t v = w0 + ((k - w0) & (a.wvols - 1));
+    return v < a.nvol ? v * a.bpv + (b - k * a.bpv) : kNoBin;
+}
 
 // (inlined: a call in the staging path costs register moves around every call
 // site, more instructions than the rare adds it guards)
@@ -140,6 +172,13 @@ __device__ __forceinline__ void route_add(const ScatterArgs &a, uint32_t cx, uin
     const uint32_t blk = __ldg(a.rprefix + w) + __popc(__ldg(f.bits + w) & ((1u << b) - 1u));
     const uint32_t local = (cx - qx * f.R) + f.R * ((cy - qy * f.R) + f.R * (cz - qz * f.R));
     atomicAdd(&a.rblocks[(uint64_t)blk * (f.R * f.R * f.R) + local], 1);
+}
+
+// The top 32 bits of v = a0*cx + a1*cy + a2*cz + b (mod 2^64), written as
+// plain 64-bit arithmetic (the compiler's own wide multiply-adds measured
+// fewer instructions than a hand-written chain).
+__device__ __forceinline__ uint32_t row_hi(const RowSeed &sd, uint32_t cx, uint32_t cy, uint32_t cz) {
+    return (uint32_t)((sd.a0 * cx + sd.a1 * cy + sd.a2 * cz + sd.b) >> 32);
 }
 
 // A particle's cell on the sketch's mesh, ready to hash: coordinates and the
@@ -210,13 +249,14 @@ __device__ __forceinline__ bool prep_particle(float x, float y, float z, uint64_
 template <int MODE, bool SAMPLED, bool PROBE>
 __device__ __forceinline__ bool prep_record(uint64_t p, uint64_t g, const SketchDesc &d,
                                             const ScatterArgs &a, Cell &c) {
+    constexpr bool CELLS = MODE == kModeCells || MODE == kModeSuperCells;
     const bool keep = !SAMPLED || splitmix64_at(a.sample_seed, g) < a.thr;
-    c.cx = packed_axis(p, 0, d.Gq);
-    c.cy = packed_axis(p, 1, d.Gq);
-    c.cz = packed_axis(p, 2, d.Gq);
+    c.cx = CELLS ? (uint32_t)(p & kPackMask) : packed_axis(p, 0, d.Gq);
+    c.cy = CELLS ? (uint32_t)((p >> kPackBits) & kPackMask) : packed_axis(p, 1, d.Gq);
+    c.cz = CELLS ? (uint32_t)((p >> (2 * kPackBits)) & kPackMask) : packed_axis(p, 2, d.Gq);
     c.bin0 = 0;
     const bool valid = !(p & kPackInvalid);
-    if (MODE == kModeSuperPacked) {
+    if (MODE == kModeSuperPacked || MODE == kModeSuperCells) {
         c.cx = __umulhi(c.cx, d.fmagic);
         c.cy = __umulhi(c.cy, d.fmagic);
         c.cz = __umulhi(c.cz, d.fmagic);
@@ -240,9 +280,13 @@ __device__ __forceinline__ uint32_t vol_of(const ScatterArgs &a, uint64_t i) {
 // belongs to volume v (vols[v].start <= i < vols[v+1].start, found from the
 // hint v upward); it is sampled with its index inside that volume's stream and
 // quantised on that volume's mesh.
+// The cell's bins are ring slots of its volume's slot group in the window of
+// volumes that have rings; a volume outside the window [w0, w0 + wvols) (a tile spanning
+// more volumes than the window holds) adds its rows directly.
 template <bool SAMPLED>
 __device__ __forceinline__ bool prep_particle_batch(float x, float y, float z, uint64_t i,
-                                                    const ScatterArgs &a, uint32_t &v, Cell &c) {
+                                                    const SketchDesc &d, const ScatterArgs &a,
+                                                    uint32_t w0, uint32_t &v, Cell &c, uint32_t *C) {
     while (v + 1 < a.nvol && i >= a.vols[v + 1].start) ++v;
     const VolumeDesc &V = a.vols[v];
     const uint64_t g = V.g0 + (i - V.start);
@@ -252,22 +296,41 @@ __device__ __forceinline__ bool prep_particle_batch(float x, float y, float z, u
     if (a.probe && g - V.probe_base < a.probe_per_vol)
         write_probe(a.probe + (uint64_t)v * a.probe_per_vol, g - V.probe_base, valid, c.cx, c.cy,
                     c.cz, V.G);
+    if (v - w0 >= a.wvols) {
+        if (keep && valid)
+            for (uint32_t r = 0; r < d.rows; ++r) {
+                const uint32_t h = row_hi(d.seed[r], c.cx, c.cy, c.cz) >> a.hshift;
+                direct_add(C, a.S, (h >> (a.S + 1)) + a.rbase[r] + V.bin0, h & a.code_mask);
+            }
+        return false;
+    }
+    c.bin0 = (v & (a.wvols - 1)) * a.bpv;
+    return keep && valid;
+}
+
+// prep_particle_batch for a tile that lies in one volume of the window: the
+// volume's fields are loaded once a tile (vg = g0 - start, probe_v = its
+// probe window, pbase = its probe_base, bin0 = its slot group's first ring).
+template <bool SAMPLED>
+__device__ __forceinline__ bool prep_particle_vol(float x, float y, float z, uint64_t i, uint64_t vg,
+                                                  float inv, uint32_t G, uint32_t bin0,
+                                                  uint64_t *probe_v, uint64_t pbase,
+                                                  const ScatterArgs &a, Cell &c) {
+    const uint64_t g = vg + i;
+    const bool keep = !SAMPLED || splitmix64_at(a.sample_seed, g) < a.thr;
+    const bool valid = mesh_cell(x, y, z, inv, G, (float)G, c);
+    c.bin0 = bin0;
+    if (probe_v && g - pbase < a.probe_per_vol) write_probe(probe_v, g - pbase, valid, c.cx, c.cy, c.cz, G);
     return keep && valid;
 }
 
 // A full ring gives the reservation back (no flush runs while codes are
 // staged, so the position is reused) and adds the code directly.
+template <bool WIN>
 __device__ __forceinline__ void stage_full(uint32_t bin, uint32_t code, const ScatterArgs &a,
                                            const Smem &s, uint32_t *C) {
     atomicAdd(&s.fill[bin], 0xFFFEFFFEu);   // minus (1 << 16 | 2)
-    direct_add(C, a.S, bin + a.bin_base, code);
-}
-
-// The top 32 bits of v = a0*cx + a1*cy + a2*cz + b (mod 2^64), written as
-// plain 64-bit arithmetic (the compiler's own wide multiply-adds measured
-// fewer instructions than a hand-written chain).
-__device__ __forceinline__ uint32_t row_hi(const RowSeed &sd, uint32_t cx, uint32_t cy, uint32_t cz) {
-    return (uint32_t)((sd.a0 * cx + sd.a1 * cy + sd.a2 * cz + sd.b) >> 32);
+    direct_add(C, a.S, gbin_of<WIN>(a, s, bin), code);
 }
 
 // Bins and codes of every row of one cell, staged in the bins' rings.  The
@@ -277,7 +340,7 @@ __device__ __forceinline__ uint32_t row_hi(const RowSeed &sd, uint32_t cx, uint3
 // A reservation (fill += 1 << 16 | 2) returns the entries waiting for a flush
 // (w >> 16) and the code's byte offset in the ring (w mod 2 slot); the byte
 // offset is kept below 2^16 by the flush phases.
-template <int T>
+template <int T, bool WIN>
 __device__ __forceinline__ void stage_cell(const Cell &c, const SketchDesc &d, const ScatterArgs &a,
                                            const Smem &s, uint32_t *C) {
     unsigned char *ring = reinterpret_cast<unsigned char *>(s.ring);
@@ -298,7 +361,7 @@ __device__ __forceinline__ void stage_cell(const Cell &c, const SketchDesc &d, c
             if ((w[r] >> 16) < a.slot)
                 *reinterpret_cast<uint16_t *>(ring + bin[r] * rbytes + (w[r] & (rbytes - 1))) = (uint16_t)code[r];
             else
-                stage_full(bin[r], code[r], a, s, C);
+                stage_full<WIN>(bin[r], code[r], a, s, C);
         }
     } else {
         for (uint32_t i = 0; i < a.nrows; ++i) {
@@ -309,7 +372,7 @@ __device__ __forceinline__ void stage_cell(const Cell &c, const SketchDesc &d, c
             if ((w >> 16) < a.slot)
                 *reinterpret_cast<uint16_t *>(ring + bin * rbytes + (w & (rbytes - 1))) = (uint16_t)code;
             else
-                stage_full(bin, code, a, s, C);
+                stage_full<WIN>(bin, code, a, s, C);
         }
     }
 }
@@ -343,10 +406,9 @@ __device__ __forceinline__ uint4 ring_chunk(const uint16_t *ring, uint32_t p0, u
 // Entries at or after index pad_from (relative to p0, even) are written as
 // cancelling pairs (the last, partial half).  Halves of 16 or more entries
 // leave in whole 32-byte sectors, one store each.
-__device__ __forceinline__ void write_out(uint32_t bin, uint32_t p0, uint32_t cnt, uint32_t rp,
-                                          uint32_t pad_from, uint32_t tl, uint32_t TS,
+__device__ __forceinline__ void write_out(uint32_t bin, uint32_t gbin, uint32_t p0, uint32_t cnt,
+                                          uint32_t rp, uint32_t pad_from, uint32_t tl, uint32_t TS,
                                           const ScatterArgs &a, const Smem &s, uint32_t *C) {
-    const uint32_t gbin = bin + a.bin_base;
     const uint32_t g = a.B.ngroups > 1 ? __umulhi(gbin, a.gmagic) : 0u;
     const uint32_t cap = s.gcap[g];
     uint16_t *dst = a.B.codes + s.gbase[g] +
@@ -372,12 +434,12 @@ __device__ __forceinline__ uint32_t flush_count(uint32_t pend, bool final, const
     return pend >= a.slot ? a.slot : (pend >= a.half ? a.half : 0u);
 }
 
-// Flush one bin whose fill word is w (lane tl of a team of TS lanes):
-// returns the entries written.  final: an odd last entry is added directly
-// so the padding is whole cancelling pairs.
-__device__ __forceinline__ uint32_t flush_bin(uint32_t b, uint32_t w, uint32_t rp, bool final,
-                                              uint32_t tl, uint32_t TS, const ScatterArgs &a,
-                                              const Smem &s, uint32_t *C) {
+// Flush ring slot b (global bin gb) whose fill word is w (lane tl of a team
+// of TS lanes): returns the entries written.  final: an odd last entry is
+// added directly so the padding is whole cancelling pairs.
+__device__ __forceinline__ uint32_t flush_bin(uint32_t b, uint32_t gb, uint32_t w, uint32_t rp,
+                                              bool final, uint32_t tl, uint32_t TS,
+                                              const ScatterArgs &a, const Smem &s, uint32_t *C) {
     const uint32_t pend = w >> 16;
     const uint32_t cnt = flush_count(pend, final, a);
     if (!cnt) return 0;
@@ -386,9 +448,9 @@ __device__ __forceinline__ uint32_t flush_bin(uint32_t b, uint32_t w, uint32_t r
     if (final) {
         pad_from = pend & ~1u;
         if ((pend & 1u) && tl == 0)
-            direct_add(C, a.S, b + a.bin_base, s.ring[b * a.slot + ((p0 + pend - 1) & (a.slot - 1))]);
+            direct_add(C, a.S, gb, s.ring[b * a.slot + ((p0 + pend - 1) & (a.slot - 1))]);
     }
-    write_out(b, p0, cnt, rp, pad_from, tl, TS, a, s, C);
+    write_out(b, gb, p0, cnt, rp, pad_from, tl, TS, a, s, C);
     return cnt;
 }
 
@@ -396,27 +458,43 @@ __device__ __forceinline__ uint32_t flush_bin(uint32_t b, uint32_t w, uint32_t r
 // every bin whose ring holds a complete half writes it to the block's region,
 // and every fill word's byte offset is reduced modulo the ring.  final: every
 // bin writes everything it holds and leaves its region fill in global memory.
+// A batch window moving to start at volume nw does the same as final for the
+// ring slots whose volume leaves, then loads the entering bins' region fills.
 // A team of TS lanes takes one bin: one lane while halves are small, a whole
 // warp for the large halves of sketches with few bins.
-__device__ __forceinline__ void flush_phase(bool final, const ScatterArgs &a, const Smem &s,
-                                            uint32_t *C) {
+template <bool WIN>
+__device__ __forceinline__ void flush_phase(bool final, uint32_t nw, const ScatterArgs &a,
+                                            const Smem &s, uint32_t *C) {
     const uint32_t rmask = 2 * a.slot - 1;
     const uint32_t TS = a.team, per = 32 / TS;
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const uint32_t tl = lane & (TS - 1);
-    for (uint32_t base = warp * per; base < a.nbins; base += nwarps * per) {
+    for (uint32_t base = warp * per; base < a.nbins; base += nwarps * per) {   // warp-uniform
         const uint32_t b = base + lane / TS;
+        uint32_t w = 0, rp = 0, cnt = 0, gb = kNoBin, ng = kNoBin;
+        bool leave = final;
         if (b < a.nbins) {
-            const uint32_t w = s.fill[b];
-            const uint32_t rp = s.cur[b];
-            const uint32_t cnt = flush_bin(b, w, rp, final, tl, TS, a, s, C);
-            if (tl == 0) {
-                if (final) {
-                    a.B.fill[(uint64_t)(b + a.bin_base) * a.B.nblocks + blockIdx.x] = rp + cnt;
-                } else {
-                    s.cur[b] = rp + cnt;
-                    s.fill[b] = (w - (cnt << 16)) & (0xFFFF0000u | rmask);
+            w = s.fill[b];
+            rp = s.cur[b];
+            gb = gbin_of<WIN>(a, s, b);
+            if (WIN && !final) {
+                ng = window_gbin(a, nw, b);
+                leave = ng != gb;
+            }
+            if (!WIN || gb != kNoBin) cnt = flush_bin(b, gb, w, rp, leave, tl, TS, a, s, C);
+        }
+        __syncwarp();          // the team has read the slot's words
+        if (b < a.nbins && tl == 0) {
+            if (leave) {
+                if (!WIN || gb != kNoBin) a.B.fill[(uint64_t)gb * a.B.nblocks + blockIdx.x] = rp + cnt;
+                if (WIN && !final) {  // the slot's next volume enters
+                    s.gbin[b] = ng;
+                    s.fill[b] = 0;
+                    s.cur[b] = ng != kNoBin ? a.B.fill[(uint64_t)ng * a.B.nblocks + blockIdx.x] : 0u;
                 }
+            } else {
+                s.cur[b] = rp + cnt;
+                s.fill[b] = (w - (cnt << 16)) & (0xFFFF0000u | rmask);
             }
         }
     }
@@ -429,7 +507,7 @@ __device__ __forceinline__ void stage_queue(const uint64_t *q, uint32_t cnt, con
     const uint32_t lane = threadIdx.x & 31;
     if (lane < cnt) {
         const uint64_t v = q[lane];
-        stage_cell<T>(BATCH ? unpack_cell_batch(v) : unpack_cell(v), d, a, s, C);
+        stage_cell<T, BATCH>(BATCH ? unpack_cell_batch(v) : unpack_cell(v), d, a, s, C);
     }
 }
 
@@ -444,20 +522,33 @@ __global__ void __launch_bounds__(kScatterThreads, 1)
     k_bin_scatter(const float *__restrict__ xyz, const SketchDesc d, const ScatterArgs a,
                   uint32_t *__restrict__ C) {
     constexpr bool BATCH = MODE == kModeBatch;
-    constexpr bool PACKED = MODE == kModePlainPacked || MODE == kModeSuperPacked;
+    constexpr bool PACKED = MODE == kModePlainPacked || MODE == kModeSuperPacked ||
+                            MODE == kModeCells || MODE == kModeSuperCells;
     extern __shared__ __align__(16) unsigned char smem[];
-    const SmemLayout Ly = smem_layout(a.nbins, a.slot, a.B.ngroups, SAMPLED ? 1u : 0u);
+    const SmemLayout Ly = smem_layout(a.nbins, a.slot, a.B.ngroups, SAMPLED ? 1u : 0u, BATCH);
     Smem s;
     s.fill = reinterpret_cast<uint32_t *>(smem + Ly.fill);
     s.cur = reinterpret_cast<uint32_t *>(smem + Ly.cur);
     s.gbase = reinterpret_cast<uint64_t *>(smem + Ly.gbase);
     s.gcap = reinterpret_cast<uint32_t *>(smem + Ly.gcap);
+    s.gbin = reinterpret_cast<uint32_t *>(smem + Ly.gbin);
     s.ring = reinterpret_cast<uint16_t *>(smem + Ly.ring);
     s.queue = reinterpret_cast<uint64_t *>(smem + Ly.queue);
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t per_tile = (uint64_t)blockDim.x * kPPT;
+    uint64_t n = a.n;                          // elements this launch takes
+    if (a.n_dev) {
+        const uint64_t total = *a.n_dev;
+        n = total > a.n_base ? min(a.n, total - a.n_base) : 0;
+    }
+    const uint64_t ntiles = (n + per_tile - 1) / per_tile;
+    // batch window: starts at the first volume of the block's first tile
+    uint32_t w0 = BATCH && blockIdx.x < ntiles ? (a.tvols[blockIdx.x] & 0xFFFFu) : 0u;
     for (uint32_t b = threadIdx.x; b < a.nbins; b += blockDim.x) {
+        const uint32_t gb = BATCH ? window_gbin(a, w0, b) : b + a.bin_base;
+        if (BATCH) s.gbin[b] = gb;
         s.fill[b] = 0;
-        s.cur[b] = a.B.fill[(uint64_t)(b + a.bin_base) * a.B.nblocks + blockIdx.x];
+        s.cur[b] = gb != kNoBin ? a.B.fill[(uint64_t)gb * a.B.nblocks + blockIdx.x] : 0u;
     }
     for (uint32_t g = threadIdx.x; g < a.B.ngroups; g += blockDim.x) {
         s.gbase[g] = a.B.gbase[g];
@@ -466,9 +557,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1)
     __syncthreads();
 
     const float Gf = (float)d.Gq;
-    const uint64_t per_tile = (uint64_t)blockDim.x * kPPT;
-    const uint64_t ntiles = (a.n + per_tile - 1) / per_tile;
-    const uint64_t full_groups = a.n / kPPT;
+    const uint64_t full_groups = n / kPPT;
     const float4 *p4 = reinterpret_cast<const float4 *>(xyz);
     const uint4 *r4 = reinterpret_cast<const uint4 *>(xyz);
     const unsigned long long *rec = reinterpret_cast<const unsigned long long *>(xyz);
@@ -517,7 +606,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1)
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) {
                         const uint64_t i = kPPT * g4 + j;
-                        ok[j] = i < a.n && prep_record<MODE, SAMPLED, true>(full ? p[j] : __ldcs(rec + i),
+                        ok[j] = i < n && prep_record<MODE, SAMPLED, true>(full ? p[j] : __ldcs(rec + i),
                                                                             a.g0 + i, d, a, c[j]);
                     }
                 }
@@ -531,18 +620,35 @@ __global__ void __launch_bounds__(kScatterThreads, 1)
                 }
                 const float px[kPPT] = {u.x, u.w, v.z, w.y}, py[kPPT] = {u.y, v.x, v.w, w.z},
                             pz[kPPT] = {u.z, v.y, w.x, w.w};
-                if (BATCH) {   // the volume of this warp's first particle, then upward per lane
-                    uint32_t v0 = 0;
-                    const uint64_t i0 = (tile * blockDim.x + (warp << 5)) * kPPT;
-                    if (lane == 0) v0 = vol_of(a, i0 < a.n ? i0 : a.n - 1);
-                    uint32_t vh = __shfl_sync(0xFFFFFFFFu, v0, 0);
+                const uint32_t tv = BATCH ? a.tvols[tile] : 0u;
+                if (BATCH && (tv >> 16) == (tv & 0xFFFFu) && (tv & 0xFFFFu) - w0 < a.wvols) {
+                    // the whole tile in one volume of the window (block-uniform)
+                    const uint32_t v = tv & 0xFFFFu;
+                    const VolumeDesc &V = a.vols[v];
+                    const uint64_t vg = V.g0 - V.start, pbase = V.probe_base;
+                    const float inv = V.inv_cell;
+                    const uint32_t G = V.G, bin0 = (v & (a.wvols - 1)) * a.bpv;
+                    uint64_t *probe_v = a.probe ? a.probe + (uint64_t)v * a.probe_per_vol : nullptr;
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) {
                         const uint64_t i = kPPT * g4 + j;
-                        ok[j] = i < a.n &&
-                                (full ? prep_particle_batch<SAMPLED>(px[j], py[j], pz[j], i, a, vh, c[j])
+                        ok[j] = i < n &&
+                                (full ? prep_particle_vol<SAMPLED>(px[j], py[j], pz[j], i, vg, inv, G, bin0,
+                                                                   probe_v, pbase, a, c[j])
+                                      : prep_particle_vol<SAMPLED>(__ldcs(xyz + 3 * i), __ldcs(xyz + 3 * i + 1),
+                                                                   __ldcs(xyz + 3 * i + 2), i, vg, inv, G, bin0,
+                                                                   probe_v, pbase, a, c[j]));
+                    }
+                } else if (BATCH) {   // from the tile's first volume upward per lane
+                    uint32_t vh = tv & 0xFFFFu;
+#pragma unroll
+                    for (int j = 0; j < kPPT; ++j) {
+                        const uint64_t i = kPPT * g4 + j;
+                        ok[j] = i < n &&
+                                (full ? prep_particle_batch<SAMPLED>(px[j], py[j], pz[j], i, d, a, w0, vh, c[j], C)
                                       : prep_particle_batch<SAMPLED>(__ldcs(xyz + 3 * i), __ldcs(xyz + 3 * i + 1),
-                                                                     __ldcs(xyz + 3 * i + 2), i, a, vh, c[j]));
+                                                                     __ldcs(xyz + 3 * i + 2), i, d, a, w0, vh,
+                                                                     c[j], C));
                     }
                 } else if (full && !probe_tile) {
                     const uint64_t g = a.g0 + kPPT * g4;
@@ -553,7 +659,7 @@ __global__ void __launch_bounds__(kScatterThreads, 1)
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) {
                         const uint64_t i = kPPT * g4 + j;
-                        ok[j] = i < a.n &&
+                        ok[j] = i < n &&
                                 (full ? prep_particle<MODE, SAMPLED, true>(px[j], py[j], pz[j], a.g0 + i, Gf, d, a, c[j])
                                       : prep_particle<MODE, SAMPLED, true>(__ldcs(xyz + 3 * i), __ldcs(xyz + 3 * i + 1),
                                                                            __ldcs(xyz + 3 * i + 2), a.g0 + i, Gf, d, a,
@@ -566,11 +672,11 @@ __global__ void __launch_bounds__(kScatterThreads, 1)
                 // tail): stage straight from registers
                 if (__all_sync(0xFFFFFFFFu, ok[0] & ok[1] & ok[2] & ok[3])) {
 #pragma unroll
-                    for (int j = 0; j < kPPT; ++j) stage_cell<T>(c[j], d, a, s, C);
+                    for (int j = 0; j < kPPT; ++j) stage_cell<T, BATCH>(c[j], d, a, s, C);
                 } else {
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j)
-                        if (ok[j]) stage_cell<T>(c[j], d, a, s, C);
+                        if (ok[j]) stage_cell<T, BATCH>(c[j], d, a, s, C);
                 }
             } else {
                 // kept cells go through the warp's queue, 32 at a time, so the
@@ -597,17 +703,30 @@ __global__ void __launch_bounds__(kScatterThreads, 1)
             nq = 0;
             __syncwarp();
         }
+        // a batch window moves to the next period's first volume when that
+        // period's volumes do not all fall in it (one tile a period then)
+        if (BATCH && threadIdx.x == 0) {
+            uint32_t nw = w0;
+            if (tile < ntiles) {
+                const uint32_t tv = a.tvols[tile];
+                if ((tv & 0xFFFFu) - w0 >= a.wvols || (tv >> 16) - w0 >= a.wvols) nw = tv & 0xFFFFu;
+            }
+            s.gbin[a.nbins] = nw;
+        }
         __syncthreads();
-        flush_phase(false, a, s, C);
+        const uint32_t nw = BATCH ? s.gbin[a.nbins] : 0u;
+        flush_phase<BATCH>(false, nw, a, s, C);
+        w0 = nw;
         __syncthreads();
     }
     // every bin now holds fewer than `half` staged codes: write the partial
     // half, padded with cancelling pairs, and leave the region fill in global
-    flush_phase(true, a, s, C);
+    flush_phase<BATCH>(true, 0u, a, s, C);
 }
 
 // Launch one variant (the caller filled `a`; smem from smem_layout).
-template <int MODE>
+// SAMPLING: instantiate the sampled variants too (cell records never sample).
+template <int MODE, bool SAMPLING = true>
 cudaError_t launch_mode(const float *xyz, const SketchDesc &d, const ScatterArgs &a, bool sampled,
                         size_t smem, uint32_t *C, cudaStream_t s) {
     const bool vec = (reinterpret_cast<uintptr_t>(xyz) & 15u) == 0;
@@ -620,11 +739,18 @@ cudaError_t launch_mode(const float *xyz, const SketchDesc &d, const ScatterArgs
     // five rows in one pass (every configuration here but the largest
     // sketches) get a fully unrolled variant; row passes and an unaligned
     // buffer (a slice of a larger one) the generic one
-    if (a.nrows == 5 && a.row0 == 0 && vec)
-        return sampled ? launch(k_bin_scatter<5, true, MODE, true>) : launch(k_bin_scatter<5, true, MODE, false>);
-    if (vec)
-        return sampled ? launch(k_bin_scatter<0, true, MODE, true>) : launch(k_bin_scatter<0, true, MODE, false>);
-    return sampled ? launch(k_bin_scatter<0, false, MODE, true>) : launch(k_bin_scatter<0, false, MODE, false>);
+    if constexpr (SAMPLING) {
+        if (sampled) {
+            if (a.nrows == 5 && a.row0 == 0 && vec) return launch(k_bin_scatter<5, true, MODE, true>);
+            if (vec) return launch(k_bin_scatter<0, true, MODE, true>);
+            return launch(k_bin_scatter<0, false, MODE, true>);
+        }
+    } else if (sampled) {
+        return cudaErrorInvalidValue;
+    }
+    if (a.nrows == 5 && a.row0 == 0 && vec) return launch(k_bin_scatter<5, true, MODE, false>);
+    if (vec) return launch(k_bin_scatter<0, true, MODE, false>);
+    return launch(k_bin_scatter<0, false, MODE, false>);
 }
 
 // launchers of the variants, one translation unit each group of modes
@@ -633,6 +759,8 @@ cudaError_t launch_modes_sketch(int mode, const float *xyz, const SketchDesc &d,
 cudaError_t launch_modes_batch_route(int mode, const float *xyz, const SketchDesc &d,
                                      const ScatterArgs &a, bool sampled, size_t smem, uint32_t *C,
                                      cudaStream_t s);
+cudaError_t launch_modes_cells(int mode, const float *xyz, const SketchDesc &d, const ScatterArgs &a,
+                               size_t smem, uint32_t *C, cudaStream_t s);
 
 }  // namespace binned
 }  // namespace hs

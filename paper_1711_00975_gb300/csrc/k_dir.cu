@@ -25,15 +25,6 @@ namespace hs {
 
 namespace {
 
-__device__ __forceinline__ uint64_t line_value(const RowSeed &s, uint32_t cy, uint32_t cz) {
-    return s.b + mul_lo64(s.a1, cy) + mul_lo64(s.a2, cz);
-}
-
-__device__ __forceinline__ bool exact_hot(const uint32_t *__restrict__ bits, uint64_t words_per_row,
-                                          int r, uint32_t bucket) {
-    return (__ldg(bits + (uint64_t)r * words_per_row + (bucket >> 5)) >> (bucket & 31)) & 1u;
-}
-
 __global__ void k_dir_count(const SketchDesc d, int r, uint32_t D, uint32_t *__restrict__ cnt) {
     const uint64_t lines = (uint64_t)d.G * d.G;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;

@@ -136,6 +136,91 @@ __global__ void __launch_bounds__(256) k_pack(const float *__restrict__ xyz, uin
     }
 }
 
+// A probe entry of the compaction pass: the key of the particle's cell on
+// the probe's mesh (the F^3 block holding it when F > 1), or kInvalidKey.
+__device__ __forceinline__ void compact_probe(const CompactProbe &p, uint64_t g, bool valid,
+                                              uint32_t cx, uint32_t cy, uint32_t cz) {
+    if (!p.probe || g - p.base >= p.end - p.base) return;
+    uint64_t key = kInvalidKey;
+    if (valid) {
+        if (p.F > 1) {
+            cx = __umulhi(cx, p.fmagic);
+            cy = __umulhi(cy, p.fmagic);
+            cz = __umulhi(cz, p.fmagic);
+        }
+        key = key_of(cx, cy, cz, p.G);
+    }
+    p.probe[g - p.base] = key;
+}
+
+// Sample and quantise every particle once; append the cells of the kept,
+// valid ones.  The sampling decision and the cell are the ones the float32
+// path takes (splitmix64 of the global index against the same threshold;
+// axis_cell on the fine mesh).  A thread takes four particles (three float4
+// when the buffer is 16-byte aligned, which page-locked host memory read over
+// the host link wants); a warp reserves its records with one atomic.
+__device__ __forceinline__ bool compact_one(float x, float y, float z, uint64_t g,
+                                            const SketchDesc &d, uint64_t thr, int keep_all,
+                                            uint64_t seed, const CompactProbe &p0,
+                                            const CompactProbe &p1, uint64_t &rec) {
+    uint32_t cx = 0, cy = 0, cz = 0;
+    const bool valid = particle_cell(d, x, y, z, cx, cy, cz);
+    compact_probe(p0, g, valid, cx, cy, cz);
+    compact_probe(p1, g, valid, cx, cy, cz);
+    rec = (uint64_t)cx | ((uint64_t)cy << kPackBits) | ((uint64_t)cz << (2 * kPackBits));
+    return valid && (keep_all || splitmix64_at(seed, g) < thr);
+}
+
+__global__ void __launch_bounds__(256) k_compact(const float *__restrict__ xyz, uint64_t n,
+                                                 uint64_t g0, const SketchDesc d, uint64_t thr,
+                                                 int keep_all, int vec, uint64_t seed,
+                                                 const CompactProbe p0, const CompactProbe p1,
+                                                 uint64_t *__restrict__ cells,
+                                                 unsigned long long *__restrict__ count) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t groups = (n + 3) / 4, full = vec ? n / 4 : 0;
+    const float4 *p4 = reinterpret_cast<const float4 *>(xyz);
+    for (uint64_t base = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5; base < groups;
+         base += warps << 5) {                                   // warp-uniform
+        const uint64_t q = base + lane;
+        uint64_t rec[4] = {0, 0, 0, 0};
+        uint32_t keep = 0;
+        if (q < full) {
+            const float4 u = __ldcs(p4 + 3 * q), v = __ldcs(p4 + 3 * q + 1), w = __ldcs(p4 + 3 * q + 2);
+            const float px[4] = {u.x, u.w, v.z, w.y}, py[4] = {u.y, v.x, v.w, w.z},
+                        pz[4] = {u.z, v.y, w.x, w.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                keep |= (uint32_t)compact_one(px[j], py[j], pz[j], g0 + 4 * q + j, d, thr, keep_all,
+                                              seed, p0, p1, rec[j]) << j;
+        } else if (q < groups) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint64_t i = 4 * q + j;
+                if (i < n)
+                    keep |= (uint32_t)compact_one(__ldcs(xyz + 3 * i), __ldcs(xyz + 3 * i + 1),
+                                                  __ldcs(xyz + 3 * i + 2), g0 + i, d, thr, keep_all,
+                                                  seed, p0, p1, rec[j]) << j;
+            }
+        }
+        const uint32_t c = __popc(keep);
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
+        }
+        const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        unsigned long long at = 0;
+        if (lane == 0 && total) at = atomicAdd(count, (unsigned long long)total);
+        at = __shfl_sync(0xFFFFFFFFu, at, 0) + (incl - c);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (keep & (1u << j)) cells[at++] = rec[j];
+    }
+}
+
 // Random fire-and-forget adds into an n_counters table (power of two): the
 // L2 reduction rate that bounds the update when the particle stream does not.
 __global__ void __launch_bounds__(256) k_red_rate(uint32_t *__restrict__ T, uint64_t mask,
@@ -228,6 +313,21 @@ cudaError_t launch_pack(const float *xyz, uint64_t n, double box, uint64_t *out,
     if (n == 0) return cudaSuccess;
     uint64_t blocks = std::min<uint64_t>((n + 255) / 256, 16384);
     k_pack<<<(unsigned)blocks, 256, 0, s>>>(xyz, n, (float)((double)(1u << kPackBits) / box), out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact_cells(const float *xyz, uint64_t n, uint64_t g0, const SketchDesc &d,
+                                 double rate, uint64_t sample_seed, const CompactProbe &p0,
+                                 const CompactProbe &p1, uint64_t *cells,
+                                 unsigned long long *count, int blocks, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    if (d.F != 1 || d.Gq >= (1u << kPackBits)) return cudaErrorInvalidValue;
+    const bool sampled = rate < 1.0;
+    const uint64_t thr = sampled ? (uint64_t)ldexp(rate, 64) : 0;
+    const uint64_t want = ((n + 3) / 4 + 255) / 256;
+    const int vec = (reinterpret_cast<uintptr_t>(xyz) & 15u) == 0;
+    k_compact<<<(unsigned)std::min<uint64_t>(want, (uint64_t)blocks), 256, 0, s>>>(
+        xyz, n, g0, d, thr, sampled ? 0 : 1, vec, sample_seed, p0, p1, cells, count);
     return cudaGetLastError();
 }
 

@@ -59,7 +59,8 @@ class hs_stats(ctypes.Structure):
                 ("topk_calls", ctypes.c_uint64), ("last_candidates", ctypes.c_uint64),
                 ("last_threshold", ctypes.c_int32), ("last_passes", ctypes.c_uint32),
                 ("flush_launches", ctypes.c_uint64), ("flush_ms", ctypes.c_double),
-                ("h2d_bytes", ctypes.c_uint64), ("h2d_ms", ctypes.c_double)]
+                ("h2d_bytes", ctypes.c_uint64), ("h2d_ms", ctypes.c_double),
+                ("host_path_volumes", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
