@@ -59,6 +59,10 @@ def parse():
                     help="100 Mpc/h training boxes of the learned router (seeds 1000..)")
     ap.add_argument("--second-rate", type=float, default=0.1,
                     help="also time this sample rate (0 to skip)")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the sub-volume batch leg and print its record (profiling)")
+    ap.add_argument("--batch-particles", type=float, default=3e8,
+                    help="particles of the batch leg, over its 64 sub-volumes")
     return ap.parse_args()
 
 
@@ -186,15 +190,15 @@ def cpu_sample_rates(xyz_host: np.ndarray, n_update: int, n_cells: int, k: int, 
     return n_update / (t1 - t0), n_cells / (t2 - t1), cores, t2 - t0
 
 
-def run_batched(steps: int, warmup: int):
-    """64 sub-volumes of uneven size (2^16..2^26 particles, about 3e8 in all),
-    each with its own 5 x 2^18 sketch and top-500, updated as one batch."""
+def run_batched(steps: int, warmup: int, total: float = 3e8):
+    """64 sub-volumes of uneven size (2^16..2^26 particles, about `total` in
+    all), each with its own 5 x 2^18 sketch and top-500, updated as one batch."""
     import torch
 
     import synth
     from paper_1711_00975_gb300 import halosketch as hs
 
-    specs = synth.subvolume_specs(seed=3)
+    specs = synth.subvolume_specs(seed=3, target_total=total)
     counts = [s.n for s in specs]
     offsets = np.concatenate([[0], np.cumsum(counts)]).astype(np.uint64)
     total = int(offsets[-1])
@@ -905,7 +909,7 @@ def run_ours(args):
     if not args.no_batch and world == 1:
         del dev
         torch.cuda.empty_cache()
-        batched = run_batched(max(3, args.steps // 2), args.warmup)
+        batched = run_batched(max(3, args.steps // 2), args.warmup, args.batch_particles)
 
     cpu = None
     if not args.no_cpu and world == 1:
@@ -948,6 +952,9 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.batch_only:
+        print(json.dumps(run_batched(max(3, args.steps), args.warmup, args.batch_particles)))
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

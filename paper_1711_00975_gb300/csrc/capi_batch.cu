@@ -13,9 +13,6 @@
 namespace {
 
 constexpr uint64_t kBatchProbe = 1ull << 16;   // probe keys per volume
-// bins of 2^13 counters: 32 a row of a 2^18-counter volume, so a warp's
-// reservations in one row rarely share a ring (fewer shared-atomic conflicts)
-constexpr uint32_t kBatchMaxS = 13;
 
 }  // namespace
 
@@ -204,7 +201,7 @@ hs_status batch_create(const hs_params *params, uint32_t n_volumes, const double
     b->d.Gq = b->d.G;
     b->d.F = 1;
     // every bin is numbered (16 bits); rings are kept for a window of volumes
-    b->bl = bin_layout(batch_flat_desc(b), kBinSmemBudget, false, kBatchMaxS);
+    b->bl = bin_layout(batch_flat_desc(b), kBinSmemBudget, false);
     const BatchRing ring = batch_ring(b->bl, b->d, n_volumes, 1.0, 0);
     b->bl.slot = ring.slot;
     b->bl.half = ring.slot / 2;
@@ -627,6 +624,7 @@ static hs_status batch_topk_device(hs_batch *b, uint32_t k, uint32_t F, uint64_t
         V.kk = (uint32_t)std::min<uint64_t>(k, cells);
         V.use = 1;
         V.D = b->tk.D[v];
+        V.gmagic = div_magic(b->G[v]);   // items below 2^16 G and cells below 2^34: x < 2^48 / G
     }
     HS_CUDA(cudaEventRecord(b->tk.ev_a, b->stream));
     HS_CUDA(cudaGraphLaunch(b->tk.gexec, b->stream));

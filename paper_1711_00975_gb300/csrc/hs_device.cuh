@@ -48,6 +48,20 @@ __host__ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64
     return z ^ (z >> 31);
 }
 
+// Division by an invariant G with one high multiply (the multiply-and-shift
+// method of Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994).  With M = ceil(2^48 / G) = (2^48 + e) / G,
+// 0 <= e < G, x M / 2^48 = x / G + x e / (G 2^48); writing x = q G + r the
+// fraction r / G + x e / (G 2^48) stays below 1 when x e < 2^48, so
+// floor(x M / 2^48) = q for every x < 2^48 / G.  div_magic(G) = M << 16 (G >= 2,
+// so it fits 64 bits); 0 asks for a plain division.
+__host__ __device__ inline uint64_t div_magic(uint32_t G) {
+    return G >= 2 ? (((1ull << 48) + G - 1) / G) << 16 : 0ull;
+}
+__device__ __forceinline__ uint64_t div_invariant(uint64_t x, uint32_t G, uint64_t magic) {
+    return magic ? __umul64hi(x, magic) : x / G;
+}
+
 // Low 64 bits of a * x for a 64-bit a and 32-bit x: one wide and one narrow
 // integer multiply-add instead of a full 64x64 product.
 __device__ __forceinline__ uint64_t mul_lo64(uint64_t a, uint32_t x) {

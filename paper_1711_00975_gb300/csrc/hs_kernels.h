@@ -260,6 +260,7 @@ struct BatchTopkVol {     // one volume's query, filled by the host before each 
     uint32_t use;         // 0: the host's general path answers this volume
     uint32_t D;           // its directories have 2^D slots (D >= log2 W: a
                           // bucket's lines are the records of a run of slots)
+    uint64_t gmagic;      // div_magic(G): x / G as one high multiply
 };
 struct BatchTopkBufs {    // device buffers; per-volume arrays are volume-major
     const BatchTopkVol *vol;

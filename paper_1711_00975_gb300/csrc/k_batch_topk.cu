@@ -286,102 +286,87 @@ __device__ __forceinline__ void bt_candidate(const int32_t *__restrict__ Cv, con
     }
 }
 
-// A block takes a contiguous share of the work items (ordered by volume,
-// row, hot bucket, column), volume by volume; SB: the volume's hot bitmap
-// (rows x W bits) is first copied to shared memory, so the row checks of a
-// line read shared memory.
-template <int T, bool SB>
-__global__ void __launch_bounds__(1024, 1)
+template <int T>
+__global__ void __launch_bounds__(256, 6)   // 42 registers: 6 blocks an SM (measured faster than 4)
     k_bt_query(const int32_t *__restrict__ C, const SketchDesc d, BatchTopkBufs b) {
-    extern __shared__ uint32_t sbits[];
     const uint32_t n = b.nvol * b.F;
     const uint64_t total = b.pre[n];
     const uint32_t rows = T > 0 ? (uint32_t)T : d.rows;
     const uint32_t need = rows - (rows - 1) / 2;
     const uint64_t wpr = d.W >> 5;
     const uint32_t s = 64 - d.log2w;
-    const uint64_t share = (total + gridDim.x - 1) / gridDim.x;
-    const uint64_t q_begin = (uint64_t)blockIdx.x * share < total ? (uint64_t)blockIdx.x * share : total;
-    const uint64_t q_end = q_begin + share < total ? q_begin + share : total;
-    if (q_begin >= q_end) return;
-    uint32_t v = 0;   // the volume of the first item: the last v with pre[v F] <= q_begin
-    {
-        uint32_t lo = 0, hi = b.nvol;
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (b.pre[mid * b.F] <= q_begin) lo = mid; else hi = mid;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t q0 = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5; q0 < total;
+         q0 += warps << 5) {                                      // warp-uniform
+        // the pair holding the warp's first item (the last j with pre[j] <= q0),
+        // then upward per lane
+        uint32_t j = 0;
+        if (lane == 0) {
+            uint32_t lo = 0, hi = n;
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (__ldg(b.pre + mid) <= q0) lo = mid; else hi = mid;
+            }
+            j = lo;
         }
-        v = lo;
-    }
-    for (; v < b.nvol; ++v) {                                   // block-uniform
-        const uint64_t va = b.pre[v * b.F];
-        if (va >= q_end) break;
-        const uint64_t vb = b.pre[(v + 1) * b.F];
-        const uint64_t qa = va > q_begin ? va : q_begin, qb = vb < q_end ? vb : q_end;
-        if (qa >= qb) continue;
-        const uint32_t G = b.vol[v].G, D = b.vol[v].D;
-        const int32_t theta = b.theta[v];
-        const bool scan = b.scan[v] != 0;
+        j = __shfl_sync(0xFFFFFFFFu, j, 0);
+        const uint64_t q = q0 + lane;
+        if (q >= total) continue;
+        while (j + 1 < n && __ldg(b.pre + j + 1) <= q) ++j;
+        const uint32_t v = j / b.F;
+        const int r = (int)(j - v * b.F);
+        const uint32_t G = b.vol[v].G;
+        const uint64_t gm = b.vol[v].gmagic;
+        const uint64_t local = q - __ldg(b.pre + j);
         const int32_t *Cv = C + (uint64_t)v * d.rows * d.W;
         const uint32_t *bits = b.bits + (uint64_t)v * d.rows * wpr;
-        if (SB) {
-            __syncthreads();                                     // the last volume's lookups are done
-            for (uint32_t i = threadIdx.x; i < rows * wpr; i += blockDim.x) sbits[i] = __ldcs(bits + i);
-            __syncthreads();
-            bits = sbits;
+        const int32_t theta = b.theta[v];
+        if (b.scan[v]) {                     // one cell of a scanned volume
+            const uint64_t rest = div_invariant(local, G, gm), cz = div_invariant(rest, G, gm);
+            const uint32_t cx = (uint32_t)(local - rest * G), cy = (uint32_t)(rest - cz * G);
+            uint32_t nhot = 0, left = rows;
+            bool skip = false;
+            for (uint32_t rr = 0; rr < rows; ++rr) {
+                const uint64_t val = row_value(d.seed[rr], cx, cy, cz);
+                nhot += exact_hot(bits, wpr, (int)rr, bucket_of(val, d.log2w));
+                if (nhot + --left < need) { skip = true; break; }
+            }
+            if (!skip) bt_candidate<T>(Cv, d, rows, v, G, theta, cx, cy, cz, b);
+            continue;
         }
-        for (uint64_t q = qa + threadIdx.x; q < qb; q += blockDim.x) {
-            uint32_t r = 0;                                      // the row of item q
-            while (r + 1 < b.F && b.pre[v * b.F + r + 1] <= q) ++r;
-            const uint64_t local = q - b.pre[v * b.F + r];
-            if (scan) {                                          // one cell of a scanned volume
-                const uint32_t cx = (uint32_t)(local % G);
-                const uint64_t rest = local / G;
-                const uint32_t cy = (uint32_t)(rest % G), cz = (uint32_t)(rest / G);
-                uint32_t nhot = 0, left = rows;
+        const uint64_t hi = div_invariant(local, G, gm);      // local = hi G + cx
+        const uint32_t h = __ldg(b.hot + (uint64_t)j * b.hot_cap + hi);
+        const uint32_t cx = (uint32_t)(local - hi * G);
+        const uint32_t *off = b.dir_off[j];
+        const DirRecord *rec = b.dir_rec[j];
+        const uint32_t D = b.vol[v].D;
+        const uint64_t Tx = d.seed[r].a0 * (uint64_t)cx;
+        // lines with L in [h 2^s - Tx, (h+1) 2^s - Tx): the records of slots
+        // a .. z (cyclic), contiguous in the counting-sorted array
+        const uint64_t lo = ((uint64_t)h << s) - Tx;
+        const uint64_t a = lo >> (64 - D), z = (lo + ((1ull << s) - 1)) >> (64 - D);
+        const uint32_t ea = __ldg(off + a), ez = __ldg(off + z + 1);
+        const uint32_t eend = a <= z ? ez : __ldg(off + (1ull << D));
+        for (int part = 0; part < (a <= z ? 1 : 2); ++part) {
+            const uint32_t e0 = part ? 0u : ea, e1 = part ? ez : eend;
+#pragma unroll 4
+            for (uint32_t e = e0; e < e1; ++e) {
+                const DirRecord p = __ldg(rec + e);
+                const uint32_t cy = p & 0xFFFFu, cz = p >> 16;
+                if (((line_value(d.seed[r], cy, cz) + Tx) >> s) != h) continue;
+                // the rows before r cold, at least `need` rows hot
+                uint32_t nhot = 1, left = rows - 1;
                 bool skip = false;
                 for (uint32_t rr = 0; rr < rows; ++rr) {
+                    if ((int)rr == r) continue;
                     const uint64_t val = row_value(d.seed[rr], cx, cy, cz);
-                    const uint32_t bk = bucket_of(val, d.log2w);
-                    nhot += (bits[rr * wpr + (bk >> 5)] >> (bk & 31)) & 1u;
+                    const bool hh = exact_hot(bits, wpr, (int)rr, bucket_of(val, d.log2w));
+                    if ((int)rr < r && hh) { skip = true; break; }
+                    nhot += hh;
                     if (nhot + --left < need) { skip = true; break; }
                 }
                 if (!skip) bt_candidate<T>(Cv, d, rows, v, G, theta, cx, cy, cz, b);
-                continue;
-            }
-            const uint32_t j = v * b.F + r;
-            const uint32_t h = __ldg(b.hot + (uint64_t)j * b.hot_cap + local / G);
-            const uint32_t cx = (uint32_t)(local % G);
-            const uint32_t *off = b.dir_off[j];
-            const DirRecord *rec = b.dir_rec[j];
-            const uint64_t Tx = d.seed[r].a0 * (uint64_t)cx;
-            // lines with L in [h 2^s - Tx, (h+1) 2^s - Tx): the records of slots
-            // a .. z (cyclic), contiguous in the counting-sorted array
-            const uint64_t lo = ((uint64_t)h << s) - Tx;
-            const uint64_t a = lo >> (64 - D), z = (lo + ((1ull << s) - 1)) >> (64 - D);
-            const uint32_t ea = __ldg(off + a), ez = __ldg(off + z + 1);
-            const uint32_t eend = a <= z ? ez : __ldg(off + (1ull << D));
-            for (int part = 0; part < (a <= z ? 1 : 2); ++part) {
-                const uint32_t e0 = part ? 0u : ea, e1 = part ? ez : eend;
-#pragma unroll 4
-                for (uint32_t e = e0; e < e1; ++e) {
-                    const DirRecord p = __ldg(rec + e);
-                    const uint32_t cy = p & 0xFFFFu, cz = p >> 16;
-                    if (((line_value(d.seed[r], cy, cz) + Tx) >> s) != h) continue;
-                    // the rows before r cold, at least `need` rows hot
-                    uint32_t nhot = 1, left = rows - 1;
-                    bool skip = false;
-                    for (uint32_t rr = 0; rr < rows; ++rr) {
-                        if (rr == r) continue;
-                        const uint64_t val = row_value(d.seed[rr], cx, cy, cz);
-                        const uint32_t bk = bucket_of(val, d.log2w);
-                        const bool hh = (bits[rr * wpr + (bk >> 5)] >> (bk & 31)) & 1u;
-                        if (rr < r && hh) { skip = true; break; }
-                        nhot += hh;
-                        if (nhot + --left < need) { skip = true; break; }
-                    }
-                    if (!skip) bt_candidate<T>(Cv, d, rows, v, G, theta, cx, cy, cz, b);
-                }
             }
         }
     }
@@ -546,18 +531,8 @@ cudaError_t launch_batch_topk(const int32_t *C, const SketchDesc &d, const Batch
     const uint64_t hwords = (uint64_t)b.nvol * b.F * (d.W >> 5);
     k_bt_hot<<<(unsigned)std::min<uint64_t>((hwords + 255) / 256, (uint64_t)num_sms * 8), 256, 0, s>>>(d, b, hwords);
     k_bt_prefix<<<1, 1024, 0, s>>>(b, d.log2w);
-    // the hot bitmap of a volume in shared memory when it fits
-    const size_t sbytes = (size_t)d.rows * (d.W >> 5) * 4;
-    auto query = [&](auto kern, size_t smem) {
-        cudaError_t err = smem ? ensure_smem_limit(kern, smem) : cudaSuccess;
-        if (err == cudaSuccess) kern<<<num_sms, 1024, smem, s>>>(C, d, b);
-        return err;
-    };
-    if (sbytes <= 200 * 1024)
-        e = d.rows == 5 ? query(k_bt_query<5, true>, sbytes) : query(k_bt_query<0, true>, sbytes);
-    else
-        e = d.rows == 5 ? query(k_bt_query<5, false>, 0) : query(k_bt_query<0, false>, 0);
-    if (e != cudaSuccess) return e;
+    if (d.rows == 5) k_bt_query<5><<<num_sms * 16, 256, 0, s>>>(C, d, b);
+    else k_bt_query<0><<<num_sms * 16, 256, 0, s>>>(C, d, b);
     const size_t smem = batch_topk_final_smem(b.k);
     if ((e = ensure_smem_limit(k_bt_final, smem)) != cudaSuccess) return e;
     k_bt_final<<<b.nvol, 1024, smem, s>>>(b, (uint32_t)(smem / 12));

@@ -469,6 +469,27 @@ __device__ __forceinline__ void flush_phase(bool final, uint32_t nw, const Scatt
     const uint32_t TS = a.team, per = 32 / TS;
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const uint32_t tl = lane & (TS - 1);
+    if (!WIN) {   // rings of fixed bins
+        for (uint32_t base = warp * per; base < a.nbins; base += nwarps * per) {
+            const uint32_t b = base + lane / TS;
+            if (b < a.nbins) {   // a team of 32 is the whole warp, so uniform when TS > 1
+                const uint32_t w = s.fill[b];
+                const uint32_t rp = s.cur[b];
+                const uint32_t gb = b + a.bin_base;
+                const uint32_t cnt = flush_bin(b, gb, w, rp, final, tl, TS, a, s, C);
+                if (TS > 1) __syncwarp();   // the team has read the words lane 0 rewrites
+                if (tl == 0) {
+                    if (final) {
+                        a.B.fill[(uint64_t)gb * a.B.nblocks + blockIdx.x] = rp + cnt;
+                    } else {
+                        s.cur[b] = rp + cnt;
+                        s.fill[b] = (w - (cnt << 16)) & (0xFFFF0000u | rmask);
+                    }
+                }
+            }
+        }
+        return;
+    }
     for (uint32_t base = warp * per; base < a.nbins; base += nwarps * per) {   // warp-uniform
         const uint32_t b = base + lane / TS;
         uint32_t w = 0, rp = 0, cnt = 0, gb = kNoBin, ng = kNoBin;

@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(256)
                 const uint32_t *__restrict__ offsets, const DirRecord *__restrict__ rec,
                 const uint4 *__restrict__ inl, const uint32_t *__restrict__ hot, uint64_t n_hot,
                 const uint32_t *__restrict__ bits, int32_t theta, uint32_t mode, uint64_t line_lo,
-                uint64_t line_hi, SearchOut out, RouteFilter skip) {
+                uint64_t line_hi, SearchOut out, RouteFilter skip, uint64_t gmagic) {
     const uint32_t rows = T > 0 ? (uint32_t)T : d.rows;
     const uint32_t need = rows - (rows - 1) / 2;
     const uint64_t words_per_row = d.W >> 5 ? d.W >> 5 : 1;
@@ -176,8 +176,9 @@ __global__ void __launch_bounds__(256)
     const uint64_t total = n_hot * d.G;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += stride) {
-        const uint32_t h = hot[q / d.G];
-        const uint32_t cx = (uint32_t)(q % d.G);
+        const uint64_t hi = div_invariant(q, d.G, gmagic);   // q = hi G + cx
+        const uint32_t h = hot[hi];
+        const uint32_t cx = (uint32_t)(q - hi * d.G);
         const uint64_t Tx = d.seed[r].a0 * (uint64_t)cx;
         const uint64_t lo = ((uint64_t)h << s) - Tx;
         const uint64_t slot0 = lo >> (64 - D);
@@ -286,16 +287,20 @@ cudaError_t launch_dir_query(const int32_t *C, const SketchDesc &d, int r, uint3
     if (total == 0) return cudaSuccess;
     uint64_t blocks = (total + 255) / 256;
     if (blocks > (uint64_t)max_blocks) blocks = (uint64_t)max_blocks;
+    // the multiply form of q / G holds for q < 2^48 / G
+    const uint64_t gmagic = total < (1ull << 48) / d.G ? div_magic(d.G) : 0ull;
     if (d.rows == 5)
         k_dir_query<5><<<(unsigned)blocks, 256, 0, s>>>(C, d, r, D, offsets, rec,
                                                        inl ? dir_inline(offsets, D) : nullptr,
                                                        hot, n_hot, bits,
-                                                       theta, mode, line_lo, line_hi, out, skip);
+                                                       theta, mode, line_lo, line_hi, out, skip,
+                                                       gmagic);
     else
         k_dir_query<0><<<(unsigned)blocks, 256, 0, s>>>(C, d, r, D, offsets, rec,
                                                        inl ? dir_inline(offsets, D) : nullptr,
                                                        hot, n_hot, bits,
-                                                       theta, mode, line_lo, line_hi, out, skip);
+                                                       theta, mode, line_lo, line_hi, out, skip,
+                                                       gmagic);
     return cudaGetLastError();
 }
 
