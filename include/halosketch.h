@@ -305,9 +305,9 @@ typedef struct hs_batch hs_batch;
 
 /* Scatter configuration chosen by batch_autotune. */
 typedef struct {
-    uint32_t rounds;         /* tiles of 4096 particles staged between flushes    */
+    uint32_t rounds;         /* tiles of 3072 particles staged between flushes    */
     uint32_t slot;           /* shared-memory ring depth (codes per bin)          */
-    uint32_t configs_tried;
+    uint32_t configs_tried;  /* 0: the process's earlier choice for this shape    */
     float best_ms;           /* its time for the tuning data                      */
 } hs_tune;
 
@@ -325,9 +325,12 @@ hs_status batch_counters(hs_batch *b, uint32_t volume, int32_t *out);
 hs_status batch_reset(hs_batch *b);
 hs_status batch_volume_info(const hs_batch *b, uint32_t volume, hs_info *out);
 hs_status batch_stats(hs_batch *b, hs_stats *out, int reset);
-/* Time the scatter's block size and shared-memory ring depth on the given
- * particles and keep the fastest for later updates.  The tuning runs update the
- * sketches, so the batch is reset afterwards. */
+/* Time the scatter's shared-memory ring depth (the deepest that fits the ring
+ * window of volumes, a half and a quarter of it) on the given particles and
+ * keep the fastest for later updates.  The tuning runs update the sketches, so
+ * the batch is reset afterwards.  The choice is kept for the process, keyed by
+ * (device, log2_width, rows, sample_rate): a later call for the same shape
+ * applies it without running (configs_tried = 0) and leaves the batch as it is. */
 hs_status batch_autotune(hs_batch *b, const float *xyz, const uint64_t *offsets,
                          double sample_rate, hs_tune *out);
 hs_status batch_destroy(hs_batch *b);

@@ -1,6 +1,9 @@
 // capi_batch.cu - batches of independent sub-volumes (batch_* of the C ABI).
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <thread>
+#include <tuple>
 
 #include "capi_internal.h"
 
@@ -13,6 +16,15 @@
 namespace {
 
 constexpr uint64_t kBatchProbe = 1ull << 16;   // probe keys per volume
+
+// Ring depths chosen by batch_autotune, per (device, log2 W, rows, sample
+// rate), kept for the process so later batches of the same shape skip tuning.
+struct TuneChoice {
+    uint32_t slot;
+    float ms;
+};
+std::mutex g_tune_mu;
+std::map<std::tuple<int, uint32_t, uint32_t, double>, TuneChoice> g_tune_cache;
 
 }  // namespace
 
@@ -737,6 +749,21 @@ hs_status batch_autotune(hs_batch *b, const float *xyz, const uint64_t *offsets,
     st = batch_ensure_bins(b, offsets, sample_rate);
     if (st != HS_OK) return st;
     batch_drop_graph(b);
+    const auto key = std::make_tuple(b->device, b->d.log2w, b->d.rows, sample_rate);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {          // tuned before for this shape: no runs
+            b->slot = it->second.slot;
+            b->rounds = 1;
+            out->rounds = 1;
+            out->slot = it->second.slot ? it->second.slot
+                                        : batch_ring(b->bl, b->d, b->nvol, sample_rate, 0).slot;
+            out->configs_tried = 0;
+            out->best_ms = it->second.ms;
+            return HS_OK;
+        }
+    }
     // candidates: the ring depth that fits the window, a half and a quarter
     // of it (a shallower ring lets the window hold more volumes); one tile
     // is staged between flush phases
@@ -769,6 +796,10 @@ hs_status batch_autotune(hs_batch *b, const float *xyz, const uint64_t *offsets,
     }
     b->slot = best_slot;
     b->rounds = best_rounds;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = TuneChoice{best_slot, best};
+    }
     st = batch_reset(b);                              // tuning runs touched the counters
     if (st != HS_OK) return st;
     HS_CUDA(cudaStreamSynchronize(b->stream));

@@ -96,6 +96,16 @@ def test_batch_autotune_then_exact(hs):
         assert np.array_equal(b.counters(v), C)
     b.reset()
     assert not b.counters(2).any()
+    # a second batch of the same shape takes the kept choice without running
+    b2 = hs.Batch(5, 16, [s.box for s in specs], 0.1, hash_seed=11, sample_seed=2)
+    tune2 = b2.autotune(d, off, 0.5)
+    assert tune2["configs_tried"] == 0 and tune2["slot"] == tune["slot"]
+    b2.update(d, off, 0.5)
+    for v, spec in enumerate(specs):
+        p = oracle.Params(5, 16, spec.box, 0.1, 11, 2)
+        C = _oracle_counters(spec, xyz[off[v]:off[v + 1]], p, rate=0.5)
+        assert np.array_equal(b2.counters(v), C)
+    b2.close()
     b.close()
 
 
