@@ -485,19 +485,19 @@ static uint32_t scatter_passes(const hs_sketch *h) {
 }
 
 // The compaction pass pays when the binned updates of h (and of its
-// super-item sketch) would read the float32 input in several passes: it
-// reads 12 bytes a particle once and writes 8 a kept one, which every pass
-// then reads instead of 12 a particle.
+// super-item sketch) would read the input in several passes: it reads the
+// input once (12 bytes a float32 particle, 8 a packed record) and writes 8 a
+// kept one, which every pass then reads instead of the input.
 bool want_compact(hs_sketch *h, uint64_t n, double rate, bool packed) {
-    if (packed || h->routing || h->is_view || h->d.F != 1 || h->d.Gq >= (1u << kPackBits))
-        return false;
+    if (h->routing || h->is_view || h->d.F != 1 || h->d.Gq >= (1u << kPackBits)) return false;
     if (!want_binned(h, n, rate)) return false;
     uint32_t passes = scatter_passes(h);
     if (h->super) {
         if (!want_binned(h->super, n, rate)) return false;
         passes += scatter_passes(h->super);
     }
-    return 12.0 + 8.0 * rate * (1.0 + passes) < 12.0 * passes;
+    const double in = packed ? 8.0 : 12.0;
+    return in + 8.0 * rate * (1.0 + passes) < in * passes;
 }
 
 // Binned update of h from the cell records of a compaction pass: `bound`
@@ -555,11 +555,12 @@ static hs_status cells_flush(hs_sketch *h, double rate) {
     return HS_OK;
 }
 
-// The compaction pass over float32 particles (device or page-locked host
-// memory) of a call of call_n particles: the cells of the kept ones are
-// appended; it writes both sketches' probes.
+// The compaction pass over float32 particles or packed records (device or
+// page-locked host memory) of a call of call_n particles: the cells of the
+// kept ones are appended; it writes both sketches' probes.
 static hs_status cells_append(hs_sketch *h, const float *xyz, uint64_t n, uint64_t g0, double rate,
-                              uint64_t call_n) {
+                              uint64_t call_n, bool packed) {
+    const size_t esz = packed ? 8 : 12;
     const uint64_t want = std::max<uint64_t>(std::min(call_n, kCellsMax), 1u << 20);
     if (h->cells_bound == 0 && h->cells_cap < want) {
         if (h->cells) cudaFree(h->cells);
@@ -583,8 +584,10 @@ static hs_status cells_append(hs_sketch *h, const float *xyz, uint64_t n, uint64
         EventPair ev;
         HS_TRY(take_events(h, &ev));
         cudaEventRecord(ev.a, h->stream);
-        HS_CUDA(launch_compact_cells(xyz + 3 * off, cnt, g0 + off, h->d, rate, h->p.sample_seed, p0,
-                                     p1, h->cells, h->cells_cnt, h->num_sms * 8, h->stream));
+        const float *src = reinterpret_cast<const float *>(reinterpret_cast<const char *>(xyz) + off * esz);
+        HS_CUDA(launch_compact_cells(src, cnt, g0 + off, h->d, rate, h->p.sample_seed, p0, p1,
+                                     h->cells, h->cells_cnt, h->num_sms * 8, h->stream,
+                                     packed ? 1 : 0));
         cudaEventRecord(ev.b, h->stream);
         h->pending_update.push_back(ev);
         h->stats.kernel_launches += 1;
@@ -599,7 +602,7 @@ static hs_status cells_append(hs_sketch *h, const float *xyz, uint64_t n, uint64
 // scatter.  update_finish ends the call.
 hs_status update_piece(hs_sketch *h, const float *xyz, uint64_t n, uint64_t g0, double rate,
                        bool packed, bool compact, uint64_t call_n) {
-    if (compact) return cells_append(h, xyz, n, g0, rate, call_n);
+    if (compact) return cells_append(h, xyz, n, g0, rate, call_n, packed);
     HS_TRY(launch_update_timed(h, xyz, n, g0, rate, packed));
     if (h->super) HS_TRY(launch_update_timed(h->super, xyz, n, g0, rate, packed));
     return HS_OK;

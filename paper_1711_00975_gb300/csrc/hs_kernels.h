@@ -103,7 +103,8 @@ struct BatchRing {
 BatchRing batch_ring(const BinLayout &L, const SketchDesc &d, uint32_t ngroups, double rate,
                      uint32_t slot_cap);
 // Compaction of a stream piece for several passes over it: every particle is
-// sampled (index g0 + i) and quantised once on d's mesh (d.F == 1); the
+// sampled (index g0 + i) and quantised once on d's mesh (d.F == 1; packed:
+// xyz holds packed position records, decoded as the packed scatter does); the
 // cells of kept, valid particles are appended to `cells` (cx | cy << 21 |
 // cz << 42, in no particular order) and counted in *count (reset by the
 // caller).  The probes of the sketch (probe, G) and of its super-item sketch
@@ -118,7 +119,8 @@ struct CompactProbe {
 cudaError_t launch_compact_cells(const float *xyz, uint64_t n, uint64_t g0, const SketchDesc &d,
                                  double rate, uint64_t sample_seed, const CompactProbe &p0,
                                  const CompactProbe &p1, uint64_t *cells,
-                                 unsigned long long *count, int blocks, cudaStream_t s);
+                                 unsigned long long *count, int blocks, cudaStream_t s,
+                                 int packed = 0);
 // C[bin range] += the codes of every region, then fill = 0
 cudaError_t launch_bin_accumulate(const BinLayout &L, const BinStore &B, int32_t *C,
                                   cudaStream_t s);

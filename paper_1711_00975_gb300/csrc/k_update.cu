@@ -153,24 +153,41 @@ __device__ __forceinline__ void compact_probe(const CompactProbe &p, uint64_t g,
     p.probe[g - p.base] = key;
 }
 
-// Sample and quantise every particle once; append the cells of the kept,
-// valid ones.  The sampling decision and the cell are the ones the float32
+// Sample and quantise every particle once (PACKED: decode every packed
+// position record); append the cells of the kept, valid ones.  The sampling decision and the cell are the ones the float32
 // path takes (splitmix64 of the global index against the same threshold;
 // axis_cell on the fine mesh).  A thread takes four particles (three float4
 // when the buffer is 16-byte aligned, which page-locked host memory read over
 // the host link wants); a warp reserves its records with one atomic.
-__device__ __forceinline__ bool compact_one(float x, float y, float z, uint64_t g,
-                                            const SketchDesc &d, uint64_t thr, int keep_all,
-                                            uint64_t seed, const CompactProbe &p0,
-                                            const CompactProbe &p1, uint64_t &rec) {
-    uint32_t cx = 0, cy = 0, cz = 0;
-    const bool valid = particle_cell(d, x, y, z, cx, cy, cz);
+__device__ __forceinline__ bool compact_cell(bool valid, uint32_t cx, uint32_t cy, uint32_t cz,
+                                             uint64_t g, uint64_t thr, int keep_all, uint64_t seed,
+                                             const CompactProbe &p0, const CompactProbe &p1,
+                                             uint64_t &rec) {
     compact_probe(p0, g, valid, cx, cy, cz);
     compact_probe(p1, g, valid, cx, cy, cz);
     rec = (uint64_t)cx | ((uint64_t)cy << kPackBits) | ((uint64_t)cz << (2 * kPackBits));
     return valid && (keep_all || splitmix64_at(seed, g) < thr);
 }
 
+__device__ __forceinline__ bool compact_one(float x, float y, float z, uint64_t g,
+                                            const SketchDesc &d, uint64_t thr, int keep_all,
+                                            uint64_t seed, const CompactProbe &p0,
+                                            const CompactProbe &p1, uint64_t &rec) {
+    uint32_t cx = 0, cy = 0, cz = 0;
+    const bool valid = particle_cell(d, x, y, z, cx, cy, cz);
+    return compact_cell(valid, cx, cy, cz, g, thr, keep_all, seed, p0, p1, rec);
+}
+
+// the same for a packed position record (the cell packed_cell gives)
+__device__ __forceinline__ bool compact_rec(uint64_t p, uint64_t g, const SketchDesc &d, uint64_t thr,
+                                            int keep_all, uint64_t seed, const CompactProbe &p0,
+                                            const CompactProbe &p1, uint64_t &rec) {
+    uint32_t cx = 0, cy = 0, cz = 0;
+    const bool valid = packed_cell(d, p, cx, cy, cz);
+    return compact_cell(valid, cx, cy, cz, g, thr, keep_all, seed, p0, p1, rec);
+}
+
+template <bool PACKED>
 __global__ void __launch_bounds__(256) k_compact(const float *__restrict__ xyz, uint64_t n,
                                                  uint64_t g0, const SketchDesc d, uint64_t thr,
                                                  int keep_all, int vec, uint64_t seed,
@@ -186,7 +203,26 @@ __global__ void __launch_bounds__(256) k_compact(const float *__restrict__ xyz, 
         const uint64_t q = base + lane;
         uint64_t rec[4] = {0, 0, 0, 0};
         uint32_t keep = 0;
-        if (q < full) {
+        if (PACKED && q < groups) {                     // four records: two 16-byte loads
+            const unsigned long long *r8 = reinterpret_cast<const unsigned long long *>(xyz);
+            uint64_t p[4];
+            if (q < full) {
+                const uint4 ua = __ldcs(reinterpret_cast<const uint4 *>(r8) + 2 * q);
+                const uint4 ub = __ldcs(reinterpret_cast<const uint4 *>(r8) + 2 * q + 1);
+                p[0] = ua.x | ((uint64_t)ua.y << 32);
+                p[1] = ua.z | ((uint64_t)ua.w << 32);
+                p[2] = ub.x | ((uint64_t)ub.y << 32);
+                p[3] = ub.z | ((uint64_t)ub.w << 32);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) p[j] = 4 * q + j < n ? __ldcs(r8 + 4 * q + j) : 0ull;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (4 * q + j < n)
+                    keep |= (uint32_t)compact_rec(p[j], g0 + 4 * q + j, d, thr, keep_all, seed, p0, p1,
+                                                  rec[j]) << j;
+        } else if (!PACKED && q < full) {
             const float4 u = __ldcs(p4 + 3 * q), v = __ldcs(p4 + 3 * q + 1), w = __ldcs(p4 + 3 * q + 2);
             const float px[4] = {u.x, u.w, v.z, w.y}, py[4] = {u.y, v.x, v.w, w.z},
                         pz[4] = {u.z, v.y, w.x, w.w};
@@ -194,7 +230,7 @@ __global__ void __launch_bounds__(256) k_compact(const float *__restrict__ xyz, 
             for (int j = 0; j < 4; ++j)
                 keep |= (uint32_t)compact_one(px[j], py[j], pz[j], g0 + 4 * q + j, d, thr, keep_all,
                                               seed, p0, p1, rec[j]) << j;
-        } else if (q < groups) {
+        } else if (!PACKED && q < groups) {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const uint64_t i = 4 * q + j;
@@ -319,15 +355,20 @@ cudaError_t launch_pack(const float *xyz, uint64_t n, double box, uint64_t *out,
 cudaError_t launch_compact_cells(const float *xyz, uint64_t n, uint64_t g0, const SketchDesc &d,
                                  double rate, uint64_t sample_seed, const CompactProbe &p0,
                                  const CompactProbe &p1, uint64_t *cells,
-                                 unsigned long long *count, int blocks, cudaStream_t s) {
+                                 unsigned long long *count, int blocks, cudaStream_t s, int packed) {
     if (n == 0) return cudaSuccess;
     if (d.F != 1 || d.Gq >= (1u << kPackBits)) return cudaErrorInvalidValue;
     const bool sampled = rate < 1.0;
     const uint64_t thr = sampled ? (uint64_t)ldexp(rate, 64) : 0;
     const uint64_t want = ((n + 3) / 4 + 255) / 256;
     const int vec = (reinterpret_cast<uintptr_t>(xyz) & 15u) == 0;
-    k_compact<<<(unsigned)std::min<uint64_t>(want, (uint64_t)blocks), 256, 0, s>>>(
-        xyz, n, g0, d, thr, sampled ? 0 : 1, vec, sample_seed, p0, p1, cells, count);
+    const unsigned grid = (unsigned)std::min<uint64_t>(want, (uint64_t)blocks);
+    if (packed)
+        k_compact<true><<<grid, 256, 0, s>>>(xyz, n, g0, d, thr, sampled ? 0 : 1, vec, sample_seed,
+                                             p0, p1, cells, count);
+    else
+        k_compact<false><<<grid, 256, 0, s>>>(xyz, n, g0, d, thr, sampled ? 0 : 1, vec, sample_seed,
+                                              p0, p1, cells, count);
     return cudaGetLastError();
 }
 

@@ -81,3 +81,29 @@ def test_row_passes_compacted_bitexact(hs, box, memory):
     wk, we = oracle.topk_full(C, p, 200, nthreads=NT)
     assert np.array_equal(keys, wk) and np.array_equal(est, we)
     sk.close()
+
+
+@pytest.mark.parametrize("memory", ["device", "pinned", "pageable"])
+def test_packed_records_compacted_bitexact(hs, box, memory):
+    """Packed position records (three 21-bit coordinates) at rate 0.1 into a
+    hierarchy: each record is decoded and sampled once by the compaction pass,
+    then both layers' passes read the kept cells."""
+    spec, x = box
+    F = 10
+    pk = oracle.pack(x, spec.box)
+    rec = pk.view(np.int64)
+    src = (torch.from_numpy(rec).cuda() if memory == "device" else
+           torch.from_numpy(rec).pin_memory() if memory == "pinned" else np.ascontiguousarray(rec))
+    sk = hs.Sketch(5, 20, spec.box, 0.1, 7, 8, flags=BINNED)
+    sk.set_hierarchy(F, 18, 2)
+    sk.update_packed(src, rate=0.1)
+    p = oracle.Params(5, 20, spec.box, 0.1, 7, 8)
+    q = oracle.super_params(p, F, 18)
+    C = oracle.sketch_update_packed(oracle.new_counters(p), p, pk, rate=0.1, nthreads=NT)
+    S = oracle.sketch_update_packed(oracle.new_counters(q), q, pk, rate=0.1, F=F, fine=p)
+    assert np.array_equal(sk.counters(), C)
+    assert np.array_equal(sk.super_counters(), S)
+    keys, est = sk.topk(300)
+    wk, we = oracle.topk_hier(C, p, S, q, F, 300, 2, nthreads=NT)
+    assert np.array_equal(keys, wk) and np.array_equal(est, we)
+    sk.close()
