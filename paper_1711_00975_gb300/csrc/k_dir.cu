@@ -160,7 +160,57 @@ __global__ void k_dir_inline(const uint32_t *__restrict__ offsets, const DirReco
     }
 }
 
-// one thread per (cx, hot bucket of row r)
+// The cells of a warp's lines that fall in their pair's bucket wait in a
+// per-warp queue and are checked 32 at a time, every lane busy: a line's
+// checks (other rows' hot bits, then the estimate) cost far more than
+// finding it, and pairs hold different numbers of lines.
+constexpr int kDirWarps = 8;          // 256 threads
+constexpr int kLineQueue = 64;
+
+__device__ __forceinline__ uint64_t pack_line(uint32_t cx, uint32_t cy, uint32_t cz) {
+    return (uint64_t)cx | ((uint64_t)cy << 16) | ((uint64_t)cz << 32);
+}
+
+// One queued cell: reported when row r is its first hot row, at least `need`
+// rows are hot and its estimate passes.
+template <int T>
+__device__ __forceinline__ void dir_check(uint64_t cell, const int32_t *__restrict__ C,
+                                          const SketchDesc &d, int r, const uint32_t *__restrict__ bits,
+                                          int32_t theta, uint32_t mode, const SearchOut &out) {
+    const uint32_t rows = T > 0 ? (uint32_t)T : d.rows;
+    const uint32_t need = rows - (rows - 1) / 2;
+    const uint64_t words_per_row = d.W >> 5 ? d.W >> 5 : 1;
+    const uint32_t cx = (uint32_t)(cell & 0xFFFFu), cy = (uint32_t)((cell >> 16) & 0xFFFFu),
+                   cz = (uint32_t)(cell >> 32);
+    // the rows before r must be cold (the cell is reported from its first hot
+    // row) and at least `need` rows hot; nearly every line fails one of the
+    // two after a row or two, so stop there
+    uint32_t nhot = 1, left = rows - 1;
+    for (uint32_t rr = 0; rr < rows; ++rr) {
+        if ((int)rr == r) continue;
+        const uint64_t v = row_value(d.seed[rr], cx, cy, cz);
+        const bool hh = exact_hot(bits, words_per_row, (int)rr, bucket_of(v, d.log2w));
+        if ((int)rr < r && hh) return;
+        nhot += hh;
+        if (nhot + --left < need) return;
+    }
+    int32_t ev[T > 0 ? T : kMaxRows];
+    for (uint32_t rr = 0; rr < rows; ++rr) {
+        const uint64_t v = row_value(d.seed[rr], cx, cy, cz);
+        ev[rr] = signed_count(__ldg(C + rr * d.W + bucket_of(v, d.log2w)), v, d.log2w);
+    }
+    const int32_t est = T == 5 ? median5(ev[0], ev[1], ev[2], ev[3], ev[4])
+                               : lower_median_dyn(ev, (int)rows);
+    const bool pass = mode == kGE ? est >= theta : (mode == kGT ? est > theta : est == theta);
+    if (!pass) return;
+    const unsigned long long idx = atomicAdd(out.count, 1ull);
+    if (idx < out.cap) {
+        out.key[idx] = key_of(cx, cy, cz, d.G);
+        out.est[idx] = est;
+    }
+}
+
+// one lane per (cx, hot bucket of row r); the warp's items advance together
 template <int T>
 __global__ void __launch_bounds__(256)
     k_dir_query(const int32_t *__restrict__ C, const SketchDesc d, int r, uint32_t D,
@@ -168,69 +218,86 @@ __global__ void __launch_bounds__(256)
                 const uint4 *__restrict__ inl, const uint32_t *__restrict__ hot, uint64_t n_hot,
                 const uint32_t *__restrict__ bits, int32_t theta, uint32_t mode, uint64_t line_lo,
                 uint64_t line_hi, SearchOut out, RouteFilter skip, uint64_t gmagic) {
-    const uint32_t rows = T > 0 ? (uint32_t)T : d.rows;
-    const uint32_t need = rows - (rows - 1) / 2;
-    const uint64_t words_per_row = d.W >> 5 ? d.W >> 5 : 1;
+    __shared__ uint64_t queue[kDirWarps][kLineQueue];
     const uint32_t s = 64 - d.log2w;
     const uint64_t nslots = 1ull << D;
     const uint64_t total = n_hot * d.G;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += stride) {
-        const uint64_t hi = div_invariant(q, d.G, gmagic);   // q = hi G + cx
-        const uint32_t h = hot[hi];
-        const uint32_t cx = (uint32_t)(q - hi * d.G);
-        const uint64_t Tx = d.seed[r].a0 * (uint64_t)cx;
-        const uint64_t lo = ((uint64_t)h << s) - Tx;
-        const uint64_t slot0 = lo >> (64 - D);
-        // one mesh line (cy, cz) of the directory: its cell in column cx, if it
-        // falls in bucket h, is estimated when row r is its first hot row
-        auto visit = [&](DirRecord p) {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    uint64_t *q = queue[warp];
+    uint32_t nq = 0;
+    // check 32 queued cells (the oldest), keep the rest
+    auto drain = [&]() {
+        __syncwarp();
+        dir_check<T>(q[lane], C, d, r, bits, theta, mode, out);
+        __syncwarp();
+        if (lane < nq - 32) q[lane] = q[32 + lane];
+        nq -= 32;
+        __syncwarp();
+    };
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t base = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5; base < total;
+         base += warps << 5) {                                   // warp-uniform
+        const uint64_t i = base + lane;
+        const bool item = i < total;
+        uint32_t h = 0, cx = 0;
+        uint64_t Tx = 0;
+        uint4 v[2] = {make_uint4(kEmpty, kEmpty, kEmpty, kEmpty), make_uint4(kEmpty, kEmpty, kEmpty, kEmpty)};
+        uint64_t slot0 = 0;
+        if (item) {
+            const uint64_t hi = div_invariant(i, d.G, gmagic);   // i = hi G + cx
+            h = hot[hi];
+            cx = (uint32_t)(i - hi * d.G);
+            Tx = d.seed[r].a0 * (uint64_t)cx;
+            slot0 = (((uint64_t)h << s) - Tx) >> (64 - D);
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+                v[j] = inl ? __ldg(inl + ((slot0 + j) & (nslots - 1))) : make_uint4(kCrowded, 0, 0, 0);
+        }
+        // a line (cy, cz) whose cell in column cx falls in bucket h, inside
+        // the pass's line window and not routed, is a cell to check
+        auto wanted = [&](DirRecord p) {
             const uint32_t cy = p & 0xFFFFu, cz = p >> 16;
-            if (((line_value(d.seed[r], cy, cz) + Tx) >> s) != h) return;
+            if (((line_value(d.seed[r], cy, cz) + Tx) >> s) != h) return false;
             const uint64_t line = (uint64_t)cy + (uint64_t)d.G * cz;
-            if (line < line_lo || line >= line_hi) return;
-            if (skip.bits && routed_cell(skip, cx, cy, cz)) return;
-            // the rows before r must be cold (the cell is reported from its
-            // first hot row) and at least `need` rows hot; nearly every line
-            // fails one of the two after a row or two, so stop there
-            uint32_t nhot = 1, left = rows - 1;
-            for (uint32_t rr = 0; rr < rows; ++rr) {
-                if ((int)rr == r) continue;
-                const uint64_t v = row_value(d.seed[rr], cx, cy, cz);
-                const bool hh = exact_hot(bits, words_per_row, (int)rr, bucket_of(v, d.log2w));
-                if ((int)rr < r && hh) return;
-                nhot += hh;
-                if (nhot + --left < need) return;
-            }
-            int32_t ev[T > 0 ? T : kMaxRows];
-            for (uint32_t rr = 0; rr < rows; ++rr) {
-                const uint64_t v = row_value(d.seed[rr], cx, cy, cz);
-                ev[rr] = signed_count(__ldg(C + rr * d.W + bucket_of(v, d.log2w)), v, d.log2w);
-            }
-            int32_t est = T == 5 ? median5(ev[0], ev[1], ev[2], ev[3], ev[4])
-                                 : lower_median_dyn(ev, (int)rows);
-            bool pass = mode == kGE ? est >= theta : (mode == kGT ? est > theta : est == theta);
-            if (!pass) return;
-            unsigned long long idx = atomicAdd(out.count, 1ull);
-            if (idx < out.cap) {
-                out.key[idx] = key_of(cx, cy, cz, d.G);
-                out.est[idx] = est;
-            }
+            if (line < line_lo || line >= line_hi) return false;
+            return !(skip.bits && routed_cell(skip, cx, cy, cz));
         };
+        auto push = [&](bool take, DirRecord p) {            // all lanes of the warp
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, take);
+            if (take) q[nq + __popc(m & lt)] = pack_line(cx, p & 0xFFFFu, p >> 16);
+            nq += __popc(m);
+            if (nq >= 32) drain();
+        };
+#pragma unroll
         for (int j = 0; j < 2; ++j) {
-            const uint64_t slot = (slot0 + j) & (nslots - 1);
-            const uint4 v = inl ? __ldg(inl + slot) : make_uint4(kCrowded, 0, 0, 0);
-            if (v.x == kCrowded) {
-                const uint32_t e0 = offsets[slot], e1 = offsets[slot + 1];
-                for (uint32_t e = e0; e < e1; ++e) visit(rec[e]);
-            } else {
-                if (v.x != kEmpty) visit(v.x);
-                if (v.y != kEmpty) visit(v.y);
-                if (v.z != kEmpty) visit(v.z);
-                if (v.w != kEmpty) visit(v.w);
+            const uint32_t e[4] = {v[j].x, v[j].y, v[j].z, v[j].w};
+            const bool crowded = e[0] == kCrowded;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool ok = item && !crowded && e[u] != kEmpty && wanted(e[u]);
+                push(ok, e[u]);
+            }
+            // a slot with more lines than an inline entry holds: its records,
+            // the warp walking the longest list
+            uint32_t e0 = 0, e1 = 0;
+            if (item && crowded) {
+                const uint64_t slot = (slot0 + j) & (nslots - 1);
+                e0 = offsets[slot];
+                e1 = offsets[slot + 1];
+            }
+            const uint32_t len = e1 - e0;
+            uint32_t most = len;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) most = max(most, __shfl_xor_sync(0xFFFFFFFFu, most, o));
+            for (uint32_t k = 0; k < most; ++k) {
+                const DirRecord p = k < len ? rec[e0 + k] : 0u;
+                push(k < len && wanted(p), p);
             }
         }
     }
+    __syncwarp();
+    if (lane < nq) dir_check<T>(q[lane], C, d, r, bits, theta, mode, out);   // the rest
 }
 
 }  // namespace
