@@ -286,9 +286,38 @@ __device__ __forceinline__ void bt_candidate(const int32_t *__restrict__ Cv, con
     }
 }
 
+// A directory record of pair j (volume j / F, row j mod F) whose cell in
+// column cx lies in its bucket: reported when row r is the cell's first hot
+// row, at least `need` rows are hot and the estimate reaches theta_v.
+template <int T>
+__device__ __forceinline__ void bt_check(uint64_t cell, const int32_t *__restrict__ C,
+                                         const SketchDesc &d, const BatchTopkBufs &b) {
+    const uint32_t rows = T > 0 ? (uint32_t)T : d.rows;
+    const uint32_t need = rows - (rows - 1) / 2;
+    const uint64_t wpr = d.W >> 5;
+    const uint32_t cx = (uint32_t)(cell & 0xFFFFu), cy = (uint32_t)((cell >> 16) & 0xFFFFu),
+                   cz = (uint32_t)((cell >> 32) & 0xFFFFu), j = (uint32_t)(cell >> 48);
+    const uint32_t v = j / b.F;
+    const int r = (int)(j - v * b.F);
+    const uint32_t *bits = b.bits + (uint64_t)v * d.rows * wpr;
+    uint32_t nhot = 1, left = rows - 1;
+    for (uint32_t rr = 0; rr < rows; ++rr) {
+        if ((int)rr == r) continue;
+        const uint64_t val = row_value(d.seed[rr], cx, cy, cz);
+        const bool hh = exact_hot(bits, wpr, (int)rr, bucket_of(val, d.log2w));
+        if ((int)rr < r && hh) return;
+        nhot += hh;
+        if (nhot + --left < need) return;
+    }
+    bt_candidate<T>(C + (uint64_t)v * d.rows * d.W, d, rows, v, b.vol[v].G, b.theta[v], cx, cy, cz, b);
+}
+
+constexpr int kBtQueue = 64;   // per-warp queue of records to check
+
 template <int T>
 __global__ void __launch_bounds__(256, 6)   // 42 registers: 6 blocks an SM (measured faster than 4)
     k_bt_query(const int32_t *__restrict__ C, const SketchDesc d, BatchTopkBufs b) {
+    __shared__ uint64_t queue[8][kBtQueue];
     const uint32_t n = b.nvol * b.F;
     const uint64_t total = b.pre[n];
     const uint32_t rows = T > 0 ? (uint32_t)T : d.rows;
@@ -296,6 +325,9 @@ __global__ void __launch_bounds__(256, 6)   // 42 registers: 6 blocks an SM (mea
     const uint64_t wpr = d.W >> 5;
     const uint32_t s = 64 - d.log2w;
     const uint32_t lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    uint64_t *qu = queue[threadIdx.x >> 5];
+    uint32_t nq = 0;
     const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t q0 = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 5; q0 < total;
          q0 += warps << 5) {                                      // warp-uniform
@@ -312,64 +344,84 @@ __global__ void __launch_bounds__(256, 6)   // 42 registers: 6 blocks an SM (mea
         }
         j = __shfl_sync(0xFFFFFFFFu, j, 0);
         const uint64_t q = q0 + lane;
-        if (q >= total) continue;
-        while (j + 1 < n && __ldg(b.pre + j + 1) <= q) ++j;
+        const bool item = q < total;
+        if (item)
+            while (j + 1 < n && __ldg(b.pre + j + 1) <= q) ++j;
         const uint32_t v = j / b.F;
         const int r = (int)(j - v * b.F);
-        const uint32_t G = b.vol[v].G;
-        const uint64_t gm = b.vol[v].gmagic;
-        const uint64_t local = q - __ldg(b.pre + j);
-        const int32_t *Cv = C + (uint64_t)v * d.rows * d.W;
-        const uint32_t *bits = b.bits + (uint64_t)v * d.rows * wpr;
-        const int32_t theta = b.theta[v];
-        if (b.scan[v]) {                     // one cell of a scanned volume
-            const uint64_t rest = div_invariant(local, G, gm), cz = div_invariant(rest, G, gm);
-            const uint32_t cx = (uint32_t)(local - rest * G), cy = (uint32_t)(rest - cz * G);
-            uint32_t nhot = 0, left = rows;
-            bool skip = false;
-            for (uint32_t rr = 0; rr < rows; ++rr) {
-                const uint64_t val = row_value(d.seed[rr], cx, cy, cz);
-                nhot += exact_hot(bits, wpr, (int)rr, bucket_of(val, d.log2w));
-                if (nhot + --left < need) { skip = true; break; }
-            }
-            if (!skip) bt_candidate<T>(Cv, d, rows, v, G, theta, cx, cy, cz, b);
-            continue;
-        }
-        const uint64_t hi = div_invariant(local, G, gm);      // local = hi G + cx
-        const uint32_t h = __ldg(b.hot + (uint64_t)j * b.hot_cap + hi);
-        const uint32_t cx = (uint32_t)(local - hi * G);
-        const uint32_t *off = b.dir_off[j];
-        const DirRecord *rec = b.dir_rec[j];
-        const uint32_t D = b.vol[v].D;
-        const uint64_t Tx = d.seed[r].a0 * (uint64_t)cx;
-        // lines with L in [h 2^s - Tx, (h+1) 2^s - Tx): the records of slots
-        // a .. z (cyclic), contiguous in the counting-sorted array
-        const uint64_t lo = ((uint64_t)h << s) - Tx;
-        const uint64_t a = lo >> (64 - D), z = (lo + ((1ull << s) - 1)) >> (64 - D);
-        const uint32_t ea = __ldg(off + a), ez = __ldg(off + z + 1);
-        const uint32_t eend = a <= z ? ez : __ldg(off + (1ull << D));
-        for (int part = 0; part < (a <= z ? 1 : 2); ++part) {
-            const uint32_t e0 = part ? 0u : ea, e1 = part ? ez : eend;
-#pragma unroll 4
-            for (uint32_t e = e0; e < e1; ++e) {
-                const DirRecord p = __ldg(rec + e);
-                const uint32_t cy = p & 0xFFFFu, cz = p >> 16;
-                if (((line_value(d.seed[r], cy, cz) + Tx) >> s) != h) continue;
-                // the rows before r cold, at least `need` rows hot
-                uint32_t nhot = 1, left = rows - 1;
+        uint32_t e0 = 0, len = 0, cx = 0, h = 0, wrap = 0xFFFFFFFFu;
+        uint64_t Tx = 0;
+        const DirRecord *rec = nullptr;
+        if (item) {
+            const uint32_t G = b.vol[v].G;
+            const uint64_t gm = b.vol[v].gmagic;
+            const uint64_t local = q - __ldg(b.pre + j);
+            if (b.scan[v]) {                 // one cell of a scanned volume: checked here
+                const uint64_t rest = div_invariant(local, G, gm), cz = div_invariant(rest, G, gm);
+                const uint32_t ccx = (uint32_t)(local - rest * G), cy = (uint32_t)(rest - cz * G);
+                const uint32_t *bits = b.bits + (uint64_t)v * d.rows * wpr;
+                uint32_t nhot = 0, left = rows;
                 bool skip = false;
                 for (uint32_t rr = 0; rr < rows; ++rr) {
-                    if ((int)rr == r) continue;
-                    const uint64_t val = row_value(d.seed[rr], cx, cy, cz);
-                    const bool hh = exact_hot(bits, wpr, (int)rr, bucket_of(val, d.log2w));
-                    if ((int)rr < r && hh) { skip = true; break; }
-                    nhot += hh;
+                    const uint64_t val = row_value(d.seed[rr], ccx, cy, (uint32_t)cz);
+                    nhot += exact_hot(bits, wpr, (int)rr, bucket_of(val, d.log2w));
                     if (nhot + --left < need) { skip = true; break; }
                 }
-                if (!skip) bt_candidate<T>(Cv, d, rows, v, G, theta, cx, cy, cz, b);
+                if (!skip)
+                    bt_candidate<T>(C + (uint64_t)v * d.rows * d.W, d, rows, v, G, b.theta[v], ccx, cy,
+                                    (uint32_t)cz, b);
+            } else {                         // a (hot bucket, column) query: its run of records
+                const uint64_t hi = div_invariant(local, G, gm);      // local = hi G + cx
+                h = __ldg(b.hot + (uint64_t)j * b.hot_cap + hi);
+                cx = (uint32_t)(local - hi * G);
+                const uint32_t *off = b.dir_off[j];
+                rec = b.dir_rec[j];
+                const uint32_t D = b.vol[v].D;
+                Tx = d.seed[r].a0 * (uint64_t)cx;
+                // lines with L in [h 2^s - Tx, (h+1) 2^s - Tx): the records of
+                // slots a .. z, contiguous in the counting-sorted array (a run
+                // that wraps past the last slot continues at record 0: index
+                // e0 + k taken modulo `wrap`)
+                const uint64_t lo = ((uint64_t)h << s) - Tx;
+                const uint64_t a = lo >> (64 - D), z = (lo + ((1ull << s) - 1)) >> (64 - D);
+                e0 = __ldg(off + a);
+                const uint32_t ez = __ldg(off + z + 1);
+                const uint32_t nrec = __ldg(off + (1ull << D));
+                len = a <= z ? ez - e0 : (nrec - e0) + ez;
+                if (a > z) wrap = nrec;
+            }
+        }
+        // the warp walks the longest run; in-bucket records are queued and
+        // checked 32 at a time
+        uint32_t most = len;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) most = max(most, __shfl_xor_sync(0xFFFFFFFFu, most, o));
+        for (uint32_t k = 0; k < most; ++k) {
+            bool take = false;
+            uint64_t cell = 0;
+            if (k < len) {
+                uint32_t idx = e0 + k;
+                if (idx >= wrap) idx -= wrap;
+                const DirRecord p = __ldg(rec + idx);
+                const uint32_t cy = p & 0xFFFFu, cz = p >> 16;
+                take = ((line_value(d.seed[r], cy, cz) + Tx) >> s) == h;
+                cell = (uint64_t)cx | ((uint64_t)cy << 16) | ((uint64_t)cz << 32) | ((uint64_t)j << 48);
+            }
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, take);
+            if (take) qu[nq + __popc(m & lt)] = cell;
+            nq += __popc(m);
+            if (nq >= 32) {
+                __syncwarp();
+                bt_check<T>(qu[lane], C, d, b);
+                __syncwarp();
+                if (lane < nq - 32) qu[lane] = qu[32 + lane];
+                nq -= 32;
+                __syncwarp();
             }
         }
     }
+    __syncwarp();
+    if (lane < nq) bt_check<T>(qu[lane], C, d, b);
 }
 
 // 7. the kk best candidates of each volume in rank order, one block a
