@@ -352,7 +352,7 @@ __device__ __forceinline__ void stage_cell(const Cell &c, const SketchDesc &d, c
         for (int r = 0; r < T; ++r) {
             const uint32_t h = row_hi(d.seed[r], c.cx, c.cy, c.cz) >> a.hshift;
             code[r] = h & a.code_mask;
-            bin[r] = (h >> (a.S + 1)) + a.rbase[r] + c.bin0;
+            bin[r] = (h >> (a.S + 1)) + a.rbase[r] + (WIN ? c.bin0 : 0u);   // bin0 = 0 outside a batch
         }
 #pragma unroll
         for (int r = 0; r < T; ++r) w[r] = atomicAdd(&s.fill[bin[r]], 0x10002u);
@@ -366,7 +366,7 @@ __device__ __forceinline__ void stage_cell(const Cell &c, const SketchDesc &d, c
     } else {
         for (uint32_t i = 0; i < a.nrows; ++i) {
             const uint32_t h = row_hi(d.seed[a.row0 + i], c.cx, c.cy, c.cz) >> a.hshift;
-            const uint32_t bin = (h >> (a.S + 1)) + a.rbase[i] + c.bin0;
+            const uint32_t bin = (h >> (a.S + 1)) + a.rbase[i] + (WIN ? c.bin0 : 0u);
             const uint32_t code = h & a.code_mask;
             const uint32_t w = atomicAdd(&s.fill[bin], 0x10002u);
             if ((w >> 16) < a.slot)
