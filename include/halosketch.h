@@ -309,6 +309,7 @@ typedef struct {
     uint32_t slot;           /* shared-memory ring depth (codes per bin)          */
     uint32_t configs_tried;  /* 0: the process's earlier choice for this shape    */
     float best_ms;           /* its time for the tuning data                      */
+    uint32_t window_volumes; /* consecutive volumes whose bins have rings         */
 } hs_tune;
 
 /* params: rows, log2_width, cell, hash_seed, sample_seed, flags as for
@@ -325,8 +326,9 @@ hs_status batch_counters(hs_batch *b, uint32_t volume, int32_t *out);
 hs_status batch_reset(hs_batch *b);
 hs_status batch_volume_info(const hs_batch *b, uint32_t volume, hs_info *out);
 hs_status batch_stats(hs_batch *b, hs_stats *out, int reset);
-/* Time the scatter's shared-memory ring depth (the deepest that fits the ring
- * window of volumes, a half and a quarter of it) on the given particles and
+/* Time the scatter's ring window and depth (the widest window whose rings
+ * hold a tile's codes; a window of one volume with its deepest ring, a half and
+ * a quarter of it) on the given particles and
  * keep the fastest for later updates.  The tuning runs update the sketches, so
  * the batch is reset afterwards.  The choice is kept for the process, keyed by
  * (device, log2_width, rows, sample_rate): a later call for the same shape

@@ -20,7 +20,7 @@ constexpr uint64_t kBatchProbe = 1ull << 16;   // probe keys per volume
 // Ring depths chosen by batch_autotune, per (device, log2 W, rows, sample
 // rate), kept for the process so later batches of the same shape skip tuning.
 struct TuneChoice {
-    uint32_t slot;
+    uint32_t wvols, slot;
     float ms;
 };
 std::mutex g_tune_mu;
@@ -44,6 +44,7 @@ struct hs_batch {
     BinBuffers bb;                      // code regions, sized per volume
     uint32_t rounds = 0;                // scatter tiles between flushes (0: default)
     uint32_t slot = 0;                  // scatter ring depth (0: largest that fits)
+    uint32_t wvols = 0;                 // ring window of volumes at most (0: up to 4)
     VolumeDesc *d_vols = nullptr;
     VolumeDesc *h_vols = nullptr;       // pinned: read by the graph's copy node
     uint32_t *tvols = nullptr;          // per scatter tile: its first and last volume
@@ -113,7 +114,8 @@ hs_status batch_ensure_bins(hs_batch *b, const uint64_t *offsets, double rate) {
         b->tvols_cap = std::max<uint64_t>(ntiles, 1024);
     }
     if (b->bb.codes) return HS_OK;
-    const uint32_t half = batch_ring(b->bl, b->d, b->nvol, rate, 0).slot / 2;
+    // padding of the deepest ring any window may use (a window of one volume)
+    const uint32_t half = batch_ring(b->bl, b->d, b->nvol, rate, 0, 1).slot / 2;
     const uint32_t nblocks = (uint32_t)b->num_sms;
     const uint32_t bpr = 1u << (b->d.log2w - b->bl.S);
     const uint32_t bpv = b->d.rows * bpr;
@@ -134,7 +136,8 @@ hs_status batch_enqueue(hs_batch *b, const float *xyz, uint64_t n, double rate) 
                             cudaMemcpyHostToDevice, b->stream));
     HS_CUDA(launch_bin_scatter(xyz, n, 0, b->d, b->C, rate, b->p.sample_seed, b->probe, 0,
                                kBatchProbe, b->bl, b->bb.store(), b->stream, b->d_vols, b->nvol,
-                               kBatchProbe, nullptr, 0, b->rounds, b->slot, b->tvols));
+                               kBatchProbe, nullptr, 0, b->rounds, b->slot, b->tvols, nullptr, 0,
+                               b->wvols));
     HS_CUDA(launch_bin_accumulate(b->bl, b->bb.store(), b->C, b->stream));
     return HS_OK;
 }
@@ -754,26 +757,30 @@ hs_status batch_autotune(hs_batch *b, const float *xyz, const uint64_t *offsets,
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {          // tuned before for this shape: no runs
+            b->wvols = it->second.wvols;
             b->slot = it->second.slot;
             b->rounds = 1;
+            const BatchRing r = batch_ring(b->bl, b->d, b->nvol, sample_rate, b->slot, b->wvols);
             out->rounds = 1;
-            out->slot = it->second.slot ? it->second.slot
-                                        : batch_ring(b->bl, b->d, b->nvol, sample_rate, 0).slot;
+            out->slot = r.slot;
+            out->window_volumes = r.wvols;
             out->configs_tried = 0;
             out->best_ms = it->second.ms;
             return HS_OK;
         }
     }
-    // candidates: the ring depth that fits the window, a half and a quarter
-    // of it (a shallower ring lets the window hold more volumes); one tile
-    // is staged between flush phases
-    const uint32_t deepest = batch_ring(b->bl, b->d, b->nvol, sample_rate, 0).slot;
-    const uint32_t slot_opt[3] = {0, deepest / 2, deepest / 4};
+    // candidates: the deepest ring of the widest window that holds a tile's
+    // codes (up to 4 volumes), then windows of one volume with the deepest
+    // ring, a half and a quarter of it; one tile is staged between flushes
+    const uint32_t deep1 = batch_ring(b->bl, b->d, b->nvol, sample_rate, 0, 1).slot;
+    const uint32_t wv_opt[4] = {0, 1, 1, 1};
+    const uint32_t slot_opt[4] = {0, 0, deep1 / 2, deep1 / 4};
     float best = 1e30f;
-    uint32_t best_slot = 0, best_rounds = 1;
+    uint32_t best_slot = 0, best_wv = 0, best_rounds = 1;
     int tried = 0;
-    for (int si = 0; si < 3; ++si) {
-        if (si > 0 && slot_opt[si] < 16) continue;
+    for (int si = 0; si < 4; ++si) {
+        if (slot_opt[si] != 0 && slot_opt[si] < 16) continue;
+        b->wvols = wv_opt[si];
         b->slot = slot_opt[si];
         b->rounds = 1;
         float ms_best = 1e30f;
@@ -792,19 +799,23 @@ hs_status batch_autotune(hs_batch *b, const float *xyz, const uint64_t *offsets,
         if (ms_best < best) {
             best = ms_best;
             best_slot = slot_opt[si];
+            best_wv = wv_opt[si];
         }
     }
+    b->wvols = best_wv;
     b->slot = best_slot;
     b->rounds = best_rounds;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tune_cache[key] = TuneChoice{best_slot, best};
+        g_tune_cache[key] = TuneChoice{best_wv, best_slot, best};
     }
     st = batch_reset(b);                              // tuning runs touched the counters
     if (st != HS_OK) return st;
     HS_CUDA(cudaStreamSynchronize(b->stream));
+    const BatchRing chosen = batch_ring(b->bl, b->d, b->nvol, sample_rate, best_slot, best_wv);
     out->rounds = best_rounds;
-    out->slot = best_slot ? best_slot : deepest;
+    out->slot = chosen.slot;
+    out->window_volumes = chosen.wvols;
     out->configs_tried = (uint32_t)tried;
     out->best_ms = best;
     return HS_OK;

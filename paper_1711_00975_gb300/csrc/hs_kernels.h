@@ -90,18 +90,20 @@ cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const 
                                uint32_t probe_per_vol = 0, const RouteTarget *route = nullptr,
                                int packed = 0, uint32_t rounds = 0, uint32_t slot = 0,
                                uint32_t *tile_vols = nullptr,
-                               const unsigned long long *n_dev = nullptr, uint64_t n_base = 0);
+                               const unsigned long long *n_dev = nullptr, uint64_t n_base = 0,
+                               uint32_t wvols_cap = 0);
 // packed: 0 float32 xyz, 1 packed position records, 2 cell records (from
 // launch_compact_cells; n is then a bound and the launch takes the records
 // [n_base, min(n_base + n, *n_dev)) of the buffer starting n_base before xyz)
 // Rings of a batch's scatter: the bins of a window of `wvols` consecutive
 // volumes (a power of two) have rings of `slot` entries; tiles holding
-// particles of later volumes move the window.  slot_cap: 0 or a smaller ring.
+// particles of later volumes move the window.  slot_cap: 0 or a smaller ring;
+// wvols_cap: 0 (4) or a smaller window.
 struct BatchRing {
     uint32_t wvols, nslots, slot;
 };
 BatchRing batch_ring(const BinLayout &L, const SketchDesc &d, uint32_t ngroups, double rate,
-                     uint32_t slot_cap);
+                     uint32_t slot_cap, uint32_t wvols_cap = 0);
 // Compaction of a stream piece for several passes over it: every particle is
 // sampled (index g0 + i) and quantised once on d's mesh (d.F == 1; packed:
 // xyz holds packed position records, decoded as the packed scatter does); the

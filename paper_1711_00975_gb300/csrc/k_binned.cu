@@ -153,7 +153,7 @@ BinLayout bin_layout(const SketchDesc &d, size_t smem_budget, bool single_pass, 
 }
 
 BatchRing batch_ring(const BinLayout &L, const SketchDesc &d, uint32_t ngroups, double rate,
-                     uint32_t slot_cap) {
+                     uint32_t slot_cap, uint32_t wvols_cap) {
     const uint32_t lbpr = d.log2w - L.S;
     const uint32_t bpv = d.rows << lbpr;
     const bool sampled = rate < 1.0;
@@ -161,7 +161,7 @@ BatchRing batch_ring(const BinLayout &L, const SketchDesc &d, uint32_t ngroups, 
     // left over from the last flush and one tile's codes
     const double per_tile = kScatterTile * rate / (double)(1u << lbpr);
     BatchRing r{0, 0, 0};
-    for (uint32_t wv = 4; wv >= 1; wv >>= 1) {
+    for (uint32_t wv = wvols_cap >= 4 || wvols_cap == 0 ? 4 : (wvols_cap >= 2 ? 2 : 1); wv >= 1; wv >>= 1) {
         uint32_t slot = ring_slot(wv * bpv, ngroups, sampled ? 1 : 0, kSmemLimit, true);
         if (slot_cap && slot_cap < slot) slot = slot_cap;
         if (slot >= 16 && (slot >= 2.5 * per_tile || wv == 1)) {
@@ -178,7 +178,7 @@ cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const 
                                const BinStore &B, cudaStream_t s, const VolumeDesc *vols,
                                uint32_t nvol, uint32_t probe_per_vol, const RouteTarget *route,
                                int packed, uint32_t rounds, uint32_t slot, uint32_t *tile_vols,
-                               const unsigned long long *n_dev, uint64_t n_base) {
+                               const unsigned long long *n_dev, uint64_t n_base, uint32_t wvols_cap) {
     if (n == 0) return cudaSuccess;
     if (vols && (!tile_vols || nvol == 0 || nvol > 65535)) return cudaErrorInvalidValue;
     if (L.slot == 0 || B.nblocks == 0 || !B.codes || !B.fill || B.ngroups == 0 ||
@@ -229,7 +229,7 @@ cudaError_t launch_bin_scatter(const float *xyz, uint64_t n, uint64_t g0, const 
         a.slot = ring_slot(a.nbins, B.ngroups, sampled ? 1 : 0, kSmemLimit);
         if (slot && slot < a.slot) a.slot = slot;     // a shallower ring (power of two)
         if (vols) {   // rings for a window of volumes, one tile between flushes
-            const BatchRing br = batch_ring(L, d, B.ngroups, rate, slot);
+            const BatchRing br = batch_ring(L, d, B.ngroups, rate, slot, wvols_cap);
             if (br.wvols == 0) return cudaErrorInvalidValue;
             a.wvols = br.wvols;
             a.bpv = d.rows << lbpr;

@@ -49,7 +49,8 @@ class hs_info(ctypes.Structure):
 
 class hs_tune(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_uint32), ("slot", ctypes.c_uint32),
-                ("configs_tried", ctypes.c_uint32), ("best_ms", ctypes.c_float)]
+                ("configs_tried", ctypes.c_uint32), ("best_ms", ctypes.c_float),
+                ("window_volumes", ctypes.c_uint32)]
 
 
 class hs_stats(ctypes.Structure):

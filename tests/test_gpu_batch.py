@@ -100,6 +100,7 @@ def test_batch_autotune_then_exact(hs):
     b2 = hs.Batch(5, 16, [s.box for s in specs], 0.1, hash_seed=11, sample_seed=2)
     tune2 = b2.autotune(d, off, 0.5)
     assert tune2["configs_tried"] == 0 and tune2["slot"] == tune["slot"]
+    assert tune2["window_volumes"] == tune["window_volumes"] in (1, 2, 4)
     b2.update(d, off, 0.5)
     for v, spec in enumerate(specs):
         p = oracle.Params(5, 16, spec.box, 0.1, 11, 2)
