@@ -319,7 +319,13 @@ hs_status batch_create(const hs_params *params, uint32_t n_volumes, const double
 hs_status batch_update(hs_batch *b, const float *xyz, const uint64_t *offsets, double sample_rate);
 /* Top-k of every volume (Algorithm 1 per volume): volume v's min(k, G_v^3)
  * entries go to keys/est[v*k ...] (HOST arrays of n_volumes*k), their number to
- * n_out[v].  Synchronous. */
+ * n_out[v], ranked (estimate desc, key asc) as topk_extract ranks them.
+ * Synchronous.  With k <= 4096 every volume is searched on the device in one
+ * captured graph (replayed while k stays the same; the per-volume directories
+ * are built on the first call); a volume outside its fixed capacities (fewer
+ * distinct probe cells than k, too many hot buckets or candidates) is answered
+ * by the per-volume search instead, counted in hs_stats.host_path_volumes.
+ * HS_FLAG_SEARCH_SCAN sends every volume to the per-volume search. */
 hs_status batch_topk(hs_batch *b, uint32_t k, uint64_t *keys, int32_t *est, uint32_t *n_out);
 /* Counters of one volume (rows x W int32, host or device out); synchronous. */
 hs_status batch_counters(hs_batch *b, uint32_t volume, int32_t *out);
