@@ -48,10 +48,7 @@ struct BinLayout {
 };
 // single_pass: every row in one launch or not at all (batches: a volume's bins
 // are offset within one launch)
-// max_S: largest bin (log2 counters; 15 fills a block's shared memory in the
-// accumulation)
-BinLayout bin_layout(const SketchDesc &d, size_t smem_budget, bool single_pass = false,
-                     uint32_t max_S = 15);
+BinLayout bin_layout(const SketchDesc &d, size_t smem_budget, bool single_pass = false);
 constexpr uint32_t kMaxBinGroups = 128;
 constexpr uint32_t kScatterTile = 3072;   // particles of one scatter tile (768 threads x 4)
 // Global side of the binned update.  Each scatter block owns one region per

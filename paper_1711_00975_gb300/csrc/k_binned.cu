@@ -127,10 +127,9 @@ cudaError_t ensure_smem_limit(const void *kernel, size_t bytes) {
     return e;
 }
 
-BinLayout bin_layout(const SketchDesc &d, size_t smem_budget, bool single_pass, uint32_t max_S) {
+BinLayout bin_layout(const SketchDesc &d, size_t smem_budget, bool single_pass) {
     BinLayout L{};
-    if (max_S > 15) max_S = 15;
-    L.S = d.log2w < max_S ? d.log2w : max_S;
+    L.S = d.log2w < 15 ? d.log2w : 15;
     const uint64_t nb = (uint64_t)d.rows << (d.log2w - L.S);
     if (nb >= 65536) return L;                // bins are 16-bit numbers (group division)
     L.nbins = (uint32_t)nb;

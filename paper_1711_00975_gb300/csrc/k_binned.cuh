@@ -266,16 +266,6 @@ __device__ __forceinline__ bool prep_record(uint64_t p, uint64_t g, const Sketch
     return keep && valid;
 }
 
-// Volume holding particle i of the concatenated buffer (binary search).
-__device__ __forceinline__ uint32_t vol_of(const ScatterArgs &a, uint64_t i) {
-    uint32_t lo = 0, hi = a.nvol;
-    while (hi - lo > 1) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (a.vols[mid].start <= i) lo = mid; else hi = mid;
-    }
-    return lo;
-}
-
 // Batch variant of prep_particle: particle i of the concatenated buffer
 // belongs to volume v (vols[v].start <= i < vols[v+1].start, found from the
 // hint v upward); it is sampled with its index inside that volume's stream and
