@@ -300,14 +300,18 @@ __device__ __forceinline__ void bt_check(uint64_t cell, const int32_t *__restric
     const uint32_t v = j / b.F;
     const int r = (int)(j - v * b.F);
     const uint32_t *bits = b.bits + (uint64_t)v * d.rows * wpr;
-    uint32_t nhot = 1, left = rows - 1;
-    for (uint32_t rr = 0; rr < rows; ++rr) {
-        if ((int)rr == r) continue;
+    // hot rows: r and rows after r (the rows before r must be cold); the rows
+    // after r first, stopping once `need` is out of reach, the rows before r last
+    uint32_t nhot = 1, left = rows - 1 - (uint32_t)r;
+    for (uint32_t rr = (uint32_t)r + 1; rr < rows; ++rr) {
         const uint64_t val = row_value(d.seed[rr], cx, cy, cz);
-        const bool hh = exact_hot(bits, wpr, (int)rr, bucket_of(val, d.log2w));
-        if ((int)rr < r && hh) return;
-        nhot += hh;
+        nhot += exact_hot(bits, wpr, (int)rr, bucket_of(val, d.log2w));
         if (nhot + --left < need) return;
+    }
+    if (nhot < need) return;
+    for (uint32_t rr = 0; rr < (uint32_t)r; ++rr) {
+        const uint64_t val = row_value(d.seed[rr], cx, cy, cz);
+        if (exact_hot(bits, wpr, (int)rr, bucket_of(val, d.log2w))) return;
     }
     bt_candidate<T>(C + (uint64_t)v * d.rows * d.W, d, rows, v, b.vol[v].G, b.theta[v], cx, cy, cz, b);
 }

@@ -182,17 +182,21 @@ __device__ __forceinline__ void dir_check(uint64_t cell, const int32_t *__restri
     const uint64_t words_per_row = d.W >> 5 ? d.W >> 5 : 1;
     const uint32_t cx = (uint32_t)(cell & 0xFFFFu), cy = (uint32_t)((cell >> 16) & 0xFFFFu),
                    cz = (uint32_t)(cell >> 32);
-    // the rows before r must be cold (the cell is reported from its first hot
-    // row) and at least `need` rows hot; nearly every line fails one of the
-    // two after a row or two, so stop there
-    uint32_t nhot = 1, left = rows - 1;
-    for (uint32_t rr = 0; rr < rows; ++rr) {
-        if ((int)rr == r) continue;
+    // the cell is reported from its first hot row r: the rows before r must
+    // be cold, so its hot rows are r and rows after r, of which at least
+    // `need` must be hot.  The rows after r come first: a line stops as soon
+    // as the rows left cannot make `need` (after one cold row for r = t - need,
+    // two for r one less, ...); the rows before r, nearly always cold, last.
+    uint32_t nhot = 1, left = rows - 1 - (uint32_t)r;
+    for (uint32_t rr = (uint32_t)r + 1; rr < rows; ++rr) {
         const uint64_t v = row_value(d.seed[rr], cx, cy, cz);
-        const bool hh = exact_hot(bits, words_per_row, (int)rr, bucket_of(v, d.log2w));
-        if ((int)rr < r && hh) return;
-        nhot += hh;
+        nhot += exact_hot(bits, words_per_row, (int)rr, bucket_of(v, d.log2w));
         if (nhot + --left < need) return;
+    }
+    if (nhot < need) return;
+    for (uint32_t rr = 0; rr < (uint32_t)r; ++rr) {
+        const uint64_t v = row_value(d.seed[rr], cx, cy, cz);
+        if (exact_hot(bits, words_per_row, (int)rr, bucket_of(v, d.log2w))) return;
     }
     int32_t ev[T > 0 ? T : kMaxRows];
     for (uint32_t rr = 0; rr < rows; ++rr) {
