@@ -237,7 +237,7 @@ hs_status ensure_dir_scratch(hs_sketch *h) {
     h->dir_D = std::min<uint32_t>(h->d.log2w, 26);
     h->hot_cap = std::min<uint64_t>(h->d.W, 1ull << 22);
     uint64_t nslots = 1ull << h->dir_D;
-    HS_CUDA(cudaMalloc(&h->xbits, (size_t)h->d.rows * wpr * 4));
+    HS_CUDA(cudaMalloc(&h->xbits, (size_t)h->d.rows * wpr * 4 * 2));   // signed maps
     HS_CUDA(cudaMalloc(&h->hot_list, (size_t)enum_rows(h) * h->hot_cap * 4));
     HS_CUDA(cudaMalloc(&h->hot_cnt, kMaxRows * sizeof(unsigned long long)));
     HS_CUDA(cudaMalloc(&h->dir_cursor, (nslots + 1) * 4));
@@ -624,8 +624,9 @@ hs_status search_pass_dir(hs_sketch *h, int32_t theta, SearchMode mode, int64_t 
         return HS_OK;
     }
     const uint32_t F = enum_rows(h);
-    HS_CUDA(launch_hot_bitmap(h->C, h->d, h->d.log2w, (int32_t)std::min<int64_t>(hot, INT32_MAX),
-                              h->xbits, h->num_sms * 8, h->stream));
+    if (h->d.W < 32 || hot < 1) return HS_OK;          // the scan instead
+    HS_CUDA(launch_signed_bits(h->C, h->d, (int32_t)std::min<int64_t>(hot, INT32_MAX), h->xbits,
+                               h->num_sms * 8, h->stream));
     HS_CUDA(cudaMemsetAsync(h->hot_cnt, 0, kMaxRows * sizeof(unsigned long long), h->stream));
     for (uint32_t r = 0; r < F; ++r)
         HS_CUDA(launch_hot_list(h->xbits, h->d, (int)r, h->hot_list + r * h->hot_cap,

@@ -243,10 +243,18 @@ cudaError_t launch_dir_build(const SketchDesc &d, int r, uint32_t D, bool inl, u
                              uint32_t *cursor, DirRecord *rec, uint32_t *scan_scratch,
                              int max_blocks, cudaStream_t s, int *launches);
 // bucket indices of the set bits of row r of an exact (one bit per bucket) hot bitmap
+// signed hot maps of every row for threshold theta >= 1 (W >= 32): bits holds
+// rows x W/32 words of the positive map (C >= theta), then of the negative
+// map (C <= -theta)
+cudaError_t launch_signed_bits(const int32_t *C, const SketchDesc &d, int32_t theta, uint32_t *bits,
+                               int max_blocks, cudaStream_t s);
+// row r's hot buckets from the signed maps, as bucket << 1 | sign bit
 cudaError_t launch_hot_list(const uint32_t *bits, const SketchDesc &d, int r, uint32_t *list,
                             unsigned long long *count, uint64_t cap, int max_blocks,
                             cudaStream_t s);
-// cells first hot in row r, with at least `need` hot rows and a passing estimate
+// cells first hot in row r, with at least `need` hot rows and a passing
+// estimate (hot: the row's signed count can reach theta: the signed maps);
+// hot: row r's list from launch_hot_list
 cudaError_t launch_dir_query(const int32_t *C, const SketchDesc &d, int r, uint32_t D, bool inl,
                              const uint32_t *offsets, const DirRecord *rec, const uint32_t *hot,
                              uint64_t n_hot, const uint32_t *bits, int32_t theta, SearchMode mode,

@@ -115,23 +115,54 @@ cudaError_t exclusive_scan(const uint32_t *in, uint32_t *out, uint64_t n, uint32
     return cudaGetLastError();
 }
 
-// list of the set bits of row r's exact hot bitmap (bucket indices)
-__global__ void k_hot_list(const uint32_t *__restrict__ bits, uint64_t words_per_row, int r,
-                           uint32_t *__restrict__ list, unsigned long long *__restrict__ count,
-                           uint64_t cap) {
+// Signed hot bitmaps of every row (one warp a word): bit b of the positive
+// map is set when C[b] >= theta, of the negative map when C[b] <= -theta.  A
+// cell's signed count in a row, sign * C[bucket], can reach theta only when
+// the map of its sign bit (0: positive, 1: negative) has its bucket set.
+// bits: rows x W/32 words of the positive map, then as many of the negative.
+__global__ void k_signed_bits(const int32_t *__restrict__ C, uint64_t words, int32_t theta,
+                              uint32_t *__restrict__ bits) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < words; w += warps) {
+        const int32_t c = __ldcs(C + w * 32 + lane);
+        const unsigned pos = __ballot_sync(0xFFFFFFFFu, c >= theta);
+        const unsigned neg = __ballot_sync(0xFFFFFFFFu, c <= -theta);
+        if (lane == 0) {
+            bits[w] = pos;
+            bits[words + w] = neg;
+        }
+    }
+}
+
+// row r's hot buckets with the sign a cell must have there: entries
+// bucket << 1 | sign bit (positive map: 0, negative map: 1)
+__global__ void k_hot_list(const uint32_t *__restrict__ bits, uint64_t words_per_row,
+                           uint64_t words, int r, uint32_t *__restrict__ list,
+                           unsigned long long *__restrict__ count, uint64_t cap) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words_per_row;
-         w += stride) {
-        uint32_t x = bits[(uint64_t)r * words_per_row + w];
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 2 * words_per_row;
+         i += stride) {
+        const uint32_t neg = i >= words_per_row;
+        const uint64_t w = i - neg * words_per_row;
+        uint32_t x = bits[neg * words + (uint64_t)r * words_per_row + w];
         if (!x) continue;
         unsigned long long base = atomicAdd(count, (unsigned long long)__popc(x));
         while (x) {
             int b = __ffs(x) - 1;
             x &= x - 1;
-            if (base < cap) list[base] = (uint32_t)(w * 32 + b);
+            if (base < cap) list[base] = ((uint32_t)(w * 32 + b) << 1) | neg;
             ++base;
         }
     }
+}
+
+// Is row rr of the cell whose row value is v hot for its sign?
+__device__ __forceinline__ bool signed_hot(const uint32_t *__restrict__ bits, uint64_t words_per_row,
+                                           uint64_t words, uint32_t rr, uint64_t v, uint32_t log2w) {
+    const uint32_t b = bucket_of(v, log2w);
+    const uint64_t neg = (v >> (63 - log2w)) & 1ull;
+    return (__ldg(bits + neg * words + (uint64_t)rr * words_per_row + (b >> 5)) >> (b & 31)) & 1u;
 }
 
 // The first records of every slot, inline: slot i's 16-byte entry holds its
@@ -179,7 +210,8 @@ __device__ __forceinline__ void dir_check(uint64_t cell, const int32_t *__restri
                                           int32_t theta, uint32_t mode, const SearchOut &out) {
     const uint32_t rows = T > 0 ? (uint32_t)T : d.rows;
     const uint32_t need = rows - (rows - 1) / 2;
-    const uint64_t words_per_row = d.W >> 5 ? d.W >> 5 : 1;
+    const uint64_t words_per_row = d.W >> 5;
+    const uint64_t words = (uint64_t)rows * words_per_row;
     const uint32_t cx = (uint32_t)(cell & 0xFFFFu), cy = (uint32_t)((cell >> 16) & 0xFFFFu),
                    cz = (uint32_t)(cell >> 32);
     // the cell is reported from its first hot row r: the rows before r must
@@ -189,15 +221,12 @@ __device__ __forceinline__ void dir_check(uint64_t cell, const int32_t *__restri
     // two for r one less, ...); the rows before r, nearly always cold, last.
     uint32_t nhot = 1, left = rows - 1 - (uint32_t)r;
     for (uint32_t rr = (uint32_t)r + 1; rr < rows; ++rr) {
-        const uint64_t v = row_value(d.seed[rr], cx, cy, cz);
-        nhot += exact_hot(bits, words_per_row, (int)rr, bucket_of(v, d.log2w));
+        nhot += signed_hot(bits, words_per_row, words, rr, row_value(d.seed[rr], cx, cy, cz), d.log2w);
         if (nhot + --left < need) return;
     }
     if (nhot < need) return;
-    for (uint32_t rr = 0; rr < (uint32_t)r; ++rr) {
-        const uint64_t v = row_value(d.seed[rr], cx, cy, cz);
-        if (exact_hot(bits, words_per_row, (int)rr, bucket_of(v, d.log2w))) return;
-    }
+    for (uint32_t rr = 0; rr < (uint32_t)r; ++rr)
+        if (signed_hot(bits, words_per_row, words, rr, row_value(d.seed[rr], cx, cy, cz), d.log2w)) return;
     int32_t ev[T > 0 ? T : kMaxRows];
     for (uint32_t rr = 0; rr < rows; ++rr) {
         const uint64_t v = row_value(d.seed[rr], cx, cy, cz);
@@ -244,25 +273,30 @@ __global__ void __launch_bounds__(256)
          base += warps << 5) {                                   // warp-uniform
         const uint64_t i = base + lane;
         const bool item = i < total;
-        uint32_t h = 0, cx = 0;
+        uint32_t h = 0, cx = 0, nslot = 0;
         uint64_t Tx = 0;
         uint4 v[2] = {make_uint4(kEmpty, kEmpty, kEmpty, kEmpty), make_uint4(kEmpty, kEmpty, kEmpty, kEmpty)};
         uint64_t slot0 = 0;
         if (item) {
             const uint64_t hi = div_invariant(i, d.G, gmagic);   // i = hi G + cx
-            h = hot[hi];
+            h = hot[hi];                                         // bucket << 1 | sign bit
             cx = (uint32_t)(i - hi * d.G);
             Tx = d.seed[r].a0 * (uint64_t)cx;
-            slot0 = (((uint64_t)h << s) - Tx) >> (64 - D);
+            // the lines whose cell in column cx has bucket and sign bit h: L in
+            // [h 2^(s-1) - Tx, (h+1) 2^(s-1) - Tx), one slot or two
+            const uint64_t lo = ((uint64_t)h << (s - 1)) - Tx;
+            slot0 = lo >> (64 - D);
+            nslot = ((lo + ((1ull << (s - 1)) - 1)) >> (64 - D)) == slot0 ? 1u : 2u;
 #pragma unroll
             for (int j = 0; j < 2; ++j)
-                v[j] = inl ? __ldg(inl + ((slot0 + j) & (nslots - 1))) : make_uint4(kCrowded, 0, 0, 0);
+                if ((uint32_t)j < nslot)
+                    v[j] = inl ? __ldg(inl + ((slot0 + j) & (nslots - 1))) : make_uint4(kCrowded, 0, 0, 0);
         }
-        // a line (cy, cz) whose cell in column cx falls in bucket h, inside
-        // the pass's line window and not routed, is a cell to check
+        // a line (cy, cz) whose cell in column cx has bucket and sign h,
+        // inside the pass's line window and not routed, is a cell to check
         auto wanted = [&](DirRecord p) {
             const uint32_t cy = p & 0xFFFFu, cz = p >> 16;
-            if (((line_value(d.seed[r], cy, cz) + Tx) >> s) != h) return false;
+            if (((line_value(d.seed[r], cy, cz) + Tx) >> (s - 1)) != h) return false;
             const uint64_t line = (uint64_t)cy + (uint64_t)d.G * cz;
             if (line < line_lo || line >= line_hi) return false;
             return !(skip.bits && routed_cell(skip, cx, cy, cz));
@@ -285,7 +319,7 @@ __global__ void __launch_bounds__(256)
             // a slot with more lines than an inline entry holds: its records,
             // the warp walking the longest list
             uint32_t e0 = 0, e1 = 0;
-            if (item && crowded) {
+            if (item && crowded && (uint32_t)j < nslot) {
                 const uint64_t slot = (slot0 + j) & (nslots - 1);
                 e0 = offsets[slot];
                 e1 = offsets[slot + 1];
@@ -339,13 +373,21 @@ cudaError_t launch_dir_build(const SketchDesc &d, int r, uint32_t D, bool inl, u
     return cudaGetLastError();
 }
 
+cudaError_t launch_signed_bits(const int32_t *C, const SketchDesc &d, int32_t theta, uint32_t *bits,
+                               int max_blocks, cudaStream_t s) {
+    if (d.W < 32 || theta < 1) return cudaErrorInvalidValue;
+    const uint64_t words = (uint64_t)d.rows * (d.W >> 5);
+    const uint64_t blocks = std::min<uint64_t>((words * 32 + 255) / 256, (uint64_t)max_blocks);
+    k_signed_bits<<<(unsigned)blocks, 256, 0, s>>>(C, words, theta, bits);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_hot_list(const uint32_t *bits, const SketchDesc &d, int r, uint32_t *list,
                             unsigned long long *count, uint64_t cap, int max_blocks,
                             cudaStream_t s) {
-    uint64_t wpr = d.W >> 5 ? d.W >> 5 : 1;
-    uint64_t blocks = (wpr + 255) / 256;
-    if (blocks > (uint64_t)max_blocks) blocks = (uint64_t)max_blocks;
-    k_hot_list<<<(unsigned)blocks, 256, 0, s>>>(bits, wpr, r, list, count, cap);
+    const uint64_t wpr = d.W >> 5;
+    const uint64_t blocks = std::min<uint64_t>((2 * wpr + 255) / 256, (uint64_t)max_blocks);
+    k_hot_list<<<(unsigned)blocks, 256, 0, s>>>(bits, wpr, (uint64_t)d.rows * wpr, r, list, count, cap);
     return cudaGetLastError();
 }
 
