@@ -556,7 +556,7 @@ static hs_status tk_prepare(hs_batch *b, uint32_t k, uint32_t F, bool *ok) {
     dev(&B.theta, nv * 4);
     dev(&B.status, nv * 4);
     dev(&B.scan, nv * 4);
-    dev(&B.bits, (size_t)nv * b->d.rows * (b->d.W >> 5) * 4);
+    dev(&B.bits, (size_t)nv * b->d.rows * (b->d.W >> 5) * 4 * 2);   // positive and negative maps
     dev(&B.hot, (size_t)nv * F * B.hot_cap * 4);
     dev(&B.hot_cnt, (size_t)nv * F * 4);
     dev(&B.pre, ((size_t)nv * F + 1) * 8);

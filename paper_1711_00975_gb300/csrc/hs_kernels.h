@@ -287,7 +287,7 @@ struct BatchTopkBufs {    // device buffers; per-volume arrays are volume-major
     int32_t *theta;               // nvol
     uint32_t *status;             // nvol: 0, or why the host must answer the volume
     uint32_t *scan;               // nvol: 1 when the volume's cells are scanned
-    uint32_t *bits;               // nvol x rows x W/32 hot bitmap
+    uint32_t *bits;               // 2 x nvol x rows x W/32: positive, then negative hot maps
     uint32_t *hot;                // nvol x F x hot_cap
     uint32_t *hot_cnt;            // nvol x F
     unsigned long long *pre;      // nvol x F + 1 work prefix

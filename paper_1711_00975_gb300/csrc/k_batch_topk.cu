@@ -144,8 +144,11 @@ __global__ void __launch_bounds__(1024) k_bt_theta(BatchTopkBufs b) {
     }
 }
 
-// 3. hot bitmap of every row of every volume: bit set iff |C| >= theta_v
-// (one warp a 32-bit word; W >= 32 so a word lies in one row)
+// 3. signed hot maps of every row of every volume (one warp a 32-bit word;
+// W >= 32 so a word lies in one row): the positive map's bit is set when
+// C >= theta_v, the negative map's when C <= -theta_v; a cell's signed count
+// sign * C can reach theta_v only when the map of its sign bit has its bucket.
+// bits: the positive maps of all volumes, then the negative maps.
 __global__ void k_bt_bits(const int32_t *__restrict__ C, const SketchDesc d, BatchTopkBufs b,
                           uint64_t words) {
     const uint32_t lane = threadIdx.x & 31;
@@ -166,9 +169,13 @@ __global__ void k_bt_bits(const int32_t *__restrict__ C, const SketchDesc d, Bat
             if (w >= words) break;                               // warp-uniform
             const uint32_t v = (uint32_t)(w / per_vol);
             const bool live = b.vol[v].use && b.status[v] == 0;
-            const int64_t x = c[u];
-            const unsigned bits = __ballot_sync(0xFFFFFFFFu, live && (x < 0 ? -x : x) >= (int64_t)b.theta[v]);
-            if (lane == 0) b.bits[w] = bits;
+            const int64_t x = c[u], th = b.theta[v];
+            const unsigned pos = __ballot_sync(0xFFFFFFFFu, live && x >= th);
+            const unsigned neg = __ballot_sync(0xFFFFFFFFu, live && x <= -th);
+            if (lane == 0) {
+                b.bits[w] = pos;
+                b.bits[words + w] = neg;
+            }
         }
     }
 }
@@ -176,22 +183,35 @@ __global__ void k_bt_bits(const int32_t *__restrict__ C, const SketchDesc d, Bat
 // 4. hot buckets of rows 0..F-1 of every volume
 __global__ void k_bt_hot(const SketchDesc d, BatchTopkBufs b, uint64_t words) {
     const uint64_t wpr = d.W >> 5;
+    const uint64_t all = (uint64_t)b.nvol * d.rows * wpr;       // words of one map
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += stride) {
-        const uint64_t vr = i / wpr, w = i - vr * wpr;   // vr = v * F + r
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 2 * words; i += stride) {
+        const uint32_t neg = i >= words;
+        const uint64_t k = i - neg * words;
+        const uint64_t vr = k / wpr, w = k - vr * wpr;   // vr = v * F + r
         const uint32_t v = (uint32_t)(vr / b.F), r = (uint32_t)(vr - (uint64_t)v * b.F);
         if (!b.vol[v].use || b.status[v]) continue;
-        uint32_t x = b.bits[((uint64_t)v * d.rows + r) * wpr + w];
+        uint32_t x = b.bits[neg * all + ((uint64_t)v * d.rows + r) * wpr + w];
         if (!x) continue;
         uint32_t at = atomicAdd(&b.hot_cnt[vr], (uint32_t)__popc(x));
         uint32_t *list = b.hot + vr * b.hot_cap;
         while (x) {
             const int bit = __ffs(x) - 1;
             x &= x - 1;
-            if (at < b.hot_cap) list[at] = (uint32_t)(w * 32 + bit);
+            if (at < b.hot_cap) list[at] = ((uint32_t)(w * 32 + bit) << 1) | neg;   // bucket, sign bit
             ++at;
         }
     }
+}
+
+// Is row rr of the cell with row value val hot for its sign in volume v?
+__device__ __forceinline__ bool bt_hot(const BatchTopkBufs &b, const SketchDesc &d, uint32_t v,
+                                       uint32_t rr, uint64_t val) {
+    const uint64_t wpr = d.W >> 5;
+    const uint32_t bk = bucket_of(val, d.log2w);
+    const uint64_t neg = (val >> (63 - d.log2w)) & 1ull;
+    const uint64_t all = (uint64_t)b.nvol * d.rows * wpr;
+    return (__ldg(b.bits + neg * all + ((uint64_t)v * d.rows + rr) * wpr + (bk >> 5)) >> (bk & 31)) & 1u;
 }
 
 // 5. each volume's search and the work of each (volume, row) pair, with its
@@ -294,25 +314,21 @@ __device__ __forceinline__ void bt_check(uint64_t cell, const int32_t *__restric
                                          const SketchDesc &d, const BatchTopkBufs &b) {
     const uint32_t rows = T > 0 ? (uint32_t)T : d.rows;
     const uint32_t need = rows - (rows - 1) / 2;
-    const uint64_t wpr = d.W >> 5;
     const uint32_t cx = (uint32_t)(cell & 0xFFFFu), cy = (uint32_t)((cell >> 16) & 0xFFFFu),
                    cz = (uint32_t)((cell >> 32) & 0xFFFFu), j = (uint32_t)(cell >> 48);
     const uint32_t v = j / b.F;
     const int r = (int)(j - v * b.F);
-    const uint32_t *bits = b.bits + (uint64_t)v * d.rows * wpr;
-    // hot rows: r and rows after r (the rows before r must be cold); the rows
-    // after r first, stopping once `need` is out of reach, the rows before r last
+    // hot rows (for the cell's sign): r and rows after r (the rows before r
+    // must be cold); the rows after r first, stopping once `need` is out of
+    // reach, the rows before r last
     uint32_t nhot = 1, left = rows - 1 - (uint32_t)r;
     for (uint32_t rr = (uint32_t)r + 1; rr < rows; ++rr) {
-        const uint64_t val = row_value(d.seed[rr], cx, cy, cz);
-        nhot += exact_hot(bits, wpr, (int)rr, bucket_of(val, d.log2w));
+        nhot += bt_hot(b, d, v, rr, row_value(d.seed[rr], cx, cy, cz));
         if (nhot + --left < need) return;
     }
     if (nhot < need) return;
-    for (uint32_t rr = 0; rr < (uint32_t)r; ++rr) {
-        const uint64_t val = row_value(d.seed[rr], cx, cy, cz);
-        if (exact_hot(bits, wpr, (int)rr, bucket_of(val, d.log2w))) return;
-    }
+    for (uint32_t rr = 0; rr < (uint32_t)r; ++rr)
+        if (bt_hot(b, d, v, rr, row_value(d.seed[rr], cx, cy, cz))) return;
     bt_candidate<T>(C + (uint64_t)v * d.rows * d.W, d, rows, v, b.vol[v].G, b.theta[v], cx, cy, cz, b);
 }
 
@@ -326,7 +342,6 @@ __global__ void __launch_bounds__(256, 6)   // 42 registers: 6 blocks an SM (mea
     const uint64_t total = b.pre[n];
     const uint32_t rows = T > 0 ? (uint32_t)T : d.rows;
     const uint32_t need = rows - (rows - 1) / 2;
-    const uint64_t wpr = d.W >> 5;
     const uint32_t s = 64 - d.log2w;
     const uint32_t lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -363,12 +378,10 @@ __global__ void __launch_bounds__(256, 6)   // 42 registers: 6 blocks an SM (mea
             if (b.scan[v]) {                 // one cell of a scanned volume: checked here
                 const uint64_t rest = div_invariant(local, G, gm), cz = div_invariant(rest, G, gm);
                 const uint32_t ccx = (uint32_t)(local - rest * G), cy = (uint32_t)(rest - cz * G);
-                const uint32_t *bits = b.bits + (uint64_t)v * d.rows * wpr;
                 uint32_t nhot = 0, left = rows;
                 bool skip = false;
                 for (uint32_t rr = 0; rr < rows; ++rr) {
-                    const uint64_t val = row_value(d.seed[rr], ccx, cy, (uint32_t)cz);
-                    nhot += exact_hot(bits, wpr, (int)rr, bucket_of(val, d.log2w));
+                    nhot += bt_hot(b, d, v, rr, row_value(d.seed[rr], ccx, cy, (uint32_t)cz));
                     if (nhot + --left < need) { skip = true; break; }
                 }
                 if (!skip)
@@ -382,12 +395,12 @@ __global__ void __launch_bounds__(256, 6)   // 42 registers: 6 blocks an SM (mea
                 rec = b.dir_rec[j];
                 const uint32_t D = b.vol[v].D;
                 Tx = d.seed[r].a0 * (uint64_t)cx;
-                // lines with L in [h 2^s - Tx, (h+1) 2^s - Tx): the records of
-                // slots a .. z, contiguous in the counting-sorted array (a run
-                // that wraps past the last slot continues at record 0: index
-                // e0 + k taken modulo `wrap`)
-                const uint64_t lo = ((uint64_t)h << s) - Tx;
-                const uint64_t a = lo >> (64 - D), z = (lo + ((1ull << s) - 1)) >> (64 - D);
+                // h = bucket << 1 | sign bit: lines with L in [h 2^(s-1) - Tx,
+                // (h+1) 2^(s-1) - Tx), the records of slots a .. z, contiguous
+                // in the counting-sorted array (a run that wraps past the last
+                // slot continues at record 0: index e0 + k taken modulo `wrap`)
+                const uint64_t lo = ((uint64_t)h << (s - 1)) - Tx;
+                const uint64_t a = lo >> (64 - D), z = (lo + ((1ull << (s - 1)) - 1)) >> (64 - D);
                 e0 = __ldg(off + a);
                 const uint32_t ez = __ldg(off + z + 1);
                 const uint32_t nrec = __ldg(off + (1ull << D));
@@ -408,7 +421,7 @@ __global__ void __launch_bounds__(256, 6)   // 42 registers: 6 blocks an SM (mea
                 if (idx >= wrap) idx -= wrap;
                 const DirRecord p = __ldg(rec + idx);
                 const uint32_t cy = p & 0xFFFFu, cz = p >> 16;
-                take = ((line_value(d.seed[r], cy, cz) + Tx) >> s) == h;
+                take = ((line_value(d.seed[r], cy, cz) + Tx) >> (s - 1)) == h;
                 cell = (uint64_t)cx | ((uint64_t)cy << 16) | ((uint64_t)cz << 32) | ((uint64_t)j << 48);
             }
             const unsigned m = __ballot_sync(0xFFFFFFFFu, take);
