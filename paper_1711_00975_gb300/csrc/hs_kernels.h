@@ -242,7 +242,6 @@ inline uint4 *dir_inline(uint32_t *offsets, uint32_t D) {
 cudaError_t launch_dir_build(const SketchDesc &d, int r, uint32_t D, bool inl, uint32_t *offsets,
                              uint32_t *cursor, DirRecord *rec, uint32_t *scan_scratch,
                              int max_blocks, cudaStream_t s, int *launches);
-// bucket indices of the set bits of row r of an exact (one bit per bucket) hot bitmap
 // signed hot maps of every row for threshold theta >= 1 (W >= 32): bits holds
 // rows x W/32 words of the positive map (C >= theta), then of the negative
 // map (C <= -theta)

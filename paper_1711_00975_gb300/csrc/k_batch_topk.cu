@@ -8,10 +8,11 @@
 //     their estimates;
 //  2. theta_v = the kk-th largest of those estimates (a lower bound on the
 //     kk-th largest estimate over all cells), by a radix select in one block;
-//  3. the hot-bucket bitmap of every row (|C| >= theta_v);
-//  4. the hot buckets of the first F rows, listed;
+//  3. the signed hot maps of every row (C >= theta_v, C <= -theta_v): a cell
+//     whose sign in row r is s_r can reach theta_v only where s_r C >= theta_v;
+//  4. the hot (bucket, sign) pairs of the first F rows, listed;
 //  5. per volume the cheaper search: a scan of its G_v^3 cells, or directory
-//     queries (|hot buckets| * G_v a row); the work prefix-summed;
+//     queries (|hot pairs| * G_v a row); the work prefix-summed;
 //  6. both searches over all volumes in one persistent grid: every cell with
 //     estimate >= theta_v is a candidate;
 //  7. one block per volume finds the kk-th best candidate (estimate desc, key
@@ -217,10 +218,10 @@ __device__ __forceinline__ bool bt_hot(const BatchTopkBufs &b, const SketchDesc 
 // 5. each volume's search and the work of each (volume, row) pair, with its
 // exclusive prefix (one block).  A volume is scanned (all G^3 cells, the
 // work of its pair (v, 0)) when that is cheaper than its directory queries
-// (one query of a (hot bucket, cx) pair reads about 1 + G^2 / W + G^2 / 2^D
-// lines) or
-// when a row's hot buckets overflowed the list; otherwise every pair (v, r)
-// has |hot buckets of row r| * G directory queries.
+// (one query of a (hot bucket, sign, cx) triple reads about
+// 1 + G^2 / (2 W) + G^2 / 2^D lines; the model counts a whole bucket, G^2 / W)
+// or when a row's hot pairs overflowed the list; otherwise every pair (v, r)
+// has |hot (bucket, sign) pairs of row r| * G directory queries.
 constexpr double kMaxBatchScan = 17179869184.0;   // 2^34 cells
 
 __global__ void __launch_bounds__(1024) k_bt_prefix(BatchTopkBufs b, uint32_t log2w) {
@@ -335,7 +336,7 @@ __device__ __forceinline__ void bt_check(uint64_t cell, const int32_t *__restric
 constexpr int kBtQueue = 64;   // per-warp queue of records to check
 
 template <int T>
-__global__ void __launch_bounds__(256, 6)   // 42 registers: 6 blocks an SM (measured faster than 4)
+__global__ void __launch_bounds__(256, 5)   // 48 registers, 5 blocks an SM: faster than 6 or 4
     k_bt_query(const int32_t *__restrict__ C, const SketchDesc d, BatchTopkBufs b) {
     __shared__ uint64_t queue[8][kBtQueue];
     const uint32_t n = b.nvol * b.F;
@@ -413,27 +414,35 @@ __global__ void __launch_bounds__(256, 6)   // 42 registers: 6 blocks an SM (mea
         uint32_t most = len;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) most = max(most, __shfl_xor_sync(0xFFFFFFFFu, most, o));
-        for (uint32_t k = 0; k < most; ++k) {
-            bool take = false;
-            uint64_t cell = 0;
-            if (k < len) {
-                uint32_t idx = e0 + k;
+        for (uint32_t k = 0; k < most; k += 4) {
+            DirRecord p[4];                  // four records loaded before any is checked
+#pragma unroll
+            for (uint32_t u = 0; u < 4; ++u) {
+                uint32_t idx = e0 + k + u;
                 if (idx >= wrap) idx -= wrap;
-                const DirRecord p = __ldg(rec + idx);
-                const uint32_t cy = p & 0xFFFFu, cz = p >> 16;
-                take = ((line_value(d.seed[r], cy, cz) + Tx) >> (s - 1)) == h;
-                cell = (uint64_t)cx | ((uint64_t)cy << 16) | ((uint64_t)cz << 32) | ((uint64_t)j << 48);
+                p[u] = k + u < len ? __ldg(rec + idx) : 0u;
             }
-            const unsigned m = __ballot_sync(0xFFFFFFFFu, take);
-            if (take) qu[nq + __popc(m & lt)] = cell;
-            nq += __popc(m);
-            if (nq >= 32) {
-                __syncwarp();
-                bt_check<T>(qu[lane], C, d, b);
-                __syncwarp();
-                if (lane < nq - 32) qu[lane] = qu[32 + lane];
-                nq -= 32;
-                __syncwarp();
+#pragma unroll
+            for (uint32_t u = 0; u < 4; ++u) {
+                bool take = false;
+                uint64_t cell = 0;
+                if (k + u < len) {
+                    const uint32_t cy = p[u] & 0xFFFFu, cz = p[u] >> 16;
+                    take = ((line_value(d.seed[r], cy, cz) + Tx) >> (s - 1)) == h;
+                    cell = (uint64_t)cx | ((uint64_t)cy << 16) | ((uint64_t)cz << 32) |
+                           ((uint64_t)j << 48);
+                }
+                const unsigned m = __ballot_sync(0xFFFFFFFFu, take);
+                if (take) qu[nq + __popc(m & lt)] = cell;
+                nq += __popc(m);
+                if (nq >= 32) {
+                    __syncwarp();
+                    bt_check<T>(qu[lane], C, d, b);
+                    __syncwarp();
+                    if (lane < nq - 32) qu[lane] = qu[32 + lane];
+                    nq -= 32;
+                    __syncwarp();
+                }
             }
         }
     }
