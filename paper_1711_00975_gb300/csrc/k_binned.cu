@@ -81,10 +81,38 @@ __global__ void __launch_bounds__(kAccThreads)
         }
     }
     __syncthreads();
+    // C[bin range] += acc, four counters a lane access and eight accesses of a
+    // lane in flight (the counters of a bin are 16-byte aligned when S >= 2);
+    // all-zero quads are neither read nor written
     uint32_t *dst = C + ((uint64_t)bin << S);
-    for (uint32_t i = threadIdx.x; i < nacc; i += blockDim.x) {
-        const int32_t v = acc[i];
-        if (v) dst[i] += (uint32_t)v;
+    if (nacc >= 4) {
+        const uint32_t nq = nacc >> 2;
+        const int4 *acc4 = reinterpret_cast<const int4 *>(acc);
+        uint4 *dst4 = reinterpret_cast<uint4 *>(dst);
+        auto any = [](int4 a) { return (a.x | a.y | a.z | a.w) != 0; };
+        for (uint32_t i0 = threadIdx.x; i0 < nq; i0 += 8 * blockDim.x) {
+            uint4 c[8];
+#pragma unroll
+            for (uint32_t u = 0; u < 8; ++u) {
+                const uint32_t i = i0 + u * blockDim.x;
+                if (i < nq && any(acc4[i])) c[u] = dst4[i];
+            }
+#pragma unroll
+            for (uint32_t u = 0; u < 8; ++u) {
+                const uint32_t i = i0 + u * blockDim.x;
+                if (i < nq) {
+                    const int4 a = acc4[i];
+                    if (any(a))
+                        dst4[i] = make_uint4(c[u].x + (uint32_t)a.x, c[u].y + (uint32_t)a.y,
+                                             c[u].z + (uint32_t)a.z, c[u].w + (uint32_t)a.w);
+                }
+            }
+        }
+    } else {
+        for (uint32_t i = threadIdx.x; i < nacc; i += blockDim.x) {
+            const int32_t v = acc[i];
+            if (v) dst[i] += (uint32_t)v;
+        }
     }
     for (uint32_t b = threadIdx.x; b < nblocks; b += blockDim.x) B.fill[(uint64_t)bin * nblocks + b] = 0;
 }
