@@ -18,7 +18,9 @@ counts s_r(j) * C[r][b_r(j)], the lower median for even t):
    before r are cold (so from its first hot row), and then estimates it.
 
 Each test plants nothing: it checks that these rules report exactly the cells
-whose oracle estimate reaches theta, each once.
+whose oracle estimate reaches theta, each once, and that the directory's
+interval of line values per (column, bucket, sign) follows from the oracle's
+hash.
 """
 import numpy as np
 import pytest
@@ -123,3 +125,33 @@ def test_negative_counters_make_cells_hot_through_the_negative_map():
     by_neg = hot & (s < 0)
     assert by_neg.any()                                # the negative maps are exercised
     assert set(reports) == set(np.nonzero(est >= theta)[0].tolist())
+
+
+@pytest.mark.parametrize("log2w", [4, 13, 24, 26])
+def test_bucket_and_sign_of_a_column_is_a_half_interval_of_line_values(log2w):
+    """The directory query's interval: in row r, with v = a0 cx + L(cy, cz)
+    (mod 2^64) and L(cy, cz) = a1 cy + a2 cz + b, the cells of column cx whose
+    (bucket, sign) is (B, s) are the lines with L in
+    [h 2^(63 - log2 W) - a0 cx, (h + 1) 2^(63 - log2 W) - a0 cx) (mod 2^64),
+    h = B << 1 | (s < 0): the oracle's bucket is the top log2 W bits of v and
+    its sign the next bit.  An interval that long covers one or two slots of
+    2^(64 - D) values for any D <= log2 W + 1."""
+    rng = np.random.default_rng(log2w)
+    p = oracle.Params(5, log2w, 64.0, 1.0, hash_seed=31 + log2w)
+    M = 1 << 64
+    half = 1 << (63 - log2w)
+    for r in range(p.rows):
+        a0, a1, a2, b = (int(x) for x in p.seeds[4 * r:4 * r + 4])
+        for _ in range(200):
+            cx, cy, cz = (int(x) for x in rng.integers(0, p.G, size=3))
+            B, s = oracle.hash_row(p, r, (cx, cy, cz))
+            h = (B << 1) | (1 if s < 0 else 0)
+            L = (a1 * cy + a2 * cz + b) % M
+            lo = (h * half - a0 * cx) % M
+            assert (L - lo) % M < half                        # inside its own interval
+            other = h ^ 1                                     # the same bucket, other sign
+            assert (L - (other * half - a0 * cx)) % M >= half
+            for D in range(1, log2w + 2):
+                first = lo >> (64 - D)
+                last = ((lo + half - 1) % M) >> (64 - D)
+                assert (last - first) % (1 << D) <= 1         # one slot or two
