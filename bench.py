@@ -828,13 +828,10 @@ def run_ours(args):
         ems = e0.elapsed_time(e1) / steps_e
         wall = (time.perf_counter() - t0) / steps_e
         est = sk.stats(reset=True)
-        # the host link alone: one plain copy of the same pinned buffer
-        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        c0.record(stream)
-        dev.copy_(host, non_blocking=True)
-        c1.record(stream)
-        torch.cuda.synchronize()
-        link_gbs = 12.0 * n_local / (c0.elapsed_time(c1) * 1e-3) / 1e9
+        # the host link alone: the best of five plain 1 GiB copies from the
+        # same pinned buffer (one copy of all 12 GB runs far below the link)
+        m = min(host.numel(), 1 << 28)
+        link_gbs = measure_h2d(host.view(-1)[:m], dev.view(-1)[:m], stream)
         step_ms = max(ems, wall * 1e3)
         e2e = {"value": n / (step_ms * 1e-3), "unit": "particles/s",
                "h2d_bytes_per_step": 12 * n, "d2h_bytes_per_step": 12 * k,
@@ -843,7 +840,8 @@ def run_ours(args):
                "h2d_gbs_copies": est["h2d_bytes"] / (est["h2d_ms"] * 1e-3) / 1e9 if est["h2d_ms"] else None,
                "h2d_gbs_plain_copy": link_gbs,
                "note": "h2d_gbs: bytes over the link per step time; h2d_gbs_copies: the staged "
-                       "copies' own rate; h2d_gbs_plain_copy: one copy of the same pinned buffer"}
+                       "copies' own rate; h2d_gbs_plain_copy: the best of five 1 GiB copies "
+                       "of the same pinned buffer"}
 
     packed = None
     if not args.no_packed and world == 1:
