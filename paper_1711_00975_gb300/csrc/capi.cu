@@ -637,7 +637,7 @@ hs_status search_pass_dir(hs_sketch *h, int32_t theta, SearchMode mode, int64_t 
                             cudaMemcpyDeviceToHost, h->stream));
     HS_CUDA(cudaStreamSynchronize(h->stream));
     // relative costs, from GB300 timings: one scanned cell ~ 1 (about 1e10
-    // cells/s); one (cx, hot bucket) query ~ 0.25 per directory slot it reads
+    // cells/s); one (cx, hot bucket and sign) query ~ 0.25 per directory slot it reads
     // (about 4e10 queries/s); building a directory ~ 1 per line.  The query
     // and build weights are kept about 4x above the measured ones.
     const double per_slot = (double)lines / (double)(1ull << h->dir_D);
